@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test names the passage of Kronbichler & Kormann (arXiv:1711.03590) or
+the piece of mathematics that fixes the expected value.  The expected values
+come from closed forms (tests/golden), exact polynomial algebra (ref1d.py),
+the separable Kronecker form of the Cartesian operators (Remark, Sec. 2.1),
+invariants of the weak forms (Eq. poisson_sip, Eq. advection), closed-form
+cell volumes of the sine-mapped cube, and the convergence order of the SIPG
+discretization.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import ref1d
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line)
+    return rows
+
+
+def _ev(s):
+    return float(eval(s, {"sqrt": math.sqrt}))
+
+
+# ---------------------------------------------------------------- 1D rules
+
+def test_quadrature_closed_forms():
+    """Gauss / Gauss-Lobatto rules equal their textbook closed forms."""
+    for row in _read_golden("quadrature_1d.txt"):
+        left, right = row.split("|")
+        tok = left.split()
+        rule, k = tok[0], int(tok[1])
+        pts = np.array([_ev(t) for t in tok[2:]])
+        wts = np.array([_ev(t) for t in right.split()])
+        x, w = oracle.gauss(k) if rule == "gauss" else oracle.gauss_lobatto(k)
+        np.testing.assert_allclose(x, pts, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(w, wts, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("k", range(1, 13))
+def test_gauss_exactness(k):
+    """k-point Gauss integrates x^m exactly for m <= 2k-1; for x^{2k} the
+    error is the classical (k!)^4 / ((2k+1) ((2k)!)^2) on [0,1]."""
+    x, w = oracle.gauss(k)
+    assert np.all(np.diff(x) > 0) and abs(w.sum() - 1.0) < 1e-14
+    for m in range(2 * k):
+        assert abs(np.dot(w, x ** m) - 1.0 / (m + 1)) < 2e-15
+    err = 1.0 / (2 * k + 1) - np.dot(w, x ** (2 * k))
+    expect = math.factorial(k) ** 4 / ((2 * k + 1) * math.factorial(2 * k) ** 2)
+    assert abs(err - expect) < 2e-15 + 1e-9 * expect
+
+
+@pytest.mark.parametrize("k", range(2, 13))
+def test_lobatto_exactness_and_nodes(k):
+    """k-point Gauss-Lobatto: endpoints included, exact for m <= 2k-3,
+    nodes equal the roots of P'_{k-1} computed by numpy's Legendre class."""
+    x, w = oracle.gauss_lobatto(k)
+    assert x[0] == 0.0 and x[-1] == 1.0
+    np.testing.assert_allclose(x, ref1d.gl_nodes(k), rtol=0, atol=1e-14)
+    for m in range(2 * k - 2):
+        assert abs(np.dot(w, x ** m) - 1.0 / (m + 1)) < 5e-15
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 9])
+def test_lagrange_basis(k):
+    """Product-formula Lagrange polynomials and derivatives equal numpy's
+    monomial-coefficient polynomials through the same nodes (the monomial
+    form loses about 1e-11 at k = 9, which sets the tolerance)."""
+    from numpy.polynomial import polynomial as P
+    x, _ = oracle.gauss_lobatto(k)
+    lc = ref1d.lagrange_coeffs(ref1d.gl_nodes(k))
+    for t in np.linspace(0, 1, 7):
+        for j in range(k):
+            assert abs(oracle.lagrange(x, j, t) - P.polyval(t, lc[j])) < 1e-10
+            assert abs(oracle.lagrange(x, j, t, deriv=True) - P.polyval(t, P.polyder(lc[j]))) < 1e-8
+
+
+# ---------------------------------------------------------------- 1D matrices
+
+def _golden_matrices():
+    out = {}
+    for row in _read_golden("matrices_1d.txt"):
+        tok = row.split(None, 2)
+        name, p = tok[0], int(tok[1])
+        mat = [[float(Fraction(e)) for e in r.split()] for r in tok[2].split(";")]
+        out[(name, p)] = np.array(mat)
+    return out
+
+
+def test_ref1d_matches_hand_worked_matrices():
+    """The independent numpy 1D construction reproduces the hand-worked
+    closed-form M and K (so it can stand in for them at higher degree)."""
+    g = _golden_matrices()
+    for p in (1, 2):
+        r = ref1d.matrices_1d(p)
+        np.testing.assert_allclose(r["M"], g[("M", p)], atol=1e-14)
+        np.testing.assert_allclose(r["K"], g[("K", p)], atol=1e-13)
+        assert abs(r["K"].sum(axis=1)).max() < 1e-13
+        assert abs(r["M"].sum() - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5])
+def test_mass_single_cell_is_kronecker(p):
+    """On one Cartesian cell of size h, (phi_i, phi_j) = h^3 (M (x) M (x) M),
+    the mass evaluation of Sec. 3.1 (interpolate, JxW, integrate)."""
+    k = p + 1
+    for nx in (1, 2):
+        mesh = dict(n=(nx, nx, nx), periodic=False)
+        n = oracle.n_dofs(mesh, p)
+        cols = []
+        for j in range(k ** 3):
+            e = np.zeros(n)
+            e[j] = 1.0
+            cols.append(oracle.mass_apply(mesh, p, e)[:k ** 3])
+        Mo = np.array(cols).T
+        M1 = ref1d.matrices_1d(p)["M"] / nx
+        np.testing.assert_allclose(Mo, ref1d.kron3(M1, M1, M1), rtol=0, atol=1e-15 * nx ** -3 * 10)
+
+
+def test_dof_points_cartesian():
+    for p in (1, 3):
+        Ns = (2, 3, 1)
+        got = oracle.dof_points(dict(n=Ns), p)
+        np.testing.assert_allclose(got, ref1d.cartesian_dof_points(p, Ns), atol=1e-15)
+
+
+# ---------------------------------------------------------------- separable 3D operators
+
+SEP_CASES = [(p, Ns, per) for p in (1, 2, 3) for Ns in ((1, 1, 1), (2, 2, 2), (4, 4, 4), (3, 2, 1))
+             for per in (True, False)] + [(4, (2, 2, 2), True), (4, (2, 1, 3), False), (5, (1, 2, 1), True)]
+
+
+@pytest.mark.parametrize("p,Ns,periodic", SEP_CASES)
+def test_sipg_cartesian_equals_kronecker_form(p, Ns, periodic):
+    """Cartesian SIPG with kappa = 1 and tau = (p+1)^2/h equals
+    A1 (x) M (x) M + M (x) A1 (x) M + M (x) M (x) A1 (Remark, Sec. 2.1) with
+    A1 the 1D SIPG matrix of Eq. (poisson_sip), built by exact polynomial
+    algebra.  The 4^3 periodic p=2 case is the 1728-dof workload."""
+    if np.prod(Ns) * (p + 1) ** 3 > 3000:
+        pytest.skip("dense comparison too large")
+    mesh = dict(n=Ns, periodic=periodic)
+    A = oracle.assemble(mesh, p, dict(op="sipg")).toarray()
+    R = ref1d.separable_sipg(p, Ns, periodic)
+    assert np.abs(A - R).max() <= 1e-13 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("p,Ns,periodic", [(1, (2, 2, 2), True), (2, (3, 2, 1), False),
+                                           (3, (2, 2, 2), False), (2, (4, 4, 4), True)])
+def test_advection_cartesian_equals_kronecker_form(p, Ns, periodic):
+    """Cartesian upwind advection with constant c is separable in the same way:
+    the 1D operator -(v', c_d u) + upwind flux (Eq. advection; boundary flux
+    |c.n| u of Algorithm 1 (iv)(c)), Kronecker-multiplied with 1D masses."""
+    c = (1.0, 0.5, 0.25)
+    mesh = dict(n=Ns, periodic=periodic)
+    A = oracle.assemble(mesh, p, dict(op="advection", velocity=c)).toarray()
+    R = ref1d.separable_advection(p, Ns, periodic, c)
+    assert np.abs(A - R).max() <= 1e-13 * np.abs(R).max()
+
+
+# ---------------------------------------------------------------- invariants
+
+DEFORMED = dict(mapping=1, amplitude=0.1)
+
+
+@pytest.mark.parametrize("coeff", [0, 1])
+@pytest.mark.parametrize("Ns", [(1, 1, 1), (2, 2, 2), (3, 2, 2)])
+def test_sipg_kills_constants_periodic(Ns, coeff):
+    """Every term of Eq. (poisson_sip) contains grad 1 = 0 or [[1]] = 0, so
+    A 1 = 0 with periodic boundaries on any geometry and coefficient."""
+    mesh = dict(n=Ns, periodic=True, **DEFORMED)
+    for p in (1, 3):
+        A = oracle.assemble(mesh, p, dict(op="sipg", coeff=coeff))
+        y = A @ np.ones(A.shape[0])
+        assert np.abs(y).max() < 1e-12 * abs(A).max()
+
+
+def test_advection_kills_constants_cartesian_periodic():
+    """With c constant on a Cartesian periodic mesh, a(v, 1) = -(grad v, c) +
+    <v, c.n> = 0 exactly (divergence theorem, exact quadrature)."""
+    mesh = dict(n=(3, 2, 2), periodic=True)
+    A = oracle.assemble(mesh, 2, dict(op="advection"))
+    assert np.abs(A @ np.ones(A.shape[0])).max() < 1e-14
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("coeff", [0, 1])
+def test_sipg_symmetric_deformed(periodic, coeff):
+    """The SIPG bilinear form is symmetric in u and v on any geometry."""
+    mesh = dict(n=(2, 3, 2), periodic=periodic, **DEFORMED)
+    A = oracle.assemble(mesh, 2, dict(op="sipg", coeff=coeff)).toarray()
+    assert np.abs(A - A.T).max() < 1e-14 * np.abs(A).max()
+
+
+def test_sipg_positive_definite_dirichlet():
+    """With tau large enough the Dirichlet SIPG form is coercive."""
+    mesh = dict(n=(2, 2, 2), periodic=False, **DEFORMED)
+    A = oracle.assemble(mesh, 2, dict(op="sipg", coeff=1)).toarray()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+
+
+# ---------------------------------------------------------------- exact polynomial identities
+
+def _face_int(expr, var, val, X, Y, Z):
+    import sympy as sp
+    others = [v for v in (X, Y, Z) if v != var]
+    e = expr.subs(var, val)
+    return sp.integrate(e, (others[0], 0, 1), (others[1], 0, 1))
+
+
+@pytest.mark.parametrize("p,N", [(1, 2), (2, 2), (3, 1), (2, 3)])
+def test_sipg_dirichlet_polynomial_identity(p, N):
+    """For v = l (linear) and u = q (monomial of degree <= p per direction),
+    both continuous and reproduced exactly by the interpolant, the interior
+    face terms vanish and Eq. (poisson_sip) with the mirror principle gives
+    a(l, q) = int grad l . grad q - int_dO (d_n l q + l d_n q) + 2 int_dO tau l q,
+    tau = (p+1)^2 N, evaluated here by exact symbolic integration."""
+    sp = pytest.importorskip("sympy")
+    X, Y, Z = sp.symbols("x y z")
+    mesh = dict(n=N, periodic=False)
+    pts = ref1d.cartesian_dof_points(p, (N, N, N))
+    A = oracle.assemble(mesh, p, dict(op="sipg"))
+    tau = (p + 1) ** 2 * N
+    rng = np.random.default_rng(7)
+    for trial in range(3):
+        a, b, c = (int(t) for t in rng.integers(0, p + 1, 3))
+        q = X ** a * Y ** b * Z ** c
+        lin = 1 + 2 * X - Y + 3 * Z if trial else sp.Integer(1)
+        grad = lambda f: [sp.diff(f, v) for v in (X, Y, Z)]
+        vol = sp.integrate(sum(gl * gq for gl, gq in zip(grad(lin), grad(q))), (X, 0, 1), (Y, 0, 1), (Z, 0, 1))
+        bnd = 0
+        for d, var in enumerate((X, Y, Z)):
+            for val, sgn in ((0, -1), (1, 1)):
+                dn_l = sgn * sp.diff(lin, var)
+                dn_q = sgn * sp.diff(q, var)
+                bnd += _face_int(-dn_l * q - lin * dn_q + 2 * tau * lin * q, var, val, X, Y, Z)
+        expect = float(vol + bnd)
+        fq = sp.lambdify((X, Y, Z), q, "numpy")
+        fl = sp.lambdify((X, Y, Z), lin + 0 * X, "numpy")
+        u = fq(pts[:, 0], pts[:, 1], pts[:, 2]) * np.ones(len(pts))
+        v = fl(pts[:, 0], pts[:, 1], pts[:, 2]) * np.ones(len(pts))
+        got = v @ (A @ u)
+        assert abs(got - expect) <= 1e-11 * max(1.0, abs(expect)), (a, b, c, got, expect)
+
+
+@pytest.mark.parametrize("p,N", [(1, 2), (2, 3)])
+def test_advection_dirichlet_boundary_sum(p, N):
+    """Summing all rows (v = 1) leaves only the boundary flux of Algorithm 1
+    (iv)(c): 1^T A u = int_dO |c.n| q for a polynomial q in the space."""
+    sp = pytest.importorskip("sympy")
+    X, Y, Z = sp.symbols("x y z")
+    c = (1.0, 0.5, 0.25)
+    mesh = dict(n=N, periodic=False)
+    pts = ref1d.cartesian_dof_points(p, (N, N, N))
+    A = oracle.assemble(mesh, p, dict(op="advection", velocity=c))
+    q = X ** p * Y * Z ** min(p, 2) + 2
+    expect = 0
+    for d, var in enumerate((X, Y, Z)):
+        for val in (0, 1):
+            expect += abs(c[d]) * _face_int(q, var, val, X, Y, Z)
+    u = sp.lambdify((X, Y, Z), q, "numpy")(pts[:, 0], pts[:, 1], pts[:, 2]) * np.ones(len(pts))
+    got = np.ones(len(pts)) @ (A @ u)
+    assert abs(got - float(expect)) < 1e-12 * abs(float(expect))
+
+
+# ---------------------------------------------------------------- geometry of the sine map
+
+def _exact_cell_volume(ijk, N, a):
+    """|K| for the map x = X + a s(X) (1,1,1): det J = 1 + a (s_x + s_y + s_z)
+    (rank-one update of the identity), integrated in closed form over the
+    Cartesian box of the cell."""
+    lo = [ijk[d] / N for d in range(3)]
+    hi = [(ijk[d] + 1) / N for d in range(3)]
+    S = [math.sin(math.pi * hi[d]) - math.sin(math.pi * lo[d]) for d in range(3)]
+    C = [(math.cos(math.pi * lo[d]) - math.cos(math.pi * hi[d])) / math.pi for d in range(3)]
+    vol = 1.0 / N ** 3
+    vol += a * (S[0] * C[1] * C[2] + C[0] * S[1] * C[2] + C[0] * C[1] * S[2])
+    return vol
+
+
+@pytest.mark.parametrize("p,N", [(2, 3), (4, 4), (7, 2)])
+def test_cell_volumes_sine_map(p, N):
+    """The k-point Gauss volume of every mapped cell matches the closed form
+    within the Gauss error (smooth trigonometric det J), and the cells tile
+    the unit cube (the map fixes the boundary of [0,1]^3)."""
+    mesh = dict(n=N, periodic=False, **DEFORMED)
+    tot = 0.0
+    for c in range(N ** 3):
+        ijk = (c % N, (c // N) % N, c // N ** 2)
+        v = oracle.cell_volume(mesh, p, c)
+        ex = _exact_cell_volume(ijk, N, 0.1)
+        tol = 2e-2 * (math.pi / N) ** (2 * (p + 1)) / math.factorial(2 * (p + 1)) + 1e-16
+        assert abs(v - ex) <= tol, (c, v, ex)
+        tot += v
+    assert abs(tot - 1.0) < 1e-6 if p == 2 else abs(tot - 1.0) < 1e-10
+
+
+def test_mass_sum_is_volume():
+    """sum_ij M_ij = sum_q det J w = |Omega| up to quadrature error."""
+    for mesh, tol in ((dict(n=(3, 2, 4)), 1e-14), (dict(n=4, **DEFORMED), 1e-9)):
+        p = 4
+        n = oracle.n_dofs(mesh, p)
+        assert abs(oracle.mass_apply(mesh, p, np.ones(n)).sum() - 1.0) < tol
+
+
+# ---------------------------------------------------------------- consistency and convergence
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p", [1, 2])
+def test_sipg_manufactured_convergence_deformed(p):
+    """Dirichlet SIPG on the sine-deformed cube with kappa = 1 + 0.5 sin(2 pi x):
+    the discrete solution of a(u_h, v) = (f, v) with f = -div(kappa grad u),
+    u = sin(pi x) sin(pi y) sin(pi z), converges at order p+1 in L2 --
+    a wrong sign, geometry term or penalty breaks consistency and the order."""
+    errs = []
+    Ns = (2, 4, 8) if p == 1 else (2, 4, 6)
+    for N in Ns:
+        mesh = dict(n=N, periodic=False, **DEFORMED)
+        A = oracle.assemble(mesh, p, dict(op="sipg", coeff=1))
+        b = oracle.rhs(mesh, p, which=1)
+        x, it, rr = oracle.cg(A, b, rtol=1e-12, maxit=20000)
+        assert rr < 1e-12
+        errs.append(oracle.l2_error(mesh, p, x))
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+    assert rates[-1] > p + 1 - 0.35, (errs, rates)
+
+
+def test_l2_error_of_interpolant_is_small():
+    """The L2 error routine: interpolating u itself gives an O(h^{p+1}) error."""
+    mesh = dict(n=4, periodic=False, **DEFORMED)
+    p = 3
+    pts = oracle.dof_points(mesh, p)
+    u = np.sin(np.pi * pts[:, 0]) * np.sin(np.pi * pts[:, 1]) * np.sin(np.pi * pts[:, 2])
+    assert oracle.l2_error(mesh, p, u) < 2e-3
+    assert oracle.l2_error(mesh, p, 0 * u) > 0.3  # ||u|| = (1/2)^{3/2}
+
+
+# ---------------------------------------------------------------- two routes agree
+
+R1R2 = [(dict(n=(1, 1, 1), periodic=True, **DEFORMED), 3), (dict(n=(2, 2, 2), periodic=True, **DEFORMED), 2),
+        (dict(n=(3, 2, 1), periodic=False, **DEFORMED), 2), (dict(n=(2, 1, 3), periodic=False), 4),
+        (dict(n=(2, 2, 2), periodic=False, **DEFORMED), 5)]
+
+
+@pytest.mark.parametrize("mesh,p", R1R2)
+@pytest.mark.parametrize("form", [dict(op="sipg", coeff=1), dict(op="sipg", coeff=0, penalty_scale=2.5),
+                                  dict(op="advection", velocity=(1.0, 0.5, 0.25)),
+                                  dict(op="advection", velocity=(-0.3, 0.0, 0.7))])
+def test_assembled_equals_cellwise(mesh, p, form):
+    """Route R1 (face loop filling four blocks) and route R2 (cell by cell,
+    each face tested from its own side) give the same y = A u."""
+    n = oracle.n_dofs(mesh, p)
+    u = np.random.default_rng(3).uniform(-1, 1, n)
+    y1 = oracle.assemble(mesh, p, form) @ u
+    y2 = oracle.apply(mesh, p, form, u)
+    assert np.linalg.norm(y1 - y2) <= 1e-14 * np.linalg.norm(y1)
+    sub = np.array([0, oracle.n_cells(mesh) - 1])
+    y3 = oracle.apply(mesh, p, form, u, cells=sub)
+    k3 = (p + 1) ** 3
+    for c in sub:
+        np.testing.assert_array_equal(y3[c * k3:(c + 1) * k3], y2[c * k3:(c + 1) * k3])
