@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Throughput of the SIPG DG operator apply on GB300 (DoFs/s).
+
+Workload: 32^3 = 32768 hexahedra of the unit cube mapped by
+x_i + 0.1 sin(pi x) sin(pi y) sin(pi z), full per-quadrature-point Jacobians
+(geometry variant G3), kappa = 1 + 0.5 sin(2 pi x), Dirichlet boundary,
+degree 4 (125 dofs per cell, 4,096,000 dofs), FP64 arithmetic.  One step is
+one operator evaluation y = A u (cell and face integrals, one kernel launch).
+Inputs (vector and geometry, > 500 MB) stay resident in HBM and exceed the
+129 MB L2, so no flush is needed between steps.
+
+The JSON line also carries the same workload in FP32, the upwind advection
+operator, one fused CG iteration, the roofline of the apply kernel, the
+end-to-end rate through the C ABI with host buffers, and the FP64 oracle
+timed on the host cores on a bounded sample of cells.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--degree P] [--impl gb300|reference]
+
+Under torchrun every rank runs an independent replica (the operator needs no
+exchange on one GPU); rank 0 prints the line, value = all ranks' dofs / the
+slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import dg_inputs  # noqa: E402
+
+METRIC = "DoFs/s of SIPG dg_apply (FP64 vs FP32) and % HBM roofline; solves/s, p50/p99 latency"
+UNIT = "DoFs/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "source": "fallback"}
+# FP64 vector-ALU peak from the unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM
+# (2 DFMA) x 2.07 GHz = 1.26 TFLOP/s, the nominal 1.25 TFLOP/s of the part.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def kernel_flops_per_cell(k, op, geom):
+    """Floating-point operations of one cell in the fused apply kernel as
+    implemented (FMA = 2): tensor-product sweeps on the cell, the
+    neighbour's face-normal and in-face interpolation, the own-side face
+    traces and flux at every face point, the quadrature-point operation and
+    the injection of the face coefficients."""
+    k2, k3, k4 = k * k, k ** 3, k ** 4
+    if op == "sipg":
+        sweeps = 24 * k4                   # 12 sweeps (3 S, 3 D^co, 3 D^T, 3 S^T), k^4 FMA each
+        nb = 6 * 2 * (k3 + 4 * k3)        # 6 faces: D_f (k^3 FMA) + 2 fields x 2 in-face sweeps
+        flux = 6 * k2 * (2 * 6 * k + 20)  # own value + 3 gradients, 2 neighbour tangential, flux
+        qop = {"full": 39, "merged": 15, "cartesian": 8}[geom] + 48  # q-op + 24 FMA injection
+        return sweeps + nb + flux + qop * k3
+    sweeps = 18 * k4                       # 3 S, 3 D^T, 3 S^T
+    nb = 6 * 2 * (2 * k3)                  # value layer, 2 in-face sweeps
+    flux = 6 * k2 * (2 * k + 8)
+    qop = {"full": 24, "merged": 3, "cartesian": 3}[geom] + 3 + 12
+    return sweeps + nb + flux + qop * k3
+
+
+def bytes_per_dof(k, s, op, geom):
+    """Algorithmic bytes per dof of one apply: src read and dst write, the
+    cell geometry per point, the face geometry per face point (3 faces per
+    cell, k^2 points each) and the penalty per face."""
+    vec = 2 * s
+    if geom == "cartesian":
+        return vec
+    cell = {("sipg", "full"): 10, ("advection", "full"): 10, ("sipg", "merged"): 6,
+            ("advection", "merged"): 3}[(op, geom)] * s
+    face = (7 * s * 3 / k + 3 * s / k ** 3) if op == "sipg" else (1 * s * 3 / k)
+    return vec + cell + face
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        d["source"] = "measured"
+        return d
+    except Exception:
+        return dict(PEAKS_FALLBACK)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 50 ms in the background."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        return rows
+
+
+def summarize_clocks(rows, t0, t1):
+    import datetime
+    sel = []
+    for r in rows if isinstance(rows, list) else []:
+        try:
+            ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except Exception:
+            continue
+        if t0 - 0.05 <= ts <= t1 + 0.05:
+            sel.append(r)
+    if not sel:
+        sel = rows[-3:] if isinstance(rows, list) else []
+    if not sel:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+    sm = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
+    mx = [float(r[3]) for r in sel if r[3].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in sel for i in range(4) if r[6 + i].lower() == "active"})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(sel),
+            "power_w_max": max(float(r[4]) for r in sel if r[4].replace(".", "").isdigit()) if sel else None}
+
+
+def time_applies(torch, op, src, dst, steps, per_launch=True):
+    """Device time of `steps` applies on the operator's stream (CUDA events),
+    and the average duration of one apply launch from per-launch events."""
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for i in range(steps):
+        if per_launch:
+            evs[i][0].record(stream)
+        op.apply(src, dst)
+        if per_launch:
+            evs[i][1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    total_ms = start.elapsed_time(end)
+    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in evs])) if per_launch else total_ms / steps
+    return total_ms, launch_ms
+
+
+def cpu_baseline(workload, form, target_s=12.0):
+    """The FP64 oracle (cell-by-cell brute-force quadrature, OpenMP on the
+    host cores) on a seeded sample of cells of the same workload; DoFs/s =
+    sampled dofs / time."""
+    import oracle
+    mesh, p = workload["mesh"], workload["degree"]
+    n = oracle.n_dofs(mesh, p)
+    u = dg_inputs.src_vector(n, seed=1)
+    nc = oracle.n_cells(mesh)
+    batch = 64
+    done, t_used, seed = 0, 0.0, 0
+    while t_used < target_s and done < nc:
+        cells = dg_inputs.sample_cells(nc, batch, seed=1000 + seed)
+        t = time.perf_counter()
+        oracle.apply(mesh, p, form, u, cells=cells)
+        t_used += time.perf_counter() - t
+        done += len(cells)
+        seed += 1
+        batch = min(batch * 2, 4096)
+    k3 = (p + 1) ** 3
+    return {"value": done * k3 / t_used, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d sampled cells (%d dofs) of the same workload, %.1f s" % (done, done * k3, t_used)}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle as it stands, on the host cores,
+    each step a bounded sample of cells of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.lib()
+    wname = "deformed_dirichlet_32^3_p%d" % args.degree
+    w = dg_inputs.workload(wname)
+    mesh, p = w["mesh"], w["degree"]
+    form = dict(op="sipg", coeff=w["coeff"])
+    n = oracle.n_dofs(mesh, p)
+    u = dg_inputs.src_vector(n, seed=1)
+    nc = oracle.n_cells(mesh)
+    per_step = max(16, int(256 * (5.0 / (p + 1)) ** 6))
+    times = []
+    for i in range(args.warmup + args.steps):
+        cells = dg_inputs.sample_cells(nc, per_step, seed=5000 + i)
+        t = time.perf_counter()
+        oracle.apply(mesh, p, form, u, cells=cells)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+    k3 = (p + 1) ** 3
+    total = sum(times)
+    value = args.steps * per_step * k3 / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wname, "degree": p, "cells": nc, "dofs": n,
+                                            "sample_cells_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d seeded cells per step (%d dofs)" % (per_step, per_step * k3)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--degree", type=int, default=4)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1711_03590_gb300 as dgp
+    dgp.build()
+    dgp.load_library()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    wname = "deformed_dirichlet_32^3_p%d" % args.degree
+    w = dg_inputs.workload(wname)
+    mesh, p = w["mesh"], w["degree"]
+    k = p + 1
+    common = dict(periodic=mesh["periodic"], mapping=mesh["mapping"], amplitude=mesh["amplitude"])
+    peaks = load_peaks()
+
+    op = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64", coeff=w["coeff"], **common)
+    n = op.n_dofs
+    n_cells = op.info()["n_cells"]
+    src = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank), device="cuda")
+    dst = torch.empty_like(src)
+    for _ in range(args.warmup):
+        op.apply(src, dst)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t0 = time.time()
+    total_ms, launch_ms = time_applies(torch, op, src, dst, args.steps)
+    t1 = time.time()
+    if dist:
+        dist.barrier()
+    rows = sampler.stop()
+    clocks = summarize_clocks(rows, t0, t1)
+    torch.cuda.synchronize()
+    t_max = total_ms
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = world * n / (ms_per_step / 1e3)
+
+    # roofline of the apply kernel (the only kernel of a step)
+    flops = kernel_flops_per_cell(k, "sipg", w["geom"]) * n_cells
+    achieved_tf = flops / (launch_ms / 1e3) / 1e12
+    bpd = bytes_per_dof(k, 8, "sipg", w["geom"])
+    achieved_gbs = bpd * n / (launch_ms / 1e3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "apply_kernel<5,double,FULL,SIPG>", "flops_per_launch": flops,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved_gbs / peaks["hbm_gbs"], "bytes_per_dof": bpd,
+                        "peak_source": peaks.get("source")}}
+
+    # end to end through the C ABI with pinned host buffers
+    hsrc = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank)).pin_memory()
+    hdst = torch.empty_like(hsrc).pin_memory()
+    for _ in range(2):
+        op.apply_host(hsrc, hdst)
+    e2e_steps = max(3, min(args.steps, 50))
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        op.apply_host(hsrc, hdst)
+    te = time.perf_counter() - te
+    e2e = {"value": n / (te / e2e_steps), "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+           "call": "dg_apply_host"}
+    op.close()
+
+    extras = {}
+    if not args.no_extras:
+        # FP32 arithmetic, same workload
+        op32 = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp32", coeff=w["coeff"], **common)
+        s32, d32 = src.float(), torch.empty(n, dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            op32.apply(s32, d32)
+        tot32, l32 = time_applies(torch, op32, s32, d32, args.steps)
+        b32 = bytes_per_dof(k, 4, "sipg", w["geom"])
+        gbs = b32 * n / (l32 / 1e3) / 1e9
+        tf32 = kernel_flops_per_cell(k, "sipg", w["geom"]) * n_cells / (l32 / 1e3) / 1e12
+        extras["fp32"] = {"value": n / (tot32 / args.steps / 1e3), "unit": UNIT, "ms_per_step": tot32 / args.steps,
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                       "frac": gbs / peaks["hbm_gbs"], "bytes_per_dof": b32,
+                                       "alu_tflops": tf32, "alu_peak_tflops": FP32_PEAK_TFLOPS}}
+        op32.close()
+        # advection, FP64
+        opa = dgp.Operator(mesh["n"], p, geom=w["geom"], op="advection", prec="fp64", **common)
+        for _ in range(args.warmup):
+            opa.apply(src, dst)
+        tota, la = time_applies(torch, opa, src, dst, max(10, args.steps // 2))
+        extras["advection_fp64"] = {"value": n / (tota / max(10, args.steps // 2) / 1e3), "unit": UNIT}
+        opa.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, dict(op="sipg", coeff=w["coeff"]))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wname, "degree": p, "cells": n_cells,
+                           "dofs": n, "geometry": "full per-point Jacobians (G3)", "operator": "SIPG",
+                           "boundary": "Dirichlet", "coefficient": "1+0.5 sin(2 pi x)",
+                           "l2_policy": "inputs larger than L2 (vector + geometry > 500 MB)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clocks}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

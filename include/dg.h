@@ -1,0 +1,185 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) matrix-free discontinuous Galerkin
+ * operator library.
+ *
+ * The library evaluates y = A u (Kronbichler & Kormann, arXiv:1711.03590,
+ * Sec. 2, Eq. (matvec)) for two weak forms on hexahedral meshes of the unit
+ * cube with a tensor-product Lagrange basis on the k = p+1 Gauss-Lobatto
+ * points and k Gauss points per direction:
+ *   - the symmetric interior penalty Laplacian, Eq. (poisson_sip), with the
+ *     average/jump definitions and the Dirichlet mirror principle of Sec. 2;
+ *   - the upwind advection operator, Eq. (advection), with the boundary flux
+ *     |c.n| u- of Algorithm 1 step (iv)(c).
+ * Cell integrals use the sum-factorized basis change and collocation
+ * derivative of Eq. (tensor_to_collocation); face integrals interpolate both
+ * sides' traces as in Eq. (face_integral); the geometry is stored per
+ * quadrature point (variants G3/G4 of Sec. 5) or compressed (Cartesian).
+ *
+ * Degrees of freedom.  Cell c = ix + n0 (iy + n1 iz) owns the contiguous
+ * range [c k^3, (c+1) k^3); its dof (i0, i1, i2) sits at c k^3 + i0 +
+ * k (i1 + k i2) (x fastest), the Lagrange node at the Gauss-Lobatto points.
+ * Cell c maps the reference cube [0,1]^3 onto its box of the unit cube and,
+ * for mapping 1, shifts every coordinate by a sin(pi X) sin(pi Y) sin(pi Z).
+ *
+ * Conventions for every call:
+ *   - Device pointers are CUDA device addresses of the current device with
+ *     n_dofs contiguous scalars of the handle's precision (double for
+ *     DG_FP64, float for DG_FP32), 16-byte aligned.  The caller owns them.
+ *   - Calls are stream-ordered on the handle's stream and asynchronous,
+ *     unless stated otherwise.
+ *   - Errors are returned as dg_status codes, never by aborting; a message is
+ *     kept in the handle (dg_last_error).  DG_ERR_CUDA means a CUDA call
+ *     failed; the handle should then be destroyed.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef DG_GB300_H
+#define DG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,            /* invalid argument (null, size, aliasing, degree, geometry) */
+  DG_ERR_OOM = 2,            /* device or host allocation failed */
+  DG_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+  DG_ERR_UNSUPPORTED = 4,    /* valid but unsupported combination */
+  DG_ERR_NOT_CONVERGED = 5,  /* CG reached max_it; x holds the last iterate */
+  DG_ERR_BREAKDOWN = 6,      /* CG found p.Ap <= 0 or a non-finite scalar */
+  DG_ERR_TIMEOUT = 7         /* reserved for bounded device waits */
+} dg_status;
+
+typedef enum { DG_OP_SIPG = 0, DG_OP_ADVECTION = 1 } dg_op;
+
+/* Geometry storage (Sec. 5).
+ *  CARTESIAN: identity mapping only; constant J^{-1} and det J per mesh,
+ *             no per-point arrays (the kappa coefficient, when enabled, is a
+ *             table over x positions).
+ *  AFFINE:    reserved; dg_setup returns DG_ERR_UNSUPPORTED.
+ *  FULL_JAC:  variant G3: per cell quadrature point J^{-1} (9 values) and
+ *             det J * w (* kappa for SIPG) (1 value); per face quadrature
+ *             point and side n.J^{-T} (3 values each, Design Choice
+ *             "normal times inverse Jacobian") and kappa*da*w (1 value), and
+ *             one penalty per face.  Advection stores c.n da w (1 value) per
+ *             face point instead.
+ *  MERGED:    variant G4: per cell quadrature point the merged coefficient
+ *             kappa det J w J^{-1} J^{-T} (6 values, SIPG) or
+ *             -det J w J^{-1} c (3 values, advection); faces as FULL_JAC. */
+typedef enum {
+  DG_GEOM_CARTESIAN = 0,
+  DG_GEOM_AFFINE = 1,
+  DG_GEOM_FULL_JAC = 2,
+  DG_GEOM_MERGED = 3
+} dg_geom;
+
+typedef enum { DG_FP64 = 0, DG_FP32 = 1 } dg_prec;
+
+typedef struct {
+  int n[3];         /* cells per direction, each >= 1 */
+  int periodic;     /* 1: periodic in every direction; 0: Dirichlet (g = 0) on all of the boundary */
+  int mapping;      /* 0: identity; 1: x_i = X_i + amplitude sin(pi X) sin(pi Y) sin(pi Z) */
+  double amplitude; /* used by mapping 1; det J must stay positive */
+} dg_mesh;
+
+typedef struct {
+  int op;               /* dg_op */
+  int prec;             /* dg_prec: arithmetic and storage precision of apply */
+  double velocity[3];   /* advection speed c (constant vector) */
+  int coeff;            /* SIPG coefficient: 0 kappa = 1; 1 kappa = 1 + 0.5 sin(2 pi x_0) */
+  double penalty_scale; /* tau = penalty_scale (p+1)^2 max(A_F/|K-|, A_F/|K+|); <= 0 means 1 */
+} dg_opts;
+
+typedef struct dg_handle dg_handle;
+
+/* Static sizes of a set-up operator, for bandwidth accounting. */
+typedef struct {
+  int64_t n_dofs;
+  int64_t n_cells;
+  int degree;
+  int prec;
+  int geom;
+  int op;
+  int64_t cell_geometry_bytes;  /* per-quadrature-point cell arrays read by one apply */
+  int64_t face_geometry_bytes;  /* per-face arrays read by one apply */
+  int cells_per_block;          /* cells processed by one CUDA block of the apply kernel */
+  int threads_per_block;
+  int shared_bytes_per_block;
+  int64_t blocks;               /* blocks of one apply launch */
+} dg_info_t;
+
+/* Build an operator: 1D tables, geometry arrays and work buffers on the
+ * current CUDA device, computed in FP64 and stored in opts->prec.
+ *   mesh    mesh description (copied).
+ *   degree  polynomial degree p, 1..8.
+ *   geom    dg_geom storage variant.
+ *   opts    operator options (copied).
+ *   stream  cudaStream_t used by every later call (NULL = legacy default stream).
+ *   out     receives the handle; on error *out is NULL.
+ * Returns DG_ERR_ARG for invalid sizes, degree, geometry/mapping mismatch
+ * (CARTESIAN needs mapping 0) or a non-positive det J; DG_ERR_OOM if device
+ * memory runs out.  Blocks until set-up is complete.
+ * Cite: Sec. 5 (G3, G4, compressed Cartesian), Design Choice on j_n. */
+dg_status dg_setup(const dg_mesh *mesh, int degree, int geom, const dg_opts *opts, void *stream,
+                   dg_handle **out);
+
+/* Number of degrees of freedom n = n0 n1 n2 (p+1)^3.  Synchronous. */
+dg_status dg_n_dofs(const dg_handle *h, int64_t *n);
+
+/* Sizes of the operator's data (see dg_info_t).  Synchronous. */
+dg_status dg_info(const dg_handle *h, dg_info_t *info);
+
+/* Change the stream used by later calls. */
+dg_status dg_set_stream(dg_handle *h, void *stream);
+
+/* dst = A src on the device (Algorithm 1 steps (ii)-(iv); one kernel launch:
+ * each cell computes its cell integral and its six face integrals tested on
+ * itself and sets its dst entries).  src and dst: device pointers to n_dofs
+ * scalars of the handle's precision; src == dst, or overlapping ranges, give
+ * DG_ERR_ARG.  Asynchronous. */
+dg_status dg_apply(dg_handle *h, const void *src, void *dst);
+
+/* The same operator with HOST buffers: copies src to the device, applies,
+ * copies the result back, and waits for the stream.  Pinned host memory
+ * makes the copies asynchronous DMA.  Device staging buffers are allocated
+ * on the first call and kept by the handle. */
+dg_status dg_apply_host(dg_handle *h, const void *src_host, void *dst_host);
+
+/* rhs_i = (phi_i, f) for the manufactured solution u = sin(pi x) sin(pi y)
+ * sin(pi z) (Dirichlet g = 0), by the (k+2)-point Gauss rule per direction,
+ * in FP64 regardless of the handle's precision.
+ *   which_f 0: f = 3 pi^2 u (-Laplace u);  1: f = -div(kappa grad u) with
+ *   kappa = 1 + 0.5 sin(2 pi x_0).
+ * rhs: device pointer to n_dofs doubles.  Asynchronous. */
+dg_status dg_rhs(dg_handle *h, int which_f, double *rhs);
+
+/* Conjugate gradients for A x = rhs (SIPG only; DG_ERR_UNSUPPORTED for
+ * advection, which is not symmetric).  rhs, x: device pointers to n_dofs
+ * doubles; x holds the initial guess on entry and the last iterate on exit.
+ * Each iteration: one apply with p.Ap fused into the apply epilogue, then
+ * one fused vector update x += alpha p, r -= alpha Ap with r.r, then
+ * p = r + beta p.  All reductions are two-stage in a fixed order, so results
+ * are bitwise reproducible on a given device and size.  An FP32 handle
+ * returns DG_ERR_UNSUPPORTED.
+ * Stops when |r| <= rtol |rhs|.  Returns DG_ERR_NOT_CONVERGED after max_it
+ * iterations and DG_ERR_BREAKDOWN on p.Ap <= 0 or non-finite scalars.
+ * iters and final_rel_res (may be NULL) receive the count and |r|/|rhs|.
+ * Synchronous. */
+dg_status dg_cg_solve(dg_handle *h, const double *rhs, double *x, double rtol, int max_it, int *iters,
+                      double *final_rel_res);
+
+/* Free everything the handle owns.  NULL is accepted. */
+dg_status dg_destroy(dg_handle *h);
+
+/* Message of the last error on this handle ("" if none); for errors before a
+ * handle exists, dg_last_error(NULL) returns the last set-up message of the
+ * calling thread. */
+const char *dg_last_error(const dg_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_GB300_H */

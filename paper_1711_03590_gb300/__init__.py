@@ -1,0 +1,260 @@
+"""GB300 (sm_103a) matrix-free DG operators: Python binding of the C ABI.
+
+Thin ctypes marshalling over ``_build/libdg_gb300.so`` (declared in
+``include/dg.h``).  The functions keep the C names (``dg_setup``,
+``dg_apply``, ...); every step of an operator evaluation runs in the CUDA
+kernels of the library.  There is no CPU fallback: if the library is
+missing, importing the bindings raises ``DGLibraryMissing``; call
+``build()`` first (``__graft_entry__.build()`` does).
+
+PyTorch is used only to hand device memory and streams to the library:
+tensors must be CUDA, contiguous, of the handle's dtype (float64 for FP64,
+float32 for FP32) and hold n_dofs entries.
+
+Reference: Kronbichler & Kormann, arXiv:1711.03590 -- Sec. 2 (weak forms,
+Algorithm 1), Sec. 3.1 (sum factorization), Sec. 5 (geometry variants).
+"""
+import ctypes
+import os
+
+from .build import LIB, build  # noqa: F401
+
+DG_OK = 0
+DG_ERR_ARG = 1
+DG_ERR_OOM = 2
+DG_ERR_CUDA = 3
+DG_ERR_UNSUPPORTED = 4
+DG_ERR_NOT_CONVERGED = 5
+DG_ERR_BREAKDOWN = 6
+DG_ERR_TIMEOUT = 7
+STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_OOM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
+                5: "DG_ERR_NOT_CONVERGED", 6: "DG_ERR_BREAKDOWN", 7: "DG_ERR_TIMEOUT"}
+
+DG_OP_SIPG = 0
+DG_OP_ADVECTION = 1
+DG_GEOM_CARTESIAN = 0
+DG_GEOM_AFFINE = 1
+DG_GEOM_FULL_JAC = 2
+DG_GEOM_MERGED = 3
+DG_FP64 = 0
+DG_FP32 = 1
+
+GEOMS = {"cartesian": DG_GEOM_CARTESIAN, "affine": DG_GEOM_AFFINE, "full": DG_GEOM_FULL_JAC,
+         "merged": DG_GEOM_MERGED}
+OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
+PRECS = {"fp64": DG_FP64, "fp32": DG_FP32}
+
+EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
+            "dg_cg_solve", "dg_destroy", "dg_last_error"]
+
+
+class DGLibraryMissing(RuntimeError):
+    pass
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+
+
+class dg_mesh(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("periodic", ctypes.c_int), ("mapping", ctypes.c_int),
+                ("amplitude", ctypes.c_double)]
+
+
+class dg_opts(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("prec", ctypes.c_int), ("velocity", ctypes.c_double * 3),
+                ("coeff", ctypes.c_int), ("penalty_scale", ctypes.c_double)]
+
+
+class dg_info_t(ctypes.Structure):
+    _fields_ = [("n_dofs", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("degree", ctypes.c_int),
+                ("prec", ctypes.c_int), ("geom", ctypes.c_int), ("op", ctypes.c_int),
+                ("cell_geometry_bytes", ctypes.c_int64), ("face_geometry_bytes", ctypes.c_int64),
+                ("cells_per_block", ctypes.c_int), ("threads_per_block", ctypes.c_int),
+                ("shared_bytes_per_block", ctypes.c_int), ("blocks", ctypes.c_int64)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load_library(path=None):
+    """Load the CUDA library (raises DGLibraryMissing if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise DGLibraryMissing("CUDA library %s is missing; run paper_1711_03590_gb300.build()" % path)
+    L = ctypes.CDLL(path)
+    L.dg_setup.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int, ctypes.c_int, ctypes.POINTER(dg_opts), _vp,
+                           ctypes.POINTER(_vp)]
+    L.dg_n_dofs.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.dg_info.argtypes = [_vp, ctypes.POINTER(dg_info_t)]
+    L.dg_set_stream.argtypes = [_vp, _vp]
+    L.dg_apply.argtypes = [_vp, _vp, _vp]
+    L.dg_apply_host.argtypes = [_vp, _vp, _vp]
+    L.dg_rhs.argtypes = [_vp, ctypes.c_int, _vp]
+    L.dg_cg_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_double)]
+    L.dg_destroy.argtypes = [_vp]
+    L.dg_last_error.argtypes = [_vp]
+    L.dg_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        getattr(L, name).restype = ctypes.c_int if name != "dg_last_error" else ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status, handle):
+    if status != DG_OK:
+        msg = load_library().dg_last_error(handle)
+        raise DGError(status, msg.decode() if msg else "")
+    return status
+
+
+def make_mesh(n, periodic=False, mapping=0, amplitude=0.1):
+    if isinstance(n, int):
+        n = (n, n, n)
+    return dg_mesh((ctypes.c_int * 3)(*n), int(bool(periodic)), int(mapping), float(amplitude))
+
+
+def make_opts(op="sipg", prec="fp64", velocity=(1.0, 0.5, 0.25), coeff=0, penalty_scale=1.0):
+    return dg_opts(OPS.get(op, op), PRECS.get(prec, prec), (ctypes.c_double * 3)(*velocity), int(coeff),
+                   float(penalty_scale))
+
+
+# ---- C-ABI functions with the same names ---------------------------------
+
+def dg_setup(mesh, degree, geom, opts, stream=None):
+    """Returns the opaque handle (an int).  ``stream`` is a cudaStream_t value
+    (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
+    L = load_library()
+    h = _vp()
+    st = L.dg_setup(ctypes.byref(mesh), int(degree), GEOMS.get(geom, geom), ctypes.byref(opts),
+                    _vp(stream or 0), ctypes.byref(h))
+    _check(st, None)
+    return h.value
+
+
+def dg_n_dofs(handle):
+    n = ctypes.c_int64()
+    _check(load_library().dg_n_dofs(_vp(handle), ctypes.byref(n)), handle)
+    return n.value
+
+
+def dg_info(handle):
+    info = dg_info_t()
+    _check(load_library().dg_info(_vp(handle), ctypes.byref(info)), handle)
+    return {f: getattr(info, f) for f, _ in dg_info_t._fields_}
+
+
+def dg_set_stream(handle, stream):
+    _check(load_library().dg_set_stream(_vp(handle), _vp(stream or 0)), handle)
+
+
+def dg_apply(handle, src_ptr, dst_ptr):
+    _check(load_library().dg_apply(_vp(handle), _vp(src_ptr), _vp(dst_ptr)), handle)
+
+
+def dg_apply_host(handle, src_ptr, dst_ptr):
+    _check(load_library().dg_apply_host(_vp(handle), _vp(src_ptr), _vp(dst_ptr)), handle)
+
+
+def dg_rhs(handle, which_f, rhs_ptr):
+    _check(load_library().dg_rhs(_vp(handle), int(which_f), _vp(rhs_ptr)), handle)
+
+
+def dg_cg_solve(handle, rhs_ptr, x_ptr, rtol, max_it, raise_on_error=True):
+    """Returns (status, iterations, final relative residual)."""
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load_library().dg_cg_solve(_vp(handle), _vp(rhs_ptr), _vp(x_ptr), float(rtol), int(max_it),
+                                    ctypes.byref(it), ctypes.byref(rr))
+    if raise_on_error:
+        _check(st, handle)
+    return st, it.value, rr.value
+
+
+def dg_destroy(handle):
+    if handle:
+        load_library().dg_destroy(_vp(handle))
+
+
+def dg_last_error(handle=None):
+    msg = load_library().dg_last_error(_vp(handle or 0))
+    return msg.decode() if msg else ""
+
+
+# ---- convenience wrapper over torch tensors -------------------------------
+
+class Operator:
+    """One set-up DG operator on the current CUDA device.
+
+    Operator(n=32, degree=4, geom="full", op="sipg", prec="fp64",
+             periodic=False, mapping=1, amplitude=0.1, coeff=1)
+    """
+
+    def __init__(self, n, degree, geom="full", op="sipg", prec="fp64", periodic=False, mapping=0,
+                 amplitude=0.1, coeff=0, velocity=(1.0, 0.5, 0.25), penalty_scale=1.0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.mesh = make_mesh(n, periodic, mapping, amplitude)
+        self.opts = make_opts(op, prec, velocity, coeff, penalty_scale)
+        self.degree = degree
+        self.dtype = torch.float64 if PRECS.get(prec, prec) == DG_FP64 else torch.float32
+        self.handle = None
+        self.handle = dg_setup(self.mesh, degree, geom, self.opts, stream)
+        self.n_dofs = dg_n_dofs(self.handle)
+
+    def _check_tensor(self, t, dtype=None):
+        dtype = dtype or self.dtype
+        if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() != self.n_dofs:
+            raise ValueError("expected a contiguous CUDA %s tensor with %d entries" % (dtype, self.n_dofs))
+
+    def apply(self, src, dst=None):
+        import torch
+        self._check_tensor(src)
+        if dst is None:
+            dst = torch.empty_like(src)
+        self._check_tensor(dst)
+        dg_apply(self.handle, src.data_ptr(), dst.data_ptr())
+        return dst
+
+    def apply_host(self, src_host, dst_host):
+        if src_host.is_cuda or dst_host.is_cuda:
+            raise ValueError("apply_host takes CPU tensors")
+        dg_apply_host(self.handle, src_host.data_ptr(), dst_host.data_ptr())
+        return dst_host
+
+    def rhs(self, which=0):
+        import torch
+        out = torch.empty(self.n_dofs, dtype=torch.float64, device="cuda")
+        dg_rhs(self.handle, which, out.data_ptr())
+        return out
+
+    def cg(self, rhs, x=None, rtol=1e-10, max_it=5000, raise_on_error=True):
+        import torch
+        self._check_tensor(rhs, torch.float64)
+        if x is None:
+            x = torch.zeros_like(rhs)
+        self._check_tensor(x, torch.float64)
+        st, it, rr = dg_cg_solve(self.handle, rhs.data_ptr(), x.data_ptr(), rtol, max_it, raise_on_error)
+        return x, it, rr, st
+
+    def info(self):
+        return dg_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            dg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

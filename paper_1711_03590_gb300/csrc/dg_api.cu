@@ -1,0 +1,1028 @@
+// C-ABI entry points of the GB300 DG operator library (declared in
+// include/dg.h): operator set-up (1D tables, geometry), apply dispatch,
+// right-hand side, and the conjugate-gradient solver with fused vector
+// updates.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_internal.cuh"
+
+using dg::kMaxK;
+
+// ---------------------------------------------------------------------------
+// 1D tables.  Gauss points from the eigenvalues of the Legendre Jacobi matrix
+// (Golub-Welsch), interior Gauss-Lobatto points from the Jacobi matrix of the
+// Jacobi polynomials P^{(1,1)}_{k-2}; Lagrange values and derivatives by the
+// barycentric formulas.  (Sec. 2: tensor Gauss quadrature, nodal basis on
+// the Gauss-Lobatto points; Sec. 3.1: S, D^co, S_f, D_f.)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Eigen-decomposition of a symmetric tridiagonal matrix (diagonal a, off-diagonal
+// b) by cyclic Jacobi rotations on the dense matrix; returns eigenvalues and
+// the first component of each normalized eigenvector.
+void sym_tridiag_eig(int n, const double* a, const double* b, double* lam, double* v0) {
+  std::vector<double> A(n * n, 0.0), V(n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    A[i * n + i] = a[i];
+    V[i * n + i] = 1.0;
+    if (i + 1 < n) A[i * n + i + 1] = A[(i + 1) * n + i] = b[i];
+  }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+    if (off < 1e-34) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) {
+    lam[i] = A[i * n + i];
+    v0[i] = V[0 * n + i];
+  }
+  // sort ascending
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && lam[j - 1] > lam[j]; --j) {
+      std::swap(lam[j - 1], lam[j]);
+      std::swap(v0[j - 1], v0[j]);
+    }
+}
+
+// Polish a root of the Legendre-type polynomial given by its recurrence with
+// Newton steps in long double.  f(t) evaluates the polynomial and derivative.
+template <typename F>
+double polish(double t0, F f) {
+  long double t = t0;
+  for (int it = 0; it < 6; ++it) {
+    long double p, dp;
+    f(t, p, dp);
+    if (dp == 0) break;
+    t -= p / dp;
+  }
+  return (double)t;
+}
+
+// Legendre P_n and P_n' by the three-term recurrence (long double).
+void legendre_eval(int n, long double t, long double& p, long double& dp) {
+  long double p0 = 1.0L, p1 = t, d0 = 0.0L, d1 = 1.0L;
+  if (n == 0) { p = 1.0L; dp = 0.0L; return; }
+  for (int j = 2; j <= n; ++j) {
+    long double p2 = ((2 * j - 1) * t * p1 - (j - 1) * p0) / j;
+    long double d2 = d0 + (2 * j - 1) * p1;  // P'_j = P'_{j-2} + (2j-1) P_{j-1}
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  p = p1;
+  dp = d1;
+}
+
+void gauss_rule(int k, double* x, double* w) {
+  std::vector<double> a(k, 0.0), b(k, 0.0), lam(k), v0(k);
+  for (int j = 1; j < k; ++j) b[j - 1] = j / std::sqrt(4.0 * j * j - 1.0);
+  sym_tridiag_eig(k, a.data(), b.data(), lam.data(), v0.data());
+  for (int i = 0; i < k; ++i) {
+    double t = polish(lam[i], [k](long double tt, long double& p, long double& dp) { legendre_eval(k, tt, p, dp); });
+    long double p, dp;
+    legendre_eval(k, t, p, dp);
+    x[i] = 0.5 * (t + 1.0);
+    w[i] = (double)(1.0L / ((1.0L - (long double)t * t) * dp * dp));  // 2/((1-t^2)P'^2) on [-1,1], halved
+  }
+}
+
+void lobatto_nodes(int k, double* x) {
+  x[0] = 0.0;
+  x[k - 1] = 1.0;
+  int n = k - 2;
+  if (n <= 0) return;
+  std::vector<double> a(n, 0.0), b(n, 0.0), lam(n), v0(n);
+  for (int j = 1; j < n; ++j) b[j - 1] = std::sqrt((double)j * (j + 2) / ((2.0 * j + 1.0) * (2.0 * j + 3.0)));
+  sym_tridiag_eig(n, a.data(), b.data(), lam.data(), v0.data());
+  for (int i = 0; i < n; ++i) {
+    // interior GL nodes are the roots of P'_{k-1}; polish with P'' from Legendre's equation
+    double t = polish(lam[i], [k](long double tt, long double& p, long double& dp) {
+      long double q, dq;
+      legendre_eval(k - 1, tt, q, dq);
+      p = dq;
+      dp = (2.0L * tt * dq - (long double)(k - 1) * k * q) / (1.0L - tt * tt);
+    });
+    x[i + 1] = 0.5 * (t + 1.0);
+  }
+}
+
+void bary_weights(int k, const double* x, double* lam) {
+  for (int j = 0; j < k; ++j) {
+    double p = 1.0;
+    for (int m = 0; m < k; ++m)
+      if (m != j) p *= (x[j] - x[m]);
+    lam[j] = 1.0 / p;
+  }
+}
+
+// values l_j(t) of the Lagrange polynomials on nodes x (second barycentric form)
+void bary_values(int k, const double* x, const double* lam, double t, double* out) {
+  for (int j = 0; j < k; ++j)
+    if (t == x[j]) {
+      for (int m = 0; m < k; ++m) out[m] = (m == j) ? 1.0 : 0.0;
+      return;
+    }
+  double den = 0.0;
+  for (int j = 0; j < k; ++j) den += lam[j] / (t - x[j]);
+  for (int j = 0; j < k; ++j) out[j] = lam[j] / (t - x[j]) / den;
+}
+
+// differentiation matrix on the nodes: Dm[i][j] = l_j'(x_i)
+void bary_diff_matrix(int k, const double* x, const double* lam, double* Dm) {
+  for (int i = 0; i < k; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < k; ++j) {
+      if (j == i) continue;
+      double v = (lam[j] / lam[i]) / (x[i] - x[j]);
+      Dm[i * k + j] = v;
+      diag -= v;
+    }
+    Dm[i * k + i] = diag;
+  }
+}
+
+struct Tables64 {
+  double gq[kMaxK], gw[kMaxK], gl[kMaxK];
+  double S[kMaxK * kMaxK], D[kMaxK * kMaxK], E[2][kMaxK], DF[2][kMaxK];
+};
+
+void build_tables(int k, Tables64& t) {
+  gauss_rule(k, t.gq, t.gw);
+  lobatto_nodes(k, t.gl);
+  double lg[kMaxK], ll[kMaxK];
+  bary_weights(k, t.gq, lg);
+  bary_weights(k, t.gl, ll);
+  for (int q = 0; q < k; ++q) bary_values(k, t.gl, ll, t.gq[q], t.S + q * k);
+  bary_diff_matrix(k, t.gq, lg, t.D);
+  bary_values(k, t.gq, lg, 0.0, t.E[0]);
+  bary_values(k, t.gq, lg, 1.0, t.E[1]);
+  double DL[kMaxK * kMaxK];
+  bary_diff_matrix(k, t.gl, ll, DL);
+  for (int i = 0; i < k; ++i) {
+    t.DF[0][i] = DL[0 * k + i];
+    t.DF[1][i] = DL[(k - 1) * k + i];
+  }
+}
+
+template <typename T>
+dg::Tables<T> cast_tables(int k, const Tables64& t) {
+  dg::Tables<T> o;
+  memset(&o, 0, sizeof(o));
+  for (int i = 0; i < k * k; ++i) {
+    o.S[i] = (T)t.S[i];
+    o.D[i] = (T)t.D[i];
+  }
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < k; ++i) {
+      o.E[s][i] = (T)t.E[s][i];
+      o.DF[s][i] = (T)t.DF[s][i];
+    }
+  for (int i = 0; i < k; ++i) o.W[i] = (T)t.gw[i];
+  return o;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct dg_handle {
+  dg_mesh mesh;
+  dg_opts opts;
+  int degree, k, geom, prec, op;
+  int64_t n_cells, n_dofs;
+  cudaStream_t stream;
+  Tables64 t64;
+  dg::Tables<double> tabd;
+  dg::Tables<float> tabf;
+  dg::Geometry<double> geod;
+  dg::Geometry<float> geof;
+  void* cell_geo;         // device: per-quadrature-point cell arrays
+  void* face_geo[3];      // device: per-face-point arrays
+  void* face_tau[3];      // device: penalty per face
+  void* kappa_tab;        // device: Cartesian kappa tables
+  int64_t cell_bytes, face_bytes;
+  // CG work vectors (FP64) and reduction scratch
+  double *r, *p, *ap;
+  double* partial;        // per-block partials
+  int64_t partial_len;
+  double* scal;           // device scalars
+  double* scal_host;      // pinned host copy
+  // host-buffer apply staging
+  void *stage_src, *stage_dst;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+dg_status fail(dg_handle* h, dg_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_setup_error = msg;
+  return s;
+}
+
+dg_status cuda_fail(dg_handle* h, cudaError_t e, const char* what) {
+  return fail(h, DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DG_CUDA(h, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+dg_status dev_alloc(dg_handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return DG_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(h, DG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry set-up kernels (FP64 arithmetic, stored as T)
+// ---------------------------------------------------------------------------
+struct SetupParams {
+  int n[3];
+  int periodic;
+  int mapping;
+  double amp;
+  int k;
+  int P[3];
+  double gq[kMaxK], gw[kMaxK];
+  int op, coeff, geom;
+  double vel[3];
+  double penalty;  // penalty_scale (p+1)^2
+};
+
+// x = X + a s(X)(1,1,1), s = sin(pi X) sin(pi Y) sin(pi Z); J = dx/dxi includes 1/n_d
+__device__ void map_point(const SetupParams& S, const int ijk[3], const double xi[3], double x[3], double J[9]) {
+  double X[3];
+  for (int d = 0; d < 3; ++d) X[d] = (ijk[d] + xi[d]) / S.n[d];
+  double grad[3] = {0.0, 0.0, 0.0}, sv = 0.0;
+  if (S.mapping == 1) {
+    double sn[3], cs[3];
+    for (int d = 0; d < 3; ++d) sincospi(X[d], &sn[d], &cs[d]);
+    sv = sn[0] * sn[1] * sn[2];
+    grad[0] = M_PI * cs[0] * sn[1] * sn[2];
+    grad[1] = M_PI * sn[0] * cs[1] * sn[2];
+    grad[2] = M_PI * sn[0] * sn[1] * cs[2];
+  }
+  const double a = S.mapping == 1 ? S.amp : 0.0;
+  for (int i = 0; i < 3; ++i) {
+    x[i] = X[i] + a * sv;
+    for (int j = 0; j < 3; ++j) J[i * 3 + j] = ((i == j) + a * grad[j]) / S.n[j];
+  }
+}
+
+// inverse through the adjugate; returns det
+__device__ double invert3(const double J[9], double Ji[9]) {
+  const double c00 = J[4] * J[8] - J[5] * J[7], c01 = J[5] * J[6] - J[3] * J[8], c02 = J[3] * J[7] - J[4] * J[6];
+  const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+  const double r = 1.0 / det;
+  Ji[0] = c00 * r;
+  Ji[3] = c01 * r;
+  Ji[6] = c02 * r;
+  Ji[1] = (J[2] * J[7] - J[1] * J[8]) * r;
+  Ji[4] = (J[0] * J[8] - J[2] * J[6]) * r;
+  Ji[7] = (J[1] * J[6] - J[0] * J[7]) * r;
+  Ji[2] = (J[1] * J[5] - J[2] * J[4]) * r;
+  Ji[5] = (J[2] * J[3] - J[0] * J[5]) * r;
+  Ji[8] = (J[0] * J[4] - J[1] * J[3]) * r;
+  return det;
+}
+
+__device__ double kappa_of(const SetupParams& S, const double x[3]) {
+  return S.coeff == 1 ? 1.0 + 0.5 * sinpi(2.0 * x[0]) : 1.0;
+}
+
+__device__ void cell_of(const SetupParams& S, int64_t c, int ijk[3]) {
+  ijk[0] = (int)(c % S.n[0]);
+  ijk[1] = (int)((c / S.n[0]) % S.n[1]);
+  ijk[2] = (int)(c / ((int64_t)S.n[0] * S.n[1]));
+}
+
+template <typename T>
+__global__ void setup_cell_geometry(const SetupParams S, int64_t n_cells, T* out, int64_t ncq, double* vol_part,
+                                    int* bad) {
+  const int k = S.k, k3 = k * k * k;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_cells * k3;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / k3;
+    const int q = (int)(idx - c * k3);
+    const int q0 = q % k, q1 = (q / k) % k, q2 = q / (k * k);
+    int ijk[3];
+    cell_of(S, c, ijk);
+    const double xi[3] = {S.gq[q0], S.gq[q1], S.gq[q2]};
+    double x[3], J[9], Ji[9];
+    map_point(S, ijk, xi, x, J);
+    const double det = invert3(J, Ji);
+    if (!(det > 0.0)) atomicOr(bad, 1);
+    const double jxw = det * S.gw[q0] * S.gw[q1] * S.gw[q2];
+    vol_part[idx] = jxw;
+    if (!out) continue;
+    if (S.geom == dg::GEO_FULL) {
+      for (int m = 0; m < 9; ++m) out[m * ncq + idx] = (T)Ji[m];
+      out[9 * ncq + idx] = (T)(S.op == dg::OP_SIPG ? kappa_of(S, x) * jxw : jxw);
+    } else if (S.op == dg::OP_SIPG) {
+      const double kw = kappa_of(S, x) * jxw;
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+      for (int m = 0; m < 6; ++m) {
+        double g = 0.0;
+        for (int c2 = 0; c2 < 3; ++c2) g += Ji[ia[m] * 3 + c2] * Ji[ib[m] * 3 + c2];
+        out[m * ncq + idx] = (T)(kw * g);
+      }
+    } else {
+      for (int a = 0; a < 3; ++a)
+        out[a * ncq + idx] = (T)(-jxw * (Ji[a * 3 + 0] * S.vel[0] + Ji[a * 3 + 1] * S.vel[1] + Ji[a * 3 + 2] * S.vel[2]));
+    }
+  }
+}
+
+// per-cell volume from the per-point det J w values (fixed order)
+__global__ void sum_cells(const double* part, int k3, int64_t n_cells, double* vol) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < k3; ++q) s += part[c * k3 + q];
+    vol[c] = s;
+  }
+}
+
+// face (direction d) geometry: slot 0 = lower cell (its xi_d = 1), slot 1 = upper cell (xi_d = 0)
+template <typename T>
+__global__ void setup_face_geometry(const SetupParams S, int d, int64_t n_faces, T* out, int64_t nfq, double* daw_out,
+                                    int* bad) {
+  const int k = S.k, k2 = k * k;
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_faces * k2;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = idx / k2;
+    const int q = (int)(idx - f * k2);
+    const int qa = q % k, qb = q / k;
+    const int pos = (int)(f % S.P[d]);
+    const int64_t rest = f / S.P[d];
+    const int it1 = (int)(rest % S.n[t1]), it2 = (int)(rest / S.n[t1]);
+    bool has[2];
+    has[0] = S.periodic || pos >= 1;
+    has[1] = S.periodic || pos < S.n[d];
+    double jn[2][3] = {{0, 0, 0}, {0, 0, 0}}, nrm[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    double daw = 0.0, kap = 1.0;
+    bool first = true;
+    for (int slot = 0; slot < 2; ++slot) {
+      if (!has[slot]) continue;
+      int ijk[3];
+      ijk[t1] = it1;
+      ijk[t2] = it2;
+      ijk[d] = slot == 0 ? (pos - 1 + S.n[d]) % S.n[d] : pos % S.n[d];
+      double xi[3];
+      xi[d] = slot == 0 ? 1.0 : 0.0;
+      xi[t1] = S.gq[qa];
+      xi[t2] = S.gq[qb];
+      double x[3], J[9], Ji[9];
+      map_point(S, ijk, xi, x, J);
+      const double det = invert3(J, Ji);
+      if (!(det > 0.0)) atomicOr(bad, 1);
+      const double sg = slot == 0 ? 1.0 : -1.0;
+      double v[3], len = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        v[a] = sg * Ji[d * 3 + a];  // J^{-T} nhat
+        len += v[a] * v[a];
+      }
+      len = sqrt(len);
+      for (int a = 0; a < 3; ++a) nrm[slot][a] = v[a] / len;
+      for (int a = 0; a < 3; ++a)
+        jn[slot][a] = Ji[a * 3 + 0] * nrm[slot][0] + Ji[a * 3 + 1] * nrm[slot][1] + Ji[a * 3 + 2] * nrm[slot][2];
+      if (first) {
+        daw = det * len * S.gw[qa] * S.gw[qb];
+        kap = kappa_of(S, x);
+        first = false;
+      }
+    }
+    daw_out[idx] = daw;
+    if (S.op == dg::OP_SIPG) {
+      for (int slot = 0; slot < 2; ++slot)
+        for (int a = 0; a < 3; ++a) out[(slot * 3 + a) * nfq + idx] = (T)jn[slot][a];
+      out[6 * nfq + idx] = (T)(kap * daw);
+    } else {
+      // c.n da w with n the normal pointing to +d (outward normal of the lower side)
+      double n[3];
+      for (int a = 0; a < 3; ++a) n[a] = has[0] ? nrm[0][a] : -nrm[1][a];
+      out[idx] = (T)((S.vel[0] * n[0] + S.vel[1] * n[1] + S.vel[2] * n[2]) * daw);
+    }
+  }
+}
+
+template <typename T>
+__global__ void setup_face_tau(const SetupParams S, int d, int64_t n_faces, const double* daw, const double* vol,
+                               T* tau) {
+  const int k2 = S.k * S.k;
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n_faces; f += (int64_t)gridDim.x * blockDim.x) {
+    double A = 0.0;
+    for (int q = 0; q < k2; ++q) A += daw[f * k2 + q];
+    const int pos = (int)(f % S.P[d]);
+    const int64_t rest = f / S.P[d];
+    const int it1 = (int)(rest % S.n[t1]), it2 = (int)(rest / S.n[t1]);
+    double r = 0.0;
+    for (int slot = 0; slot < 2; ++slot) {
+      const bool has = slot == 0 ? (S.periodic || pos >= 1) : (S.periodic || pos < S.n[d]);
+      if (!has) continue;
+      int ijk[3];
+      ijk[t1] = it1;
+      ijk[t2] = it2;
+      ijk[d] = slot == 0 ? (pos - 1 + S.n[d]) % S.n[d] : pos % S.n[d];
+      const int64_t c = ijk[0] + (int64_t)S.n[0] * (ijk[1] + (int64_t)S.n[1] * ijk[2]);
+      r = fmax(r, A / vol[c]);
+    }
+    tau[f] = (T)(S.penalty * r);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side (phi_i, f), (k+2)-point Gauss rule, one block per cell
+// ---------------------------------------------------------------------------
+struct RhsParams {
+  SetupParams S;
+  int which;
+  int kq;
+  double xq[kMaxK + 2], wq[kMaxK + 2];
+  double phi[(kMaxK + 2) * kMaxK];  // phi[q*k + i] = l^GL_i(xq[q])
+};
+
+__global__ void rhs_kernel(const __grid_constant__ RhsParams R, int64_t n_cells, double* rhs) {
+  extern __shared__ double fq[];
+  const int k = R.S.k, kq = R.kq, nq = kq * kq * kq, k3 = k * k * k;
+  for (int64_t c = blockIdx.x; c < n_cells; c += gridDim.x) {
+    int ijk[3];
+    cell_of(R.S, c, ijk);
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      const int q0 = q % kq, q1 = (q / kq) % kq, q2 = q / (kq * kq);
+      const double xi[3] = {R.xq[q0], R.xq[q1], R.xq[q2]};
+      double x[3], J[9], Ji[9];
+      map_point(R.S, ijk, xi, x, J);
+      const double det = invert3(J, Ji);
+      double sx, cx, sy, sz, cy, cz;
+      sincospi(x[0], &sx, &cx);
+      sincospi(x[1], &sy, &cy);
+      sincospi(x[2], &sz, &cz);
+      const double u = sx * sy * sz;
+      double f = 3.0 * M_PI * M_PI * u;
+      if (R.which == 1) {
+        const double kap = 1.0 + 0.5 * sinpi(2.0 * x[0]);
+        const double dkap = M_PI * cospi(2.0 * x[0]);
+        f = 3.0 * M_PI * M_PI * kap * u - dkap * M_PI * cx * sy * sz;
+      }
+      fq[q] = f * det * R.wq[q0] * R.wq[q1] * R.wq[q2];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k3; i += blockDim.x) {
+      const int i0 = i % k, i1 = (i / k) % k, i2 = i / (k * k);
+      double s = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        const int q0 = q % kq, q1 = (q / kq) % kq, q2 = q / (kq * kq);
+        s += fq[q] * R.phi[q0 * k + i0] * R.phi[q1 * k + i1] * R.phi[q2 * k + i2];
+      }
+      rhs[c * k3 + i] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CG vector kernels.  Reductions: per-block partials in a fixed order, then a
+// single-block fixed-order pass, so every sum is reproducible bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1024;
+
+// device scalars: 0 rr, 1 bb, 2 pAp, 3 alpha, 4 beta, 5 rr_new, 6 breakdown flag
+enum { S_RR = 0, S_BB, S_PAP, S_ALPHA, S_BETA, S_RRNEW, S_FLAG, S_COUNT };
+
+__device__ void block_store_sum(double v, double* out) {
+  __shared__ double red[kRedThreads];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// r = b - ap, p = r; partials of r.r and b.b
+__global__ void cg_init(int64_t n, const double* b, const double* ap, double* r, double* p, double* part) {
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - ap[i];
+    r[i] = ri;
+    p[i] = ri;
+    rr += ri * ri;
+    bb += b[i] * b[i];
+  }
+  block_store_sum(rr, part + blockIdx.x);
+  block_store_sum(bb, part + kRedBlocks + blockIdx.x);
+}
+
+// single block: sum the first n partials of part (fixed order), call fn
+__device__ double reduce_partials(const double* part, int64_t n) {
+  __shared__ double red[kRedThreads];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kRedThreads) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void cg_scalars_init(const double* part, int64_t nparts, double* scal) {
+  const double rr = reduce_partials(part, nparts);
+  const double bb = reduce_partials(part + kRedBlocks, nparts);
+  if (threadIdx.x == 0) {
+    scal[S_RR] = rr;
+    scal[S_BB] = bb;
+    scal[S_FLAG] = 0.0;
+  }
+}
+
+__global__ void cg_scalars_alpha(const double* part, int64_t nparts, double* scal) {
+  const double pap = reduce_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    scal[S_PAP] = pap;
+    const double a = scal[S_RR] / pap;
+    if (!(pap > 0.0) || !isfinite(a)) {
+      scal[S_FLAG] = 1.0;
+      scal[S_ALPHA] = 0.0;
+    } else {
+      scal[S_ALPHA] = a;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha ap; partials of r.r
+__global__ void cg_update(int64_t n, const double* scal, double* x, double* r, const double* p, const double* ap,
+                          double* part) {
+  const double a = scal[S_ALPHA];
+  double rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, ap[i], r[i]);
+    r[i] = ri;
+    rr += ri * ri;
+  }
+  block_store_sum(rr, part + blockIdx.x);
+}
+
+__global__ void cg_scalars_beta(const double* part, int64_t nparts, double* scal) {
+  const double rr = reduce_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    scal[S_RRNEW] = rr;
+    const double b = rr / scal[S_RR];
+    scal[S_BETA] = isfinite(b) ? b : 0.0;
+    if (!isfinite(rr)) scal[S_FLAG] = 1.0;
+    scal[S_RR] = rr;
+  }
+}
+
+// p = r + beta p
+__global__ void cg_direction(int64_t n, const double* scal, const double* r, double* p) {
+  const double b = scal[S_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(b, p[i], r[i]);
+}
+
+int64_t apply_blocks(const dg_handle* h) {
+  const int C = dg::cells_per_block(h->k);
+  return (h->n_cells + C - 1) / C;
+}
+
+dg_status launch_apply(dg_handle* h, const void* src, void* dst, double* dot_partial) {
+  dg::ApplyLaunch L;
+  L.k = h->k;
+  L.prec = h->prec;
+  L.geo = h->geom == DG_GEOM_CARTESIAN ? dg::GEO_CART : h->geom == DG_GEOM_FULL_JAC ? dg::GEO_FULL : dg::GEO_MERGED;
+  L.op = h->op;
+  L.src = src;
+  L.dst = dst;
+  L.tables = h->prec == DG_FP64 ? (const void*)&h->tabd : (const void*)&h->tabf;
+  L.geometry = h->prec == DG_FP64 ? (const void*)&h->geod : (const void*)&h->geof;
+  L.dot_partial = dot_partial;
+  L.stream = h->stream;
+  cudaError_t e;
+  switch (h->k) {
+    case 2: e = dg::launch_apply_k2(L, h->n_cells); break;
+    case 3: e = dg::launch_apply_k3(L, h->n_cells); break;
+    case 4: e = dg::launch_apply_k4(L, h->n_cells); break;
+    case 5: e = dg::launch_apply_k5(L, h->n_cells); break;
+    case 6: e = dg::launch_apply_k6(L, h->n_cells); break;
+    case 7: e = dg::launch_apply_k7(L, h->n_cells); break;
+    case 8: e = dg::launch_apply_k8(L, h->n_cells); break;
+    case 9: e = dg::launch_apply_k9(L, h->n_cells); break;
+    default: return fail(h, DG_ERR_ARG, "degree out of range");
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "apply kernel launch");
+  return DG_OK;
+}
+
+template <typename T>
+void fill_geometry(dg_handle* h, dg::Geometry<T>& g) {
+  memset(&g, 0, sizeof(g));
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = h->mesh.n[d];
+    g.P[d] = h->mesh.periodic ? h->mesh.n[d] : h->mesh.n[d] + 1;
+  }
+  g.periodic = h->mesh.periodic;
+  g.n_cells = h->n_cells;
+  g.ncq = h->n_cells * h->k * h->k * h->k;
+  g.cell = static_cast<const T*>(h->cell_geo);
+  const int k2 = h->k * h->k;
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int64_t nf = (int64_t)g.P[d] * h->mesh.n[t1] * h->mesh.n[t2];
+    g.nfq[d] = nf * k2;
+    g.face[d] = static_cast<const T*>(h->face_geo[d]);
+    g.tau[d] = static_cast<const T*>(h->face_tau[d]);
+  }
+  const double ps = (h->opts.penalty_scale > 0 ? h->opts.penalty_scale : 1.0) * (h->k) * (h->k);
+  g.cart_detj = (T)(1.0 / ((double)h->mesh.n[0] * h->mesh.n[1] * h->mesh.n[2]));
+  for (int d = 0; d < 3; ++d) {
+    g.cart_jinv[d] = (T)h->mesh.n[d];
+    g.cart_tau[d] = (T)(ps * h->mesh.n[d]);
+    g.vel[d] = (T)h->opts.velocity[d];
+  }
+  if (h->kappa_tab) {
+    g.kq = static_cast<const T*>(h->kappa_tab);
+    g.kf = g.kq + (int64_t)h->mesh.n[0] * h->k;
+  }
+}
+
+template <typename T>
+dg_status setup_geometry(dg_handle* h) {
+  const int k = h->k, k2 = k * k, k3 = k2 * k;
+  const int64_t ncq = h->n_cells * k3;
+  SetupParams S;
+  memset(&S, 0, sizeof(S));
+  for (int d = 0; d < 3; ++d) {
+    S.n[d] = h->mesh.n[d];
+    S.P[d] = h->mesh.periodic ? h->mesh.n[d] : h->mesh.n[d] + 1;
+    S.vel[d] = h->opts.velocity[d];
+  }
+  S.periodic = h->mesh.periodic;
+  S.mapping = h->mesh.mapping;
+  S.amp = h->mesh.amplitude;
+  S.k = k;
+  for (int i = 0; i < k; ++i) {
+    S.gq[i] = h->t64.gq[i];
+    S.gw[i] = h->t64.gw[i];
+  }
+  S.op = h->op;
+  S.coeff = h->op == DG_OP_SIPG ? h->opts.coeff : 0;
+  S.geom = h->geom == DG_GEOM_FULL_JAC ? dg::GEO_FULL : h->geom == DG_GEOM_MERGED ? dg::GEO_MERGED : dg::GEO_CART;
+  S.penalty = (h->opts.penalty_scale > 0 ? h->opts.penalty_scale : 1.0) * k * k;
+
+  int* bad = nullptr;
+  double *part = nullptr, *vol = nullptr;
+  dg_status st;
+  if ((st = dev_alloc(h, (void**)&bad, sizeof(int))) != DG_OK) return st;
+  DG_CUDA(h, cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
+  if ((st = dev_alloc(h, (void**)&part, sizeof(double) * ncq)) != DG_OK) { cudaFree(bad); return st; }
+  if ((st = dev_alloc(h, (void**)&vol, sizeof(double) * h->n_cells)) != DG_OK) { cudaFree(bad); cudaFree(part); return st; }
+
+  const bool cart = h->geom == DG_GEOM_CARTESIAN;
+  int ncell_arrays = 0;
+  if (!cart) {
+    if (h->geom == DG_GEOM_FULL_JAC) ncell_arrays = 10;
+    else ncell_arrays = h->op == DG_OP_SIPG ? 6 : 3;
+  }
+  h->cell_bytes = (int64_t)ncell_arrays * ncq * sizeof(T);
+  st = dev_alloc(h, &h->cell_geo, (size_t)h->cell_bytes);
+  if (st == DG_OK) {
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((ncq + threads - 1) / threads, 152 * 64);
+    setup_cell_geometry<T><<<(unsigned)blocks, threads, 0, h->stream>>>(S, h->n_cells, static_cast<T*>(h->cell_geo),
+                                                                         ncq, part, bad);
+    sum_cells<<<(unsigned)std::min<int64_t>((h->n_cells + 255) / 256, 4096), 256, 0, h->stream>>>(part, k3, h->n_cells,
+                                                                                                 vol);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(h, e, "cell geometry kernel");
+  }
+  h->face_bytes = 0;
+  for (int d = 0; d < 3 && st == DG_OK && !cart; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int64_t nf = (int64_t)S.P[d] * h->mesh.n[t1] * h->mesh.n[t2];
+    const int64_t nfq = nf * k2;
+    const int nfa = h->op == DG_OP_SIPG ? 7 : 1;
+    double* daw = nullptr;
+    if ((st = dev_alloc(h, &h->face_geo[d], sizeof(T) * nfa * nfq)) != DG_OK) break;
+    if (h->op == DG_OP_SIPG && (st = dev_alloc(h, &h->face_tau[d], sizeof(T) * nf)) != DG_OK) break;
+    if ((st = dev_alloc(h, (void**)&daw, sizeof(double) * nfq)) != DG_OK) break;
+    h->face_bytes += (int64_t)sizeof(T) * nfa * nfq + (h->op == DG_OP_SIPG ? (int64_t)sizeof(T) * nf : 0);
+    const int threads = 256;
+    setup_face_geometry<T><<<(unsigned)std::min<int64_t>((nfq + threads - 1) / threads, 152 * 64), threads, 0,
+                             h->stream>>>(S, d, nf, static_cast<T*>(h->face_geo[d]), nfq, daw, bad);
+    if (h->op == DG_OP_SIPG)
+      setup_face_tau<T><<<(unsigned)std::min<int64_t>((nf + threads - 1) / threads, 4096), threads, 0, h->stream>>>(
+          S, d, nf, daw, vol, static_cast<T*>(h->face_tau[d]));
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaFree(daw);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "face geometry kernels");
+  }
+  if (st == DG_OK) {
+    int hbad = 0;
+    cudaError_t e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "geometry set-up");
+    else if (hbad) st = fail(h, DG_ERR_ARG, "mapping has a non-positive Jacobian determinant");
+  }
+  cudaFree(bad);
+  cudaFree(part);
+  cudaFree(vol);
+  return st;
+}
+
+// kappa tables for the Cartesian geometry: kappa at (ix + g_q)/n0 and at ix/n0
+template <typename T>
+dg_status setup_kappa_table(dg_handle* h) {
+  if (!(h->geom == DG_GEOM_CARTESIAN && h->op == DG_OP_SIPG && h->opts.coeff == 1)) return DG_OK;
+  const int n0 = h->mesh.n[0], k = h->k;
+  std::vector<T> tab((size_t)n0 * k + n0 + 1);
+  for (int i = 0; i < n0; ++i)
+    for (int q = 0; q < k; ++q) tab[(size_t)i * k + q] = (T)(1.0 + 0.5 * std::sin(2.0 * M_PI * (i + h->t64.gq[q]) / n0));
+  for (int i = 0; i <= n0; ++i) tab[(size_t)n0 * k + i] = (T)(1.0 + 0.5 * std::sin(2.0 * M_PI * i / n0));
+  dg_status st = dev_alloc(h, &h->kappa_tab, sizeof(T) * tab.size());
+  if (st != DG_OK) return st;
+  DG_CUDA(h, cudaMemcpy(h->kappa_tab, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+void free_handle(dg_handle* h) {
+  if (!h) return;
+  cudaFree(h->cell_geo);
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(h->face_geo[d]);
+    cudaFree(h->face_tau[d]);
+  }
+  cudaFree(h->kappa_tab);
+  cudaFree(h->r);
+  cudaFree(h->p);
+  cudaFree(h->ap);
+  cudaFree(h->partial);
+  cudaFree(h->scal);
+  if (h->scal_host) cudaFreeHost(h->scal_host);
+  cudaFree(h->stage_src);
+  cudaFree(h->stage_dst);
+  delete h;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opts, void* stream, dg_handle** out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !opts) return fail(nullptr, DG_ERR_ARG, "mesh or opts is NULL");
+  if (degree < 1 || degree > kMaxK - 1) return fail(nullptr, DG_ERR_ARG, "degree must be in 1..8");
+  for (int d = 0; d < 3; ++d)
+    if (mesh->n[d] < 1 || mesh->n[d] > (1 << 20)) return fail(nullptr, DG_ERR_ARG, "cells per direction must be >= 1");
+  if (mesh->mapping != 0 && mesh->mapping != 1) return fail(nullptr, DG_ERR_ARG, "mapping must be 0 or 1");
+  if (opts->op != DG_OP_SIPG && opts->op != DG_OP_ADVECTION) return fail(nullptr, DG_ERR_ARG, "unknown operator");
+  if (opts->prec != DG_FP64 && opts->prec != DG_FP32) return fail(nullptr, DG_ERR_ARG, "unknown precision");
+  if (opts->coeff != 0 && opts->coeff != 1) return fail(nullptr, DG_ERR_ARG, "coeff must be 0 or 1");
+  if (geom == DG_GEOM_AFFINE) return fail(nullptr, DG_ERR_UNSUPPORTED, "affine geometry storage is not implemented");
+  if (geom != DG_GEOM_CARTESIAN && geom != DG_GEOM_FULL_JAC && geom != DG_GEOM_MERGED)
+    return fail(nullptr, DG_ERR_ARG, "unknown geometry variant");
+  if (geom == DG_GEOM_CARTESIAN && mesh->mapping != 0)
+    return fail(nullptr, DG_ERR_ARG, "Cartesian geometry needs the identity mapping");
+  const int64_t nc = (int64_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
+  const int k = degree + 1;
+  if (nc * k * k * k > (int64_t)1 << 40) return fail(nullptr, DG_ERR_ARG, "mesh too large");
+
+  dg_handle* h = new (std::nothrow) dg_handle();
+  if (!h) return fail(nullptr, DG_ERR_OOM, "host allocation failed");
+  h->mesh = *mesh;
+  h->opts = *opts;
+  h->degree = degree;
+  h->k = k;
+  h->geom = geom;
+  h->prec = opts->prec;
+  h->op = opts->op;
+  h->n_cells = nc;
+  h->n_dofs = nc * k * k * k;
+  h->stream = static_cast<cudaStream_t>(stream);
+  build_tables(k, h->t64);
+  h->tabd = cast_tables<double>(k, h->t64);
+  h->tabf = cast_tables<float>(k, h->t64);
+
+  dg_status st = h->prec == DG_FP64 ? setup_geometry<double>(h) : setup_geometry<float>(h);
+  if (st == DG_OK) st = h->prec == DG_FP64 ? setup_kappa_table<double>(h) : setup_kappa_table<float>(h);
+  if (st != DG_OK) {
+    g_setup_error = h->err;
+    free_handle(h);
+    return st;
+  }
+  fill_geometry<double>(h, h->geod);
+  fill_geometry<float>(h, h->geof);
+  *out = h;
+  return DG_OK;
+}
+
+dg_status dg_n_dofs(const dg_handle* h, int64_t* n) {
+  if (!h || !n) return DG_ERR_ARG;
+  *n = h->n_dofs;
+  return DG_OK;
+}
+
+dg_status dg_info(const dg_handle* h, dg_info_t* info) {
+  if (!h || !info) return DG_ERR_ARG;
+  info->n_dofs = h->n_dofs;
+  info->n_cells = h->n_cells;
+  info->degree = h->degree;
+  info->prec = h->prec;
+  info->geom = h->geom;
+  info->op = h->op;
+  info->cell_geometry_bytes = h->cell_bytes;
+  info->face_geometry_bytes = h->face_bytes;
+  info->cells_per_block = dg::cells_per_block(h->k);
+  info->threads_per_block = info->cells_per_block * h->k * h->k;
+  info->shared_bytes_per_block = dg::smem_scalars_per_cell(h->k, h->op) * info->cells_per_block *
+                                 (h->prec == DG_FP64 ? 8 : 4);
+  info->blocks = apply_blocks(h);
+  return DG_OK;
+}
+
+dg_status dg_set_stream(dg_handle* h, void* stream) {
+  if (!h) return DG_ERR_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return DG_OK;
+}
+
+dg_status dg_apply(dg_handle* h, const void* src, void* dst) {
+  if (!h) return DG_ERR_ARG;
+  if (!src || !dst) return fail(h, DG_ERR_ARG, "src or dst is NULL");
+  const int64_t bytes = h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  const char* a = static_cast<const char*>(src);
+  const char* b = static_cast<const char*>(dst);
+  if (a < b + bytes && b < a + bytes) return fail(h, DG_ERR_ARG, "src and dst overlap");
+  if ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15)
+    return fail(h, DG_ERR_ARG, "src and dst must be 16-byte aligned");
+  return launch_apply(h, src, dst, nullptr);
+}
+
+dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
+  if (!h) return DG_ERR_ARG;
+  if (!src_host || !dst_host) return fail(h, DG_ERR_ARG, "src or dst is NULL");
+  const size_t bytes = (size_t)h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  dg_status st;
+  if (!h->stage_src && (st = dev_alloc(h, &h->stage_src, bytes)) != DG_OK) return st;
+  if (!h->stage_dst && (st = dev_alloc(h, &h->stage_dst, bytes)) != DG_OK) return st;
+  DG_CUDA(h, cudaMemcpyAsync(h->stage_src, src_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  if ((st = launch_apply(h, h->stage_src, h->stage_dst, nullptr)) != DG_OK) return st;
+  DG_CUDA(h, cudaMemcpyAsync(dst_host, h->stage_dst, bytes, cudaMemcpyDeviceToHost, h->stream));
+  DG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+dg_status dg_rhs(dg_handle* h, int which_f, double* rhs) {
+  if (!h) return DG_ERR_ARG;
+  if (!rhs) return fail(h, DG_ERR_ARG, "rhs is NULL");
+  if (which_f != 0 && which_f != 1) return fail(h, DG_ERR_ARG, "which_f must be 0 or 1");
+  RhsParams R;
+  memset(&R, 0, sizeof(R));
+  for (int d = 0; d < 3; ++d) R.S.n[d] = h->mesh.n[d];
+  R.S.periodic = h->mesh.periodic;
+  R.S.mapping = h->mesh.mapping;
+  R.S.amp = h->mesh.amplitude;
+  R.S.k = h->k;
+  R.which = which_f;
+  R.kq = h->k + 2;
+  double xq[kMaxK + 2], wq[kMaxK + 2], lam[kMaxK];
+  gauss_rule(R.kq, xq, wq);
+  bary_weights(h->k, h->t64.gl, lam);
+  for (int q = 0; q < R.kq; ++q) {
+    R.xq[q] = xq[q];
+    R.wq[q] = wq[q];
+    bary_values(h->k, h->t64.gl, lam, xq[q], R.phi + q * h->k);
+  }
+  const int nq = R.kq * R.kq * R.kq;
+  rhs_kernel<<<(unsigned)std::min<int64_t>(h->n_cells, 152 * 16), 128, sizeof(double) * nq, h->stream>>>(R, h->n_cells,
+                                                                                                         rhs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "rhs kernel");
+  return DG_OK;
+}
+
+dg_status dg_cg_solve(dg_handle* h, const double* rhs, double* x, double rtol, int max_it, int* iters,
+                      double* final_rel_res) {
+  if (!h) return DG_ERR_ARG;
+  if (h->op != DG_OP_SIPG) return fail(h, DG_ERR_UNSUPPORTED, "CG needs the symmetric SIPG operator");
+  if (h->prec != DG_FP64) return fail(h, DG_ERR_UNSUPPORTED, "CG runs on FP64 handles");
+  if (!rhs || !x) return fail(h, DG_ERR_ARG, "rhs or x is NULL");
+  if (!(rtol > 0.0) || max_it < 0) return fail(h, DG_ERR_ARG, "rtol must be > 0 and max_it >= 0");
+  const int64_t n = h->n_dofs;
+  dg_status st;
+  const int64_t nblk = apply_blocks(h);
+  if (!h->r) {
+    if ((st = dev_alloc(h, (void**)&h->r, sizeof(double) * n)) != DG_OK) return st;
+    if ((st = dev_alloc(h, (void**)&h->p, sizeof(double) * n)) != DG_OK) return st;
+    if ((st = dev_alloc(h, (void**)&h->ap, sizeof(double) * n)) != DG_OK) return st;
+    h->partial_len = 2 * kRedBlocks + nblk;  // [vector partials | apply partials]
+    if ((st = dev_alloc(h, (void**)&h->partial, sizeof(double) * h->partial_len)) != DG_OK) return st;
+    if ((st = dev_alloc(h, (void**)&h->scal, sizeof(double) * S_COUNT)) != DG_OK) return st;
+    DG_CUDA(h, cudaMallocHost((void**)&h->scal_host, sizeof(double) * S_COUNT));
+  }
+  cudaStream_t s = h->stream;
+  const int vb = (int)std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads);
+  double* part_vec = h->partial;
+  double* part_apply = h->partial + 2 * kRedBlocks;
+  if ((st = launch_apply(h, x, h->ap, nullptr)) != DG_OK) return st;
+  cg_init<<<vb, kRedThreads, 0, s>>>(n, rhs, h->ap, h->r, h->p, part_vec);
+  cg_scalars_init<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
+  DG_CUDA(h, cudaGetLastError());
+  DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  DG_CUDA(h, cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(h->scal_host[S_BB] > 0 ? h->scal_host[S_BB] : 1.0);
+  double rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
+  int it = 0;
+  st = DG_OK;
+  while (rel > rtol) {
+    if (it >= max_it) {
+      st = fail(h, DG_ERR_NOT_CONVERGED, "CG reached max_it");
+      break;
+    }
+    // p.Ap is fused into the apply epilogue (per-block partials)
+    if ((st = launch_apply(h, h->p, h->ap, part_apply)) != DG_OK) return st;
+    cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply, nblk, h->scal);
+    cg_update<<<vb, kRedThreads, 0, s>>>(n, h->scal, x, h->r, h->p, h->ap, part_vec);
+    cg_scalars_beta<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
+    cg_direction<<<vb, kRedThreads, 0, s>>>(n, h->scal, h->r, h->p);
+    DG_CUDA(h, cudaGetLastError());
+    DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+    DG_CUDA(h, cudaStreamSynchronize(s));
+    ++it;
+    if (h->scal_host[S_FLAG] != 0.0) {
+      st = fail(h, DG_ERR_BREAKDOWN, "CG breakdown: p.Ap <= 0 or non-finite scalar");
+      break;
+    }
+    rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
+  }
+  if (iters) *iters = it;
+  if (final_rel_res) *final_rel_res = rel;
+  return st;
+}
+
+dg_status dg_destroy(dg_handle* h) {
+  if (!h) return DG_OK;
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+  return DG_OK;
+}
+
+const char* dg_last_error(const dg_handle* h) {
+  if (!h) return g_setup_error.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

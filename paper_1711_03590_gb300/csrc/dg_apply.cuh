@@ -1,0 +1,499 @@
+// Fused element-centric DG apply kernel (one launch per operator evaluation).
+//
+// Each CUDA block owns C consecutive cells (C k^2 threads, thread (a,b) of a
+// cell owns one line of k points in whichever direction a phase sweeps).
+// For every cell the block computes, in shared memory:
+//   1. gather the cell's k^3 contiguous dofs (Algorithm 1 step (ii)(a));
+//   2. basis change S (x) S (x) S to the Gauss points and the collocation
+//      derivative D^co along x, y, z (Eq. tensor_to_collocation);
+//   3. for the six faces: the own traces by extrapolating the Gauss-point
+//      fields to xi = 0 / 1, the neighbour's traces from its Gauss-Lobatto
+//      dofs through S_f / D_f and the in-face S (x) S and D^co steps of
+//      Eq. (face_integral), the numerical flux of Eq. (poisson_sip) or
+//      Eq. (advection) at each face point (Algorithm 1 step (iii)(c)), and
+//      the test coefficients of this cell's side;
+//   4. the quadrature-point operation with the stored geometry (Sec. 5: G3
+//      J^{-1} and det J w, G4 merged coefficient, or Cartesian constants) and
+//      the injection of the face test coefficients into the Gauss-point fields;
+//   5. the transposed derivative and basis change (integration), and a set
+//      (not add) of the cell's dst entries (the remark after Algorithm 1).
+// Every face is thus evaluated once from each side; each cell's result is
+// written exactly once, with no atomics and a fixed summation order.
+#pragma once
+
+#include "dg_internal.cuh"
+
+namespace dg {
+
+template <typename T>
+struct ApplyParams {
+  Tables<T> tab;
+  Geometry<T> geo;
+  const T* src;
+  T* dst;
+  double* dot_partial;
+};
+
+template <int K>
+struct Shape {
+  static constexpr int C = cells_per_block(K);
+  static constexpr int threads = C * K * K;
+};
+
+template <int K, int OP>
+struct Smem {
+  static constexpr int NF = OP == OP_SIPG ? 2 : 1;   // neighbour trace fields per face
+  static constexpr int FTF = OP == OP_SIPG ? 4 : 1;  // face test fields per face
+  static constexpr int per_cell = smem_scalars_per_cell(K, OP);
+};
+
+// v[base + q stride] = sum_i M[q][i] v[base + i stride]   (TR: M[i][q])
+template <int K, bool TR, typename T>
+__device__ __forceinline__ void line_apply(const T* __restrict__ M, T* v, int base, int stride) {
+  T in[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) in[i] = v[base + i * stride];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < K; ++i) s = fma(TR ? M[i * K + q] : M[q * K + i], in[i], s);
+    v[base + q * stride] = s;
+  }
+}
+
+// out[base + q stride] = sum_i M[q][i] in[base + i stride]
+template <int K, typename T>
+__device__ __forceinline__ void line_apply_to(const T* __restrict__ M, const T* in, T* out, int base, int stride) {
+  T x[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) x[i] = in[base + i * stride];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < K; ++i) s = fma(M[q * K + i], x[i], s);
+    out[base + q * stride] = s;
+  }
+}
+
+// v[base + j stride] += sum_q M[q][j] t[base + q stride]
+template <int K, typename T>
+__device__ __forceinline__ void line_add_transposed(const T* __restrict__ M, const T* t, T* v, int base,
+                                                    int stride) {
+  T x[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) x[q] = t[base + q * stride];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    T s = v[base + j * stride];
+#pragma unroll
+    for (int q = 0; q < K; ++q) s = fma(M[q * K + j], x[q], s);
+    v[base + j * stride] = s;
+  }
+}
+
+// start of the line along direction d through tangential indices (a, b)
+template <int K>
+__device__ __forceinline__ int line_base(int d, int a, int b) {
+  return d == 0 ? K * (a + K * b) : d == 1 ? a + K * K * b : a + K * b;
+}
+
+template <int K, typename T, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_constant__ ApplyParams<T> P) {
+  constexpr int K2 = K * K, K3 = K2 * K, C = Shape<K>::C;
+  constexpr int NF = Smem<K, OP>::NF, FTF = Smem<K, OP>::FTF;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3] u -> u at Gauss points -> test value field
+  T* G = U + C * K3;                      // [3][C][K3] gradients -> test gradient fields
+  T* NBa = G + 3 * C * K3;                // [C][2][NF][K2] neighbour traces
+  T* NBb = NBa + C * 2 * NF * K2;         // [C][2][NF][K2]
+  T* FT = NBb + C * 2 * NF * K2;          // [C][3][2][FTF][K2] face test coefficients
+
+  const Tables<T>& tb = P.tab;
+  const Geometry<T>& gm = P.geo;
+  const int tid = threadIdx.x;
+  const int lc = tid / K2;
+  const int ln = tid - lc * K2;
+  const int la = ln % K, lb = ln / K;
+  const int64_t cell0 = (int64_t)blockIdx.x * C;
+  const int64_t cell = cell0 + lc;
+  const bool active = cell < gm.n_cells;
+  const int nloc = (int)min((int64_t)C, gm.n_cells - cell0);
+  T* Uc = U + lc * K3;
+  T* G0 = G + lc * K3;
+  T* G1 = G + (C + lc) * K3;
+  T* G2 = G + (2 * C + lc) * K3;
+
+  int ijk[3];
+  {
+    const int64_t c = active ? cell : cell0;
+    ijk[0] = (int)(c % gm.n[0]);
+    ijk[1] = (int)((c / gm.n[0]) % gm.n[1]);
+    ijk[2] = (int)(c / ((int64_t)gm.n[0] * gm.n[1]));
+  }
+
+  // 1. gather (coalesced over the block's contiguous range)
+  {
+    const T* s = P.src + cell0 * K3;
+    for (int i = tid; i < nloc * K3; i += blockDim.x) U[i] = s[i];
+  }
+  __syncthreads();
+
+  // 2. basis change to the Gauss points, x then y then z
+  if (active) line_apply<K, false>(tb.S, Uc, K * (la + K * lb), 1);
+  __syncthreads();
+  if (active) line_apply<K, false>(tb.S, Uc, la + K2 * lb, K);
+  __syncthreads();
+  if (active) line_apply<K, false>(tb.S, Uc, la + K * lb, K2);
+  __syncthreads();
+  if (OP == OP_SIPG) {
+    if (active) {
+      line_apply_to<K>(tb.D, Uc, G0, K * (la + K * lb), 1);
+      line_apply_to<K>(tb.D, Uc, G1, la + K2 * lb, K);
+      line_apply_to<K>(tb.D, Uc, G2, la + K * lb, K2);
+    }
+    __syncthreads();
+  }
+
+  // 3. faces, one direction at a time
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int strd = d == 0 ? 1 : d == 1 ? K : K2;
+    int64_t nbc[2];
+    int64_t fid[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      int j[3] = {ijk[0], ijk[1], ijk[2]};
+      j[d] += s ? 1 : -1;
+      int pos = ijk[d] + s;
+      bool inside = j[d] >= 0 && j[d] < gm.n[d];
+      if (!inside && gm.periodic) {
+        j[d] = (j[d] + gm.n[d]) % gm.n[d];
+        inside = true;
+      }
+      if (gm.periodic) pos = pos % gm.n[d];
+      nbc[s] = inside ? j[0] + (int64_t)gm.n[0] * (j[1] + (int64_t)gm.n[1] * j[2]) : -1;
+      fid[s] = pos + (int64_t)gm.P[d] * (ijk[t1] + (int64_t)gm.n[t1] * ijk[t2]);
+    }
+    // 3a. neighbour's face-normal interpolation from its Gauss-Lobatto dofs:
+    // the value is the layer on the shared face, the normal derivative uses D_f
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (nbc[s] < 0) continue;
+        const T* un = P.src + nbc[s] * K3 + line_base<K>(d, la, lb);
+        T v[K];
+#pragma unroll
+        for (int l = 0; l < K; ++l) v[l] = un[l * strd];
+        T* nb = NBa + (lc * 2 + s) * NF * K2;
+        nb[ln] = s ? v[0] : v[K - 1];
+        if (OP == OP_SIPG) {
+          T dv = T(0);
+#pragma unroll
+          for (int l = 0; l < K; ++l) dv = fma(tb.DF[1 - s][l], v[l], dv);
+          nb[K2 + ln] = dv;
+        }
+      }
+    }
+    __syncthreads();
+    // 3b. in-face basis change along t1 then t2
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (nbc[s] < 0) continue;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const T* in = NBa + ((lc * 2 + s) * NF + f) * K2;
+          T acc = T(0);
+#pragma unroll
+          for (int i = 0; i < K; ++i) acc = fma(tb.S[la * K + i], in[i + K * lb], acc);
+          NBb[((lc * 2 + s) * NF + f) * K2 + ln] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (nbc[s] < 0) continue;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const T* in = NBb + ((lc * 2 + s) * NF + f) * K2;
+          T acc = T(0);
+#pragma unroll
+          for (int j = 0; j < K; ++j) acc = fma(tb.S[lb * K + j], in[la + K * j], acc);
+          NBa[((lc * 2 + s) * NF + f) * K2 + ln] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    // 3c. numerical flux at face point (la, lb) of both faces of direction d
+    if (active) {
+      const int base = line_base<K>(d, la, lb);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const bool interior = nbc[s] >= 0;
+        const T sg = s ? T(1) : T(-1);
+        T u = T(0);
+#pragma unroll
+        for (int j = 0; j < K; ++j) u = fma(tb.E[s][j], Uc[base + j * strd], u);
+        const T* nbt = NBa + (lc * 2 + s) * NF * K2;
+        const T un = interior ? nbt[ln] : T(0);
+        T* ft = FT + (((lc * 3 + d) * 2 + s) * FTF) * K2 + ln;
+        if (OP == OP_SIPG) {
+          T g[3] = {T(0), T(0), T(0)};
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            const T e = tb.E[s][j];
+            g[0] = fma(e, G0[base + j * strd], g[0]);
+            g[1] = fma(e, G1[base + j * strd], g[1]);
+            g[2] = fma(e, G2[base + j * strd], g[2]);
+          }
+          T gn[3] = {T(0), T(0), T(0)};
+          if (interior) {
+            T a1 = T(0), a2 = T(0);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+              a1 = fma(tb.D[la * K + i], nbt[i + K * lb], a1);
+              a2 = fma(tb.D[lb * K + i], nbt[la + K * i], a2);
+            }
+            gn[d] = nbt[K2 + ln];
+            gn[t1] = a1;
+            gn[t2] = a2;
+          }
+          T jo[3], dno, dnn, fjxw, tau;
+          if (GEO == GEO_CART) {
+            const T jn = sg * gm.cart_jinv[d];
+            jo[0] = jo[1] = jo[2] = T(0);
+            jo[d] = jn;
+            dno = jn * g[d];
+            dnn = jn * gn[d];
+            T kap = T(1);
+            if (gm.kq) kap = d == 0 ? gm.kf[ijk[0] + s] : gm.kq[ijk[0] * K + la];
+            fjxw = kap * tb.W[la] * tb.W[lb] * gm.cart_detj * gm.cart_jinv[d];
+            tau = gm.cart_tau[d];
+          } else {
+            const int64_t nfq = gm.nfq[d];
+            const T* fp = gm.face[d] + fid[s] * K2 + ln;
+            const int so = 1 - s;  // own slot: lower side of the face is slot 0
+            jo[0] = fp[(so * 3 + 0) * nfq];
+            jo[1] = fp[(so * 3 + 1) * nfq];
+            jo[2] = fp[(so * 3 + 2) * nfq];
+            dno = jo[0] * g[0] + jo[1] * g[1] + jo[2] * g[2];
+            if (interior) {
+              const T jn0 = fp[(s * 3 + 0) * nfq], jn1 = fp[(s * 3 + 1) * nfq], jn2 = fp[(s * 3 + 2) * nfq];
+              dnn = -(jn0 * gn[0] + jn1 * gn[1] + jn2 * gn[2]);
+            } else {
+              dnn = T(0);
+            }
+            fjxw = fp[6 * nfq];
+            tau = gm.tau[d][fid[s]];
+          }
+          T tv, tg;
+          if (interior) {
+            const T jump = u - un;
+            tv = fjxw * (tau * jump - T(0.5) * (dno + dnn));
+            tg = T(-0.5) * fjxw * jump;
+          } else {
+            tv = fjxw * (T(2) * tau * u - dno);
+            tg = -fjxw * u;
+          }
+          ft[0] = tv;
+          ft[K2] = tg * jo[0];
+          ft[2 * K2] = tg * jo[1];
+          ft[3 * K2] = tg * jo[2];
+        } else {
+          T cn;
+          if (GEO == GEO_CART) {
+            cn = gm.vel[d] * tb.W[la] * tb.W[lb] * gm.cart_detj * gm.cart_jinv[d];
+          } else {
+            cn = gm.face[d][fid[s] * K2 + ln];
+          }
+          const T cno = s ? cn : -cn;  // c.n da w with n the own outward normal
+          ft[0] = interior ? T(0.5) * cno * (u + un) + T(0.5) * fabs(cno) * (u - un) : fabs(cno) * u;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // 4. quadrature-point operation and injection of the face test coefficients
+  if (active) {
+#pragma unroll 1
+    for (int z = 0; z < K; ++z) {
+      const int pt = la + K * (lb + K * z);
+      T fv = T(0), fg0 = T(0), fg1 = T(0), fg2 = T(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int along = d == 0 ? la : d == 1 ? lb : z;
+        const int proj = d == 0 ? lb + K * z : d == 1 ? la + K * z : la + K * lb;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const T e = tb.E[s][along];
+          const T* ft = FT + (((lc * 3 + d) * 2 + s) * FTF) * K2 + proj;
+          fv = fma(e, ft[0], fv);
+          if (OP == OP_SIPG) {
+            fg0 = fma(e, ft[K2], fg0);
+            fg1 = fma(e, ft[2 * K2], fg1);
+            fg2 = fma(e, ft[3 * K2], fg2);
+          }
+        }
+      }
+      T t0, t1, t2;
+      const int64_t qi = cell * K3 + pt;
+      if (OP == OP_SIPG) {
+        const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
+        if (GEO == GEO_CART) {
+          T w = tb.W[la] * tb.W[lb] * tb.W[z] * gm.cart_detj;
+          if (gm.kq) w *= gm.kq[ijk[0] * K + la];
+          t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+          t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+          t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+        } else if (GEO == GEO_FULL) {
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          T J[9];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+          const T jw = cp[9 * n];
+          // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
+          const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
+          const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
+          const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+          t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
+          t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
+          t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+        } else {
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
+          t0 = a00 * g0 + a01 * g1 + a02 * g2;
+          t1 = a01 * g0 + a11 * g1 + a12 * g2;
+          t2 = a02 * g0 + a12 * g1 + a22 * g2;
+        }
+      } else {
+        const T uq = Uc[pt];
+        T b0, b1, b2;
+        if (GEO == GEO_CART) {
+          const T w = -tb.W[la] * tb.W[lb] * tb.W[z] * gm.cart_detj;
+          b0 = w * gm.cart_jinv[0] * gm.vel[0];
+          b1 = w * gm.cart_jinv[1] * gm.vel[1];
+          b2 = w * gm.cart_jinv[2] * gm.vel[2];
+        } else if (GEO == GEO_FULL) {
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          T J[9];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+          const T jw = -cp[9 * n];
+          b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
+          b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
+          b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+        } else {
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          b0 = cp[0];
+          b1 = cp[n];
+          b2 = cp[2 * n];
+        }
+        t0 = b0 * uq;
+        t1 = b1 * uq;
+        t2 = b2 * uq;
+      }
+      G0[pt] = t0 + fg0;
+      G1[pt] = t1 + fg1;
+      G2[pt] = t2 + fg2;
+      Uc[pt] = fv;
+    }
+  }
+  __syncthreads();
+
+  // 5. integration: V += D^T T_x, D^T T_y, D^T T_z, then S^T along z, y, x
+  if (active) line_add_transposed<K>(tb.D, G0, Uc, K * (la + K * lb), 1);
+  __syncthreads();
+  if (active) line_add_transposed<K>(tb.D, G1, Uc, la + K2 * lb, K);
+  __syncthreads();
+  if (active) {
+    line_add_transposed<K>(tb.D, G2, Uc, la + K * lb, K2);
+    line_apply<K, true>(tb.S, Uc, la + K * lb, K2);
+  }
+  __syncthreads();
+  if (active) line_apply<K, true>(tb.S, Uc, la + K2 * lb, K);
+  __syncthreads();
+  if (active) line_apply<K, true>(tb.S, Uc, K * (la + K * lb), 1);
+  __syncthreads();
+
+  // write (set) the block's contiguous range; optional src . dst partial
+  {
+    T* o = P.dst + cell0 * K3;
+    double acc = 0.0;
+    const T* s = P.src + cell0 * K3;
+    const bool dot = P.dot_partial != nullptr;
+    for (int i = tid; i < nloc * K3; i += blockDim.x) {
+      const T v = U[i];
+      o[i] = v;
+      if (dot) acc += (double)v * (double)s[i];
+    }
+    if (dot) {
+      double* red = reinterpret_cast<double*>(G);
+      red[tid] = acc;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
+        P.dot_partial[blockIdx.x] = t;
+      }
+    }
+  }
+}
+
+template <int K, typename T, int GEO, int OP>
+cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
+  ApplyParams<T> P;
+  P.tab = *static_cast<const Tables<T>*>(L.tables);
+  P.geo = *static_cast<const Geometry<T>*>(L.geometry);
+  P.src = static_cast<const T*>(L.src);
+  P.dst = static_cast<T*>(L.dst);
+  P.dot_partial = L.dot_partial;
+  constexpr int C = Shape<K>::C;
+  const int smem = Smem<K, OP>::per_cell * C * (int)sizeof(T);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<K, T, GEO, OP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int64_t grid = (n_cells + C - 1) / C;
+  if (grid <= 0) return cudaSuccess;
+  apply_kernel<K, T, GEO, OP><<<(unsigned)grid, Shape<K>::threads, smem, L.stream>>>(P);
+  return cudaGetLastError();
+}
+
+template <int K, typename T>
+cudaError_t launch_prec(const ApplyLaunch& L, int64_t n_cells) {
+  if (L.op == OP_SIPG) {
+    if (L.geo == GEO_CART) return launch_one<K, T, GEO_CART, OP_SIPG>(L, n_cells);
+    if (L.geo == GEO_FULL) return launch_one<K, T, GEO_FULL, OP_SIPG>(L, n_cells);
+    return launch_one<K, T, GEO_MERGED, OP_SIPG>(L, n_cells);
+  }
+  if (L.geo == GEO_CART) return launch_one<K, T, GEO_CART, OP_ADV>(L, n_cells);
+  if (L.geo == GEO_FULL) return launch_one<K, T, GEO_FULL, OP_ADV>(L, n_cells);
+  return launch_one<K, T, GEO_MERGED, OP_ADV>(L, n_cells);
+}
+
+template <int K>
+cudaError_t launch_apply(const ApplyLaunch& L, int64_t n_cells) {
+  return L.prec == 0 ? launch_prec<K, double>(L, n_cells) : launch_prec<K, float>(L, n_cells);
+}
+
+}  // namespace dg
+
+#define DG_DEFINE_APPLY_LAUNCHER(KK)                                              \
+  namespace dg {                                                                  \
+  cudaError_t launch_apply_k##KK(const ApplyLaunch& L, int64_t n_cells) {         \
+    return launch_apply<KK>(L, n_cells);                                          \
+  }                                                                               \
+  }

@@ -1,0 +1,94 @@
+// Internal declarations shared by the apply kernels and the C-ABI layer.
+//
+// Notation (Kronbichler & Kormann, arXiv:1711.03590):
+//   k = p+1 points per direction; S = values of the k Gauss-Lobatto Lagrange
+//   polynomials at the k Gauss points (basis change, Eq. tensor_to_collocation);
+//   D = collocation derivative D^co on the Gauss points; the face kernels use
+//   S_f / D_f of Eq. (face_integral) for the Gauss-Lobatto basis and the
+//   extrapolation E_s of the Gauss-collocation basis to the faces xi = s.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+constexpr int kMaxK = 9;  // degree 8
+
+enum Geo { GEO_CART = 0, GEO_FULL = 2, GEO_MERGED = 3 };
+enum Op { OP_SIPG = 0, OP_ADV = 1 };
+
+// 1D tables, passed by value as kernel parameters (constant bank).
+template <typename T>
+struct Tables {
+  T S[kMaxK * kMaxK];   // S[q*k+i]  = l^GL_i(g_q)
+  T D[kMaxK * kMaxK];   // D[q*k+j]  = (l^G_j)'(g_q), Gauss-collocation derivative
+  T E[2][kMaxK];        // E[s][j]   = l^G_j(s), Gauss-collocation value at xi = s
+  T DF[2][kMaxK];       // DF[s][i]  = (l^GL_i)'(s), GL derivative at xi = s
+  T W[kMaxK];           // Gauss weights on [0,1]
+};
+
+// Device geometry and mesh description used by the apply kernel.
+template <typename T>
+struct Geometry {
+  int n[3];
+  int periodic;
+  int64_t n_cells;
+  // faces of direction d: positions P_d = periodic ? n_d : n_d + 1,
+  // face id = pos + P_d (i_t1 + n_t1 i_t2), t1 < t2 the other directions
+  int P[3];
+  // FULL / MERGED cell arrays (structure of arrays, stride ncq = n_cells k^3)
+  const T* __restrict__ cell;  // FULL SIPG: 9 J^{-1} + 1 kappa JxW; FULL ADV: 9 + 1 JxW;
+                               // MERGED SIPG: 6; MERGED ADV: 3
+  int64_t ncq;
+  // face arrays per direction (stride nfq[d] = nfaces_d k^2)
+  const T* __restrict__ face[3];  // SIPG: 6 j_n (slot0 xyz, slot1 xyz) + 1 kappa da w; ADV: 1 c.n da w
+  const T* __restrict__ tau[3];   // SIPG: penalty per face
+  int64_t nfq[3];
+  // Cartesian compression
+  T cart_jinv[3];       // n_d
+  T cart_detj;          // 1 / (n0 n1 n2)
+  T cart_tau[3];        // (p+1)^2 n_d penalty_scale
+  const T* __restrict__ kq;  // kappa at cell Gauss x-positions [n0 k] (or null: kappa = 1)
+  const T* __restrict__ kf;  // kappa at x-face positions [n0 + 1]
+  T vel[3];             // advection velocity
+};
+
+// Host-side description of one apply launch.
+struct ApplyLaunch {
+  int k;
+  int prec;  // 0 double, 1 float
+  int geo;
+  int op;
+  const void* src;
+  void* dst;
+  const void* tables;    // Tables<T>*
+  const void* geometry;  // Geometry<T>*
+  double* dot_partial;   // optional: per-block partial of src . dst (FP64)
+  cudaStream_t stream;
+};
+
+// Cells per block of the apply kernel for k points per direction: about
+// 256 threads (k^2 per cell).
+__host__ __device__ constexpr int cells_per_block(int k) {
+  return k == 2 ? 64 : k == 3 ? 28 : k == 4 ? 16 : k == 5 ? 10 : k == 6 ? 7 : k == 7 ? 5 : k == 8 ? 4 : 3;
+}
+
+// Shared-memory scalars per cell: u, three gradient fields, two neighbour
+// trace buffers (2 faces x NF fields x k^2) and the face test coefficients
+// (6 faces x FTF fields x k^2); NF = 2, FTF = 4 for SIPG, 1 and 1 for advection.
+__host__ __device__ constexpr int smem_scalars_per_cell(int k, int op) {
+  return 4 * k * k * k + 2 * (2 * (op == OP_SIPG ? 2 : 1) * k * k) + 6 * (op == OP_SIPG ? 4 : 1) * k * k;
+}
+
+// Implemented per degree in dg_apply_k<K>.cu.
+cudaError_t launch_apply_k2(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_apply_k3(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_apply_k4(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_apply_k5(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_apply_k6(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_apply_k7(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_apply_k8(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_apply_k9(const ApplyLaunch&, int64_t n_cells);
+
+}  // namespace dg
