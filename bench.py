@@ -246,6 +246,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--degree", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision of the headline apply")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
@@ -275,10 +276,11 @@ def main():
     common = dict(periodic=mesh["periodic"], mapping=mesh["mapping"], amplitude=mesh["amplitude"])
     peaks = load_peaks()
 
-    op = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64", coeff=w["coeff"], **common)
+    op = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec=args.prec, coeff=w["coeff"], **common)
     n = op.n_dofs
     n_cells = op.info()["n_cells"]
-    src = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank), device="cuda")
+    ssz = 8 if args.prec == "fp64" else 4
+    src = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank), dtype=op.dtype, device="cuda")
     dst = torch.empty_like(src)
     for _ in range(args.warmup):
         op.apply(src, dst)
@@ -306,18 +308,23 @@ def main():
     # roofline of the apply kernel (the only kernel of a step)
     flops = kernel_flops_per_cell(k, "sipg", w["geom"]) * n_cells
     achieved_tf = flops / (launch_ms / 1e3) / 1e12
-    bpd = bytes_per_dof(k, 8, "sipg", w["geom"])
+    bpd = bytes_per_dof(k, ssz, "sipg", w["geom"])
     achieved_gbs = bpd * n / (launch_ms / 1e3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "apply_kernel<5,double,FULL,SIPG>", "flops_per_launch": flops,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": achieved_gbs / peaks["hbm_gbs"], "bytes_per_dof": bpd,
-                        "peak_source": peaks.get("source")}}
+    kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, "double" if args.prec == "fp64" else "float")
+    hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": kname, "bytes_per_dof": bpd,
+           "peak_source": peaks.get("source")}
+    if args.prec == "fp64":
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kname,
+                    "flops_per_launch": flops,
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                    "hbm": hbm}
+    else:
+        roofline = dict(hbm, alu_tflops=achieved_tf, alu_peak_tflops=FP32_PEAK_TFLOPS)
 
     # end to end through the C ABI with pinned host buffers
-    hsrc = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank)).pin_memory()
+    hsrc = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank), dtype=op.dtype).pin_memory()
     hdst = torch.empty_like(hsrc).pin_memory()
     for _ in range(2):
         op.apply_host(hsrc, hdst)
@@ -326,12 +333,12 @@ def main():
     for _ in range(e2e_steps):
         op.apply_host(hsrc, hdst)
     te = time.perf_counter() - te
-    e2e = {"value": n / (te / e2e_steps), "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+    e2e = {"value": n / (te / e2e_steps), "unit": UNIT, "h2d_bytes_per_step": n * ssz, "d2h_bytes_per_step": n * ssz,
            "call": "dg_apply_host"}
     op.close()
 
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and args.prec == "fp64":
         # FP32 arithmetic, same workload
         op32 = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp32", coeff=w["coeff"], **common)
         s32, d32 = src.float(), torch.empty(n, dtype=torch.float32, device="cuda")
@@ -361,7 +368,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": wname, "degree": p, "cells": n_cells,
                            "dofs": n, "geometry": "full per-point Jacobians (G3)", "operator": "SIPG",
                            "boundary": "Dirichlet", "coefficient": "1+0.5 sin(2 pi x)",
