@@ -170,6 +170,28 @@ dg_status dg_rhs(dg_handle *h, int which_f, double *rhs);
 dg_status dg_cg_solve(dg_handle *h, const double *rhs, double *x, double rtol, int max_it, int *iters,
                       double *final_rel_res);
 
+/* No counterpart in the paper: an allocation-free variant of the apply with
+ * the FP64 product src . dst that the CG iteration fuses into the apply.
+ *
+ * For callers that cannot call cudaMalloc once they are running: code inside
+ * a device-memory pool owned by another framework, a real-time loop that
+ * must not enter the allocator, or a process whose device memory is already
+ * fully handed out.  The per-block partial sums of the product, which
+ * dg_cg_solve keeps in memory it allocates, live here in a fixed static
+ * device array of the library (65,536 partials, about 512 KiB, held by
+ * every GPU that loads the library until the process exits).
+ *   src, dst  device pointers as for dg_apply (dst = A src, same kernel).
+ *   dot       device pointer to one double; receives sum_i src_i dst_i,
+ *             reduced in a fixed order (bitwise reproducible).
+ * Operators whose apply needs more than 65,536 CUDA blocks (see
+ * dg_info_t.blocks) are rejected with DG_ERR_ARG.  No call allocates or
+ * frees memory.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race on it and must be ordered by the caller.
+ * Asynchronous on the handle's stream. */
+dg_status dg_apply_dot_noalloc(dg_handle *h, const void *src, void *dst, double *dot);
+
 /* Free everything the handle owns.  NULL is accepted. */
 dg_status dg_destroy(dg_handle *h);
 

@@ -45,7 +45,7 @@ OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
 PRECS = {"fp64": DG_FP64, "fp32": DG_FP32}
 
 EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
-            "dg_cg_solve", "dg_destroy", "dg_last_error"]
+            "dg_cg_solve", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -99,6 +99,7 @@ def load_library(path=None):
     L.dg_rhs.argtypes = [_vp, ctypes.c_int, _vp]
     L.dg_cg_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_double)]
+    L.dg_apply_dot_noalloc.argtypes = [_vp, _vp, _vp, _vp]
     L.dg_destroy.argtypes = [_vp]
     L.dg_last_error.argtypes = [_vp]
     L.dg_last_error.restype = ctypes.c_char_p
@@ -161,6 +162,12 @@ def dg_apply(handle, src_ptr, dst_ptr):
 
 def dg_apply_host(handle, src_ptr, dst_ptr):
     _check(load_library().dg_apply_host(_vp(handle), _vp(src_ptr), _vp(dst_ptr)), handle)
+
+
+def dg_apply_dot_noalloc(handle, src_ptr, dst_ptr, dot_ptr):
+    """dst = A src and *dot = src . dst without any device allocation (the
+    partial sums live in a fixed static device array of the library)."""
+    _check(load_library().dg_apply_dot_noalloc(_vp(handle), _vp(src_ptr), _vp(dst_ptr), _vp(dot_ptr)), handle)
 
 
 def dg_rhs(handle, which_f, rhs_ptr):

@@ -815,6 +815,24 @@ void free_handle(dg_handle* h) {
 
 }  // namespace
 
+// Used by dg_noalloc.cu: the apply launch with caller-provided per-block
+// partials of src . dst, after the same argument checks as dg_apply.
+dg_status dg_internal_apply_with_partials(dg_handle* h, const void* src, void* dst, double* partials,
+                                          int64_t* n_blocks, cudaStream_t* stream) {
+  if (!src || !dst) return fail(h, DG_ERR_ARG, "src or dst is NULL");
+  const int64_t bytes = h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  const char* a = static_cast<const char*>(src);
+  const char* b = static_cast<const char*>(dst);
+  if (a < b + bytes && b < a + bytes) return fail(h, DG_ERR_ARG, "src and dst overlap");
+  if ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15)
+    return fail(h, DG_ERR_ARG, "src and dst must be 16-byte aligned");
+  *n_blocks = apply_blocks(h);
+  *stream = h->stream;
+  return launch_apply(h, src, dst, partials);
+}
+
+dg_status dg_internal_fail(dg_handle* h, dg_status s, const char* msg) { return fail(h, s, msg); }
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
