@@ -172,7 +172,7 @@ void bary_diff_matrix(int k, const double* x, const double* lam, double* Dm) {
 
 struct Tables64 {
   double gq[kMaxK], gw[kMaxK], gl[kMaxK];
-  double S[kMaxK * kMaxK], D[kMaxK * kMaxK], E[2][kMaxK], DF[2][kMaxK];
+  double S[kMaxK * kMaxK], D[kMaxK * kMaxK], DS[kMaxK * kMaxK], E[2][kMaxK], DF[2][kMaxK];
 };
 
 void build_tables(int k, Tables64& t) {
@@ -183,6 +183,14 @@ void build_tables(int k, Tables64& t) {
   bary_weights(k, t.gl, ll);
   for (int q = 0; q < k; ++q) bary_values(k, t.gl, ll, t.gq[q], t.S + q * k);
   bary_diff_matrix(k, t.gq, lg, t.D);
+  // derivative of the GL basis at the Gauss points: the Gauss-collocation
+  // derivative of its (exact) Gauss-point interpolant
+  for (int q = 0; q < k; ++q)
+    for (int i = 0; i < k; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += t.D[q * k + j] * t.S[j * k + i];
+      t.DS[q * k + i] = s;
+    }
   bary_values(k, t.gq, lg, 0.0, t.E[0]);
   bary_values(k, t.gq, lg, 1.0, t.E[1]);
   double DL[kMaxK * kMaxK];
@@ -200,6 +208,7 @@ dg::Tables<T> cast_tables(int k, const Tables64& t) {
   for (int i = 0; i < k * k; ++i) {
     o.S[i] = (T)t.S[i];
     o.D[i] = (T)t.D[i];
+    o.DS[i] = (T)t.DS[i];
   }
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < k; ++i) {
@@ -905,8 +914,7 @@ dg_status dg_info(const dg_handle* h, dg_info_t* info) {
   info->face_geometry_bytes = h->face_bytes;
   info->cells_per_block = dg::cells_per_block(h->k);
   info->threads_per_block = info->cells_per_block * h->k * h->k;
-  info->shared_bytes_per_block = dg::smem_scalars_per_cell(h->k, h->op) * info->cells_per_block *
-                                 (h->prec == DG_FP64 ? 8 : 4);
+  info->shared_bytes_per_block = dg::smem_bytes_per_block(h->k, h->op, h->prec == DG_FP64 ? 8 : 4);
   info->blocks = apply_blocks(h);
   return DG_OK;
 }

@@ -1,24 +1,28 @@
 // Fused element-centric DG apply kernel (one launch per operator evaluation).
 //
-// Each CUDA block owns C consecutive cells (C k^2 threads, thread (a,b) of a
+// Each CUDA block owns C consecutive cells (C k^2 threads; thread (a,b) of a
 // cell owns one line of k points in whichever direction a phase sweeps).
 // For every cell the block computes, in shared memory:
 //   1. gather the cell's k^3 contiguous dofs (Algorithm 1 step (ii)(a));
 //   2. basis change S (x) S (x) S to the Gauss points and the collocation
 //      derivative D^co along x, y, z (Eq. tensor_to_collocation);
-//   3. for the six faces: the own traces by extrapolating the Gauss-point
-//      fields to xi = 0 / 1, the neighbour's traces from its Gauss-Lobatto
-//      dofs through S_f / D_f and the in-face S (x) S and D^co steps of
-//      Eq. (face_integral), the numerical flux of Eq. (poisson_sip) or
-//      Eq. (advection) at each face point (Algorithm 1 step (iii)(c)), and
-//      the test coefficients of this cell's side;
+//   3. for the six faces, one direction at a time: the neighbour's traces
+//      from its Gauss-Lobatto dofs through S_f / D_f and the in-face S (x) S
+//      and derivative steps of Eq. (face_integral); the own traces by
+//      extrapolating the Gauss-point fields to xi = 0 / 1; the numerical flux
+//      of Eq. (poisson_sip) or Eq. (advection) at each face point (Algorithm 1
+//      steps (iii)(c), (iv)(c)); the test coefficients of this cell's side;
 //   4. the quadrature-point operation with the stored geometry (Sec. 5: G3
 //      J^{-1} and det J w, G4 merged coefficient, or Cartesian constants) and
 //      the injection of the face test coefficients into the Gauss-point fields;
 //   5. the transposed derivative and basis change (integration), and a set
 //      (not add) of the cell's dst entries (the remark after Algorithm 1).
-// Every face is thus evaluated once from each side; each cell's result is
-// written exactly once, with no atomics and a fixed summation order.
+// Every face is evaluated once from each side; each cell's result is written
+// exactly once, with no atomics and a fixed summation order.
+//
+// All 1D matrices are read with compile-time indices from the kernel
+// parameters (constant bank operands); the few values indexed by thread
+// position (E, W) are copied to shared memory first.
 #pragma once
 
 #include "dg_internal.cuh"
@@ -42,7 +46,9 @@ struct Shape {
 
 template <int K, int OP>
 struct Smem {
-  static constexpr int NF = OP == OP_SIPG ? 2 : 1;   // neighbour trace fields per face
+  static constexpr int NBA = OP == OP_SIPG ? 2 : 1;  // value and normal derivative of the neighbour
+  static constexpr int NBB = OP == OP_SIPG ? 3 : 1;  // after the first in-face sweep: value, d_n, d_t1
+                                                     // (FP64 per-point variant uses the first NBA)
   static constexpr int FTF = OP == OP_SIPG ? 4 : 1;  // face test fields per face
   static constexpr int per_cell = smem_scalars_per_cell(K, OP);
 };
@@ -62,18 +68,19 @@ __device__ __forceinline__ void line_apply(const T* __restrict__ M, T* v, int ba
   }
 }
 
-// out[base + q stride] = sum_i M[q][i] in[base + i stride]
+// out[ob + q os] = sum_i M[q][i] in[ib + i is]
 template <int K, typename T>
-__device__ __forceinline__ void line_apply_to(const T* __restrict__ M, const T* in, T* out, int base, int stride) {
+__device__ __forceinline__ void line_apply_to(const T* __restrict__ M, const T* in, int ib, int is, T* out, int ob,
+                                              int os) {
   T x[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) x[i] = in[base + i * stride];
+  for (int i = 0; i < K; ++i) x[i] = in[ib + i * is];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     T s = T(0);
 #pragma unroll
     for (int i = 0; i < K; ++i) s = fma(M[q * K + i], x[i], s);
-    out[base + q * stride] = s;
+    out[ob + q * os] = s;
   }
 }
 
@@ -99,16 +106,25 @@ __device__ __forceinline__ int line_base(int d, int a, int b) {
   return d == 0 ? K * (a + K * b) : d == 1 ? a + K * K * b : a + K * b;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.L2 [%0];" ::"l"(p));
+}
+
 template <int K, typename T, int GEO, int OP>
 __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_constant__ ApplyParams<T> P) {
   constexpr int K2 = K * K, K3 = K2 * K, C = Shape<K>::C;
-  constexpr int NF = Smem<K, OP>::NF, FTF = Smem<K, OP>::FTF;
+  constexpr int NBA = Smem<K, OP>::NBA, NBB = Smem<K, OP>::NBB, FTF = Smem<K, OP>::FTF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3] u -> u at Gauss points -> test value field
   T* G = U + C * K3;                      // [3][C][K3] gradients -> test gradient fields
-  T* NBa = G + 3 * C * K3;                // [C][2][NF][K2] neighbour traces
-  T* NBb = NBa + C * 2 * NF * K2;         // [C][2][NF][K2]
-  T* FT = NBb + C * 2 * NF * K2;          // [C][3][2][FTF][K2] face test coefficients
+  T* NBa = G + 3 * C * K3;                // [C][2][NBA][K2] neighbour traces
+  T* NBb = NBa + C * 2 * NBA * K2;        // [C][2][NBB][K2]
+  T* FT = NBb + C * 2 * NBB * K2;         // [C][3][2][FTF][K2] face test coefficients
+  T* sE = FT + C * 6 * FTF * K2;          // [2][K]
+  T* sW = sE + 2 * K;                     // [K]
+  T* sS = sW + K;                         // [K][K] (rows indexed by thread position)
+  T* sD = sS + K2;                        // [K][K]
+  constexpr bool kLineFaces = sizeof(T) == 4;
 
   const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
@@ -125,6 +141,28 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
   T* G1 = G + (C + lc) * K3;
   T* G2 = G + (2 * C + lc) * K3;
 
+  // 0. start the HBM fetch of this block's cell geometry into L2; it is read
+  // in phase 4, after the sweeps and face work
+  if (GEO != GEO_CART) {
+    constexpr int NA = GEO == GEO_FULL ? 10 : (OP == OP_SIPG ? 6 : 3);
+    const char* base = reinterpret_cast<const char*>(gm.cell + cell0 * K3);
+    const int64_t bytes = (int64_t)nloc * K3 * (int64_t)sizeof(T);
+    const int lines = (int)((bytes + 127) / 128) + 1;
+    for (int t = tid; t < NA * lines; t += blockDim.x) {
+      const int a = t / lines, l = t - a * lines;
+      const char* p = base + a * gm.ncq * (int64_t)sizeof(T) + (int64_t)l * 128;
+      if (p < base + a * gm.ncq * (int64_t)sizeof(T) + bytes) prefetch_l2(p);
+    }
+  }
+
+  if (tid < 2 * K) sE[tid] = tb.E[tid / K][tid % K];
+  if (tid < K) sW[tid] = tb.W[tid];
+  if (!kLineFaces)
+    for (int i = tid; i < K2; i += blockDim.x) {
+      sS[i] = tb.S[i];
+      sD[i] = tb.D[i];
+    }
+
   int ijk[3];
   {
     const int64_t c = active ? cell : cell0;
@@ -140,7 +178,7 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
   }
   __syncthreads();
 
-  // 2. basis change to the Gauss points, x then y then z
+  // 2. basis change to the Gauss points, x then y then z; collocation derivatives
   if (active) line_apply<K, false>(tb.S, Uc, K * (la + K * lb), 1);
   __syncthreads();
   if (active) line_apply<K, false>(tb.S, Uc, la + K2 * lb, K);
@@ -149,15 +187,15 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
   __syncthreads();
   if (OP == OP_SIPG) {
     if (active) {
-      line_apply_to<K>(tb.D, Uc, G0, K * (la + K * lb), 1);
-      line_apply_to<K>(tb.D, Uc, G1, la + K2 * lb, K);
-      line_apply_to<K>(tb.D, Uc, G2, la + K * lb, K2);
+      line_apply_to<K>(tb.D, Uc, K * (la + K * lb), 1, G0, K * (la + K * lb), 1);
+      line_apply_to<K>(tb.D, Uc, la + K2 * lb, K, G1, la + K2 * lb, K);
+      line_apply_to<K>(tb.D, Uc, la + K * lb, K2, G2, la + K * lb, K2);
     }
     __syncthreads();
   }
 
-  // 3. faces, one direction at a time
-#pragma unroll 1
+  // 3. faces, one direction at a time (the loop is unrolled: d is constant)
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     const int strd = d == 0 ? 1 : d == 1 ? K : K2;
@@ -177,6 +215,8 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
       nbc[s] = inside ? j[0] + (int64_t)gm.n[0] * (j[1] + (int64_t)gm.n[1] * j[2]) : -1;
       fid[s] = pos + (int64_t)gm.P[d] * (ijk[t1] + (int64_t)gm.n[t1] * ijk[t2]);
     }
+    T* nba = NBa + lc * 2 * NBA * K2;  // [2][NBA][K2]
+    T* nbb = NBb + lc * 2 * NBB * K2;  // [2][NBB][K2]
     // 3a. neighbour's face-normal interpolation from its Gauss-Lobatto dofs:
     // the value is the layer on the shared face, the normal derivative uses D_f
     if (active) {
@@ -187,44 +227,164 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
         T v[K];
 #pragma unroll
         for (int l = 0; l < K; ++l) v[l] = un[l * strd];
-        T* nb = NBa + (lc * 2 + s) * NF * K2;
-        nb[ln] = s ? v[0] : v[K - 1];
+        nba[(s * NBA) * K2 + ln] = s ? v[0] : v[K - 1];
         if (OP == OP_SIPG) {
           T dv = T(0);
 #pragma unroll
           for (int l = 0; l < K; ++l) dv = fma(tb.DF[1 - s][l], v[l], dv);
-          nb[K2 + ln] = dv;
+          nba[(s * NBA + 1) * K2 + ln] = dv;
         }
       }
     }
     __syncthreads();
-    // 3b. in-face basis change along t1 then t2
+    // 3b. in-face interpolation of the neighbour's traces to the face Gauss
+    // points.  FP32 (LSU-limited): line sweeps, one thread per line, matrices
+    // with compile-time indices.  FP64 (FP64-pipe-limited, charged per warp
+    // instruction): one thread per face point so that every lane works.
+    if (kLineFaces) {
+      // along t1 at fixed t2 index j: the value with S and with DS = d/dt1,
+      // the normal derivative with S (Cartesian meshes need no tangential
+      // derivative)
     if (active) {
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
+      constexpr int NB1 = (OP == OP_SIPG) ? (GEO == GEO_CART ? 2 : 3) : 1;
+      for (int task = ln; task < 2 * NB1 * K; task += K2) {
+        const int s = task / (NB1 * K), f = (task / K) % NB1, j = task % K;
         if (nbc[s] < 0) continue;
+        const T* in = nba + (s * NBA + (f == 1 ? 1 : 0)) * K2;
+        T* out = nbb + (s * NBB + f) * K2;
+        if (OP == OP_SIPG && f == 2)
+          line_apply_to<K>(tb.DS, in, K * j, 1, out, K * j, 1);
+        else
+          line_apply_to<K>(tb.S, in, K * j, 1, out, K * j, 1);
+      }
+    }
+    __syncthreads();
+    // ... then along t2 at fixed t1 index i, one thread per line and side for
+    // all fields; it forms the neighbour's derivative along this cell's
+    // outward normal, -j_n(nb) . grad_xi u_nb, at each face point
+    if (active && ln < 2 * K) {
+      const int s = ln / K, i = ln % K;
+      if (nbc[s] >= 0) {
+        const T* in = nbb + s * NBB * K2;
+        T* out = nba + s * NBA * K2;
+        T x0[K], val[K];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const T* in = NBa + ((lc * 2 + s) * NF + f) * K2;
+        for (int jj = 0; jj < K; ++jj) x0[jj] = in[i + K * jj];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
           T acc = T(0);
 #pragma unroll
-          for (int i = 0; i < K; ++i) acc = fma(tb.S[la * K + i], in[i + K * lb], acc);
-          NBb[((lc * 2 + s) * NF + f) * K2 + ln] = acc;
+          for (int jj = 0; jj < K; ++jj) acc = fma(tb.S[q * K + jj], x0[jj], acc);
+          val[q] = acc;
+          out[i + K * q] = acc;
+        }
+        if (OP == OP_SIPG) {
+          T x1[K], dn[K];
+#pragma unroll
+          for (int jj = 0; jj < K; ++jj) x1[jj] = in[K2 + i + K * jj];
+#pragma unroll
+          for (int q = 0; q < K; ++q) {
+            T acc = T(0);
+#pragma unroll
+            for (int jj = 0; jj < K; ++jj) acc = fma(tb.S[q * K + jj], x1[jj], acc);
+            dn[q] = acc;
+          }
+          if (GEO == GEO_CART) {
+            const T jn = (s ? T(1) : T(-1)) * gm.cart_jinv[d];
+#pragma unroll
+            for (int q = 0; q < K; ++q) out[K2 + i + K * q] = jn * dn[q];
+          } else {
+            T x2[K];
+#pragma unroll
+            for (int jj = 0; jj < K; ++jj) x2[jj] = in[2 * K2 + i + K * jj];
+            const int64_t nfq = gm.nfq[d];
+            const T* fp = gm.face[d] + fid[s] * K2 + i;
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+              T dt1 = T(0), dt2 = T(0);
+#pragma unroll
+              for (int jj = 0; jj < K; ++jj) {
+                dt1 = fma(tb.S[q * K + jj], x2[jj], dt1);
+                dt2 = fma(tb.D[q * K + jj], val[jj], dt2);
+              }
+              T gn[3];
+              gn[d] = dn[q];
+              gn[t1] = dt1;
+              gn[t2] = dt2;
+              // the neighbour is slot s of this face (slot 0 = lower side)
+              const T* f = fp + K * q;
+              out[K2 + i + K * q] = -(f[(s * 3 + 0) * nfq] * gn[0] + f[(s * 3 + 1) * nfq] * gn[1] +
+                                      f[(s * 3 + 2) * nfq] * gn[2]);
+            }
+          }
         }
       }
     }
     __syncthreads();
-    if (active) {
+    } else {
+      // along t1 (output point (qa = la, j = lb)), then along t2 (point (i = la, qb = lb))
+      if (active) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        if (nbc[s] < 0) continue;
+        for (int s = 0; s < 2; ++s) {
+          if (nbc[s] < 0) continue;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const T* in = NBb + ((lc * 2 + s) * NF + f) * K2;
-          T acc = T(0);
+          for (int f = 0; f < NBA; ++f) {
+            const T* in = nba + (s * NBA + f) * K2;
+            T acc = T(0);
 #pragma unroll
-          for (int j = 0; j < K; ++j) acc = fma(tb.S[lb * K + j], in[la + K * j], acc);
-          NBa[((lc * 2 + s) * NF + f) * K2 + ln] = acc;
+            for (int i = 0; i < K; ++i) acc = fma(sS[la * K + i], in[i + K * lb], acc);
+            nbb[(s * NBB + f) * K2 + ln] = acc;
+          }
+        }
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if (nbc[s] < 0) continue;
+#pragma unroll
+          for (int f = 0; f < NBA; ++f) {
+            const T* in = nbb + (s * NBB + f) * K2;
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc = fma(sS[lb * K + j], in[la + K * j], acc);
+            nba[(s * NBA + f) * K2 + ln] = acc;
+          }
+        }
+      }
+      __syncthreads();
+      // neighbour derivative along this cell's outward normal at point (la, lb)
+      T dnn[2] = {T(0), T(0)};
+      if (OP == OP_SIPG && active) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if (nbc[s] < 0) continue;
+          const T* nbt = nba + s * NBA * K2;
+          if (GEO == GEO_CART) {
+            dnn[s] = (s ? T(1) : T(-1)) * gm.cart_jinv[d] * nbt[K2 + ln];
+          } else {
+            T a1 = T(0), a2 = T(0);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+              a1 = fma(sD[la * K + i], nbt[i + K * lb], a1);
+              a2 = fma(sD[lb * K + i], nbt[la + K * i], a2);
+            }
+            T gn[3];
+            gn[d] = nbt[K2 + ln];
+            gn[t1] = a1;
+            gn[t2] = a2;
+            const int64_t nfq = gm.nfq[d];
+            const T* fp = gm.face[d] + fid[s] * K2 + ln;
+            dnn[s] = -(fp[(s * 3 + 0) * nfq] * gn[0] + fp[(s * 3 + 1) * nfq] * gn[1] + fp[(s * 3 + 2) * nfq] * gn[2]);
+          }
+        }
+      }
+      if (OP == OP_SIPG) {
+        __syncthreads();  // every read of the d_n field is done before it is overwritten
+        if (active) {
+#pragma unroll
+          for (int s = 0; s < 2; ++s)
+            if (nbc[s] >= 0) nba[(s * NBA + 1) * K2 + ln] = dnn[s];
         }
       }
     }
@@ -232,14 +392,24 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
     // 3c. numerical flux at face point (la, lb) of both faces of direction d
     if (active) {
       const int base = line_base<K>(d, la, lb);
+      T lu[K], lg0[K], lg1[K], lg2[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        lu[j] = Uc[base + j * strd];
+        if (OP == OP_SIPG) {
+          lg0[j] = G0[base + j * strd];
+          lg1[j] = G1[base + j * strd];
+          lg2[j] = G2[base + j * strd];
+        }
+      }
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const bool interior = nbc[s] >= 0;
         const T sg = s ? T(1) : T(-1);
         T u = T(0);
 #pragma unroll
-        for (int j = 0; j < K; ++j) u = fma(tb.E[s][j], Uc[base + j * strd], u);
-        const T* nbt = NBa + (lc * 2 + s) * NF * K2;
+        for (int j = 0; j < K; ++j) u = fma(tb.E[s][j], lu[j], u);
+        const T* nbt = nba + s * NBA * K2;
         const T un = interior ? nbt[ln] : T(0);
         T* ft = FT + (((lc * 3 + d) * 2 + s) * FTF) * K2 + ln;
         if (OP == OP_SIPG) {
@@ -247,47 +417,29 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
 #pragma unroll
           for (int j = 0; j < K; ++j) {
             const T e = tb.E[s][j];
-            g[0] = fma(e, G0[base + j * strd], g[0]);
-            g[1] = fma(e, G1[base + j * strd], g[1]);
-            g[2] = fma(e, G2[base + j * strd], g[2]);
+            g[0] = fma(e, lg0[j], g[0]);
+            g[1] = fma(e, lg1[j], g[1]);
+            g[2] = fma(e, lg2[j], g[2]);
           }
-          T gn[3] = {T(0), T(0), T(0)};
-          if (interior) {
-            T a1 = T(0), a2 = T(0);
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-              a1 = fma(tb.D[la * K + i], nbt[i + K * lb], a1);
-              a2 = fma(tb.D[lb * K + i], nbt[la + K * i], a2);
-            }
-            gn[d] = nbt[K2 + ln];
-            gn[t1] = a1;
-            gn[t2] = a2;
-          }
-          T jo[3], dno, dnn, fjxw, tau;
+          const T dnn = interior ? nbt[K2 + ln] : T(0);
+          T jo[3], dno, fjxw, tau;
           if (GEO == GEO_CART) {
             const T jn = sg * gm.cart_jinv[d];
             jo[0] = jo[1] = jo[2] = T(0);
             jo[d] = jn;
             dno = jn * g[d];
-            dnn = jn * gn[d];
             T kap = T(1);
             if (gm.kq) kap = d == 0 ? gm.kf[ijk[0] + s] : gm.kq[ijk[0] * K + la];
-            fjxw = kap * tb.W[la] * tb.W[lb] * gm.cart_detj * gm.cart_jinv[d];
+            fjxw = kap * sW[la] * sW[lb] * gm.cart_detj * gm.cart_jinv[d];
             tau = gm.cart_tau[d];
           } else {
             const int64_t nfq = gm.nfq[d];
             const T* fp = gm.face[d] + fid[s] * K2 + ln;
-            const int so = 1 - s;  // own slot: lower side of the face is slot 0
+            const int so = 1 - s;  // own slot: the lower side of the face is slot 0
             jo[0] = fp[(so * 3 + 0) * nfq];
             jo[1] = fp[(so * 3 + 1) * nfq];
             jo[2] = fp[(so * 3 + 2) * nfq];
             dno = jo[0] * g[0] + jo[1] * g[1] + jo[2] * g[2];
-            if (interior) {
-              const T jn0 = fp[(s * 3 + 0) * nfq], jn1 = fp[(s * 3 + 1) * nfq], jn2 = fp[(s * 3 + 2) * nfq];
-              dnn = -(jn0 * gn[0] + jn1 * gn[1] + jn2 * gn[2]);
-            } else {
-              dnn = T(0);
-            }
             fjxw = fp[6 * nfq];
             tau = gm.tau[d][fid[s]];
           }
@@ -307,7 +459,7 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
         } else {
           T cn;
           if (GEO == GEO_CART) {
-            cn = gm.vel[d] * tb.W[la] * tb.W[lb] * gm.cart_detj * gm.cart_jinv[d];
+            cn = gm.vel[d] * sW[la] * sW[lb] * gm.cart_detj * gm.cart_jinv[d];
           } else {
             cn = gm.face[d][fid[s] * K2 + ln];
           }
@@ -321,24 +473,29 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
 
   // 4. quadrature-point operation and injection of the face test coefficients
   if (active) {
-#pragma unroll 1
+    const T e0a = sE[la], e1a = sE[K + la], e0b = sE[lb], e1b = sE[K + lb];
+    const T* ftc = FT + lc * 6 * FTF * K2;
+#pragma unroll
     for (int z = 0; z < K; ++z) {
       const int pt = la + K * (lb + K * z);
-      T fv = T(0), fg0 = T(0), fg1 = T(0), fg2 = T(0);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int along = d == 0 ? la : d == 1 ? lb : z;
-        const int proj = d == 0 ? lb + K * z : d == 1 ? la + K * z : la + K * lb;
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const T e = tb.E[s][along];
-          const T* ft = FT + (((lc * 3 + d) * 2 + s) * FTF) * K2 + proj;
-          fv = fma(e, ft[0], fv);
-          if (OP == OP_SIPG) {
-            fg0 = fma(e, ft[K2], fg0);
-            fg1 = fma(e, ft[2 * K2], fg1);
-            fg2 = fma(e, ft[3 * K2], fg2);
-          }
+      T fv, fg0 = T(0), fg1 = T(0), fg2 = T(0);
+      {
+        // x faces: along = la, proj = lb + K z; y faces: along = lb, proj = la + K z;
+        // z faces: along = z, proj = la + K lb
+        const T* fx0 = ftc + (0 * 2 + 0) * FTF * K2 + lb + K * z;
+        const T* fx1 = ftc + (0 * 2 + 1) * FTF * K2 + lb + K * z;
+        const T* fy0 = ftc + (1 * 2 + 0) * FTF * K2 + la + K * z;
+        const T* fy1 = ftc + (1 * 2 + 1) * FTF * K2 + la + K * z;
+        const T* fz0 = ftc + (2 * 2 + 0) * FTF * K2 + la + K * lb;
+        const T* fz1 = ftc + (2 * 2 + 1) * FTF * K2 + la + K * lb;
+        const T ez0 = tb.E[0][z], ez1 = tb.E[1][z];
+        fv = e0a * fx0[0] + e1a * fx1[0] + e0b * fy0[0] + e1b * fy1[0] + ez0 * fz0[0] + ez1 * fz1[0];
+        if (OP == OP_SIPG) {
+          fg0 = e0a * fx0[K2] + e1a * fx1[K2] + e0b * fy0[K2] + e1b * fy1[K2] + ez0 * fz0[K2] + ez1 * fz1[K2];
+          fg1 = e0a * fx0[2 * K2] + e1a * fx1[2 * K2] + e0b * fy0[2 * K2] + e1b * fy1[2 * K2] +
+                ez0 * fz0[2 * K2] + ez1 * fz1[2 * K2];
+          fg2 = e0a * fx0[3 * K2] + e1a * fx1[3 * K2] + e0b * fy0[3 * K2] + e1b * fy1[3 * K2] +
+                ez0 * fz0[3 * K2] + ez1 * fz1[3 * K2];
         }
       }
       T t0, t1, t2;
@@ -346,7 +503,7 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
       if (OP == OP_SIPG) {
         const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
         if (GEO == GEO_CART) {
-          T w = tb.W[la] * tb.W[lb] * tb.W[z] * gm.cart_detj;
+          T w = sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
           if (gm.kq) w *= gm.kq[ijk[0] * K + la];
           t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
           t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
@@ -377,7 +534,7 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
         const T uq = Uc[pt];
         T b0, b1, b2;
         if (GEO == GEO_CART) {
-          const T w = -tb.W[la] * tb.W[lb] * tb.W[z] * gm.cart_detj;
+          const T w = -sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
           b0 = w * gm.cart_jinv[0] * gm.vel[0];
           b1 = w * gm.cart_jinv[1] * gm.vel[1];
           b2 = w * gm.cart_jinv[2] * gm.vel[2];
@@ -458,7 +615,7 @@ cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
   P.dst = static_cast<T*>(L.dst);
   P.dot_partial = L.dot_partial;
   constexpr int C = Shape<K>::C;
-  const int smem = Smem<K, OP>::per_cell * C * (int)sizeof(T);
+  const int smem = smem_bytes_per_block(K, OP, (int)sizeof(T));
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(apply_kernel<K, T, GEO, OP>,

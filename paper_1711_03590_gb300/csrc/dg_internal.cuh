@@ -23,6 +23,7 @@ template <typename T>
 struct Tables {
   T S[kMaxK * kMaxK];   // S[q*k+i]  = l^GL_i(g_q)
   T D[kMaxK * kMaxK];   // D[q*k+j]  = (l^G_j)'(g_q), Gauss-collocation derivative
+  T DS[kMaxK * kMaxK];  // DS[q*k+i] = (l^GL_i)'(g_q) = (D S)[q][i], GL derivative at the Gauss points
   T E[2][kMaxK];        // E[s][j]   = l^G_j(s), Gauss-collocation value at xi = s
   T DF[2][kMaxK];       // DF[s][i]  = (l^GL_i)'(s), GL derivative at xi = s
   T W[kMaxK];           // Gauss weights on [0,1]
@@ -74,11 +75,16 @@ __host__ __device__ constexpr int cells_per_block(int k) {
   return k == 2 ? 64 : k == 3 ? 28 : k == 4 ? 16 : k == 5 ? 10 : k == 6 ? 7 : k == 7 ? 5 : k == 8 ? 4 : 3;
 }
 
-// Shared-memory scalars per cell: u, three gradient fields, two neighbour
-// trace buffers (2 faces x NF fields x k^2) and the face test coefficients
-// (6 faces x FTF fields x k^2); NF = 2, FTF = 4 for SIPG, 1 and 1 for advection.
+// Shared-memory scalars per cell: u, three gradient fields, the two
+// neighbour trace buffers (2 faces x NBA / NBB fields x k^2) and the face test
+// coefficients (6 faces x FTF fields x k^2): NBA = 2, NBB = 3, FTF = 4 for
+// SIPG, 1, 1, 1 for advection.  Plus 3k + 2k^2 scalars of tables per block.
 __host__ __device__ constexpr int smem_scalars_per_cell(int k, int op) {
-  return 4 * k * k * k + 2 * (2 * (op == OP_SIPG ? 2 : 1) * k * k) + 6 * (op == OP_SIPG ? 4 : 1) * k * k;
+  return 4 * k * k * k + 2 * ((op == OP_SIPG ? 2 : 1) + (op == OP_SIPG ? 3 : 1)) * k * k +
+         6 * (op == OP_SIPG ? 4 : 1) * k * k;
+}
+__host__ __device__ constexpr int smem_bytes_per_block(int k, int op, int scalar_bytes) {
+  return (cells_per_block(k) * smem_scalars_per_cell(k, op) + 3 * k + 2 * k * k) * scalar_bytes;
 }
 
 // Implemented per degree in dg_apply_k<K>.cu.
