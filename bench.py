@@ -178,6 +178,48 @@ def time_applies(torch, op, src, dst, steps, per_launch=True):
     return total_ms, launch_ms
 
 
+def solve_metrics(torch, dgp, args, n=16, p=3, rtol=1e-10, repeats=20):
+    """Poisson -div(kappa grad u) = f (manufactured u = sin sin sin, Dirichlet)
+    on the n^3 sine-deformed mesh, degree p, G3 geometry: time to a relative
+    residual of rtol with plain FP64 CG and with the mixed-precision solver
+    (FP32 CG inside FP64 defect correction), then the latency distribution of
+    repeated mixed solves from a zero initial guess."""
+    kw = dict(geom="full", periodic=False, mapping=1, amplitude=0.1, coeff=1)
+    o64 = dgp.Operator(n, p, prec="fp64", **kw)
+    o32 = dgp.Operator(n, p, prec="fp32", **kw)
+    rhs = o64.rhs(1)
+    torch.cuda.synchronize()
+    x = torch.zeros_like(rhs)
+    o64.cg(rhs, x, rtol=1e-2, max_it=50, raise_on_error=False)  # warm-up
+    x.zero_()
+    t = time.perf_counter()
+    _, it64, rr64, st64 = o64.cg(rhs, x, rtol=rtol, max_it=50000, raise_on_error=False)
+    t64 = time.perf_counter() - t
+    lat = []
+    outer = inner = 0
+    rrm = None
+    for i in range(repeats + 1):
+        x.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, outer, inner, rrm = dgp.dg_cg_solve_mixed(o64.handle, o32.handle, rhs.data_ptr(), x.data_ptr(), rtol,
+                                                      raise_on_error=False)
+        if i:
+            lat.append(time.perf_counter() - t)
+    o64.close()
+    o32.close()
+    lat = np.array(lat)
+    return {"workload": "deformed_dirichlet_%d^3_p%d manufactured Poisson, kappa variable, G3" % (n, p),
+            "dofs": n ** 3 * (p + 1) ** 3, "rtol": rtol,
+            "fp64_cg": {"seconds": t64, "iterations": it64, "rel_residual": rr64, "status": st64},
+            "mixed": {"seconds_p50": float(np.median(lat)), "outer": outer, "inner_fp32_iterations": inner,
+                      "rel_residual": rrm},
+            "speedup_mixed_vs_fp64": t64 / float(np.median(lat)),
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                           "samples": len(lat)},
+            "solves_per_s": 1.0 / float(np.mean(lat))}
+
+
 def cpu_baseline(workload, form, target_s=12.0):
     """The FP64 oracle (cell-by-cell brute-force quadrature, OpenMP on the
     host cores) on a seeded sample of cells of the same workload; DoFs/s =
@@ -360,6 +402,9 @@ def main():
         tota, la = time_applies(torch, opa, src, dst, max(10, args.steps // 2))
         extras["advection_fp64"] = {"value": n / (tota / max(10, args.steps // 2) / 1e3), "unit": UNIT}
         opa.close()
+
+    if not args.no_extras and args.prec == "fp64":
+        extras["solve"] = solve_metrics(torch, dgp, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -170,6 +170,24 @@ dg_status dg_rhs(dg_handle *h, int which_f, double *rhs);
 dg_status dg_cg_solve(dg_handle *h, const double *rhs, double *x, double rtol, int max_it, int *iters,
                       double *final_rel_res);
 
+/* Mixed-precision solve of A x = rhs (SIPG) by FP64 defect correction around
+ * an FP32 conjugate-gradient solver.  h64 and h32 describe the same operator
+ * (mesh, degree, geometry, coefficient, penalty) in DG_FP64 and DG_FP32.
+ * Outer step: r = rhs - A x with the FP64 apply and FP64 vectors; stop when
+ * |r| <= rtol |rhs|; else solve A d = r / |r| with CG on the FP32 handle
+ * (FP32 applies and vectors, every inner product accumulated in FP64) from
+ * d = 0 until its residual drops by inner_rtol (or max_inner iterations), and
+ * update x += |r| d in FP64.  rhs, x: device pointers to n_dofs doubles; x is
+ * the initial guess on entry.  Work vectors are allocated on first use.  Runs
+ * on h64's stream.  Returns DG_ERR_NOT_CONVERGED after max_outer corrections,
+ * DG_ERR_BREAKDOWN on a non-finite residual or an inner CG breakdown.
+ * outer_iters, inner_iters (total FP32 iterations), final_rel_res may be
+ * NULL.  Synchronous.  (North-star extension; the paper's solvers are only
+ * referred to in Sec. 1 and Sec. 6.) */
+dg_status dg_cg_solve_mixed(dg_handle *h64, dg_handle *h32, const double *rhs, double *x, double rtol,
+                            int max_outer, double inner_rtol, int max_inner, int *outer_iters, int *inner_iters,
+                            double *final_rel_res);
+
 /* No counterpart in the paper: an allocation-free variant of the apply with
  * the FP64 product src . dst that the CG iteration fuses into the apply.
  *

@@ -45,7 +45,7 @@ OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
 PRECS = {"fp64": DG_FP64, "fp32": DG_FP32}
 
 EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
-            "dg_cg_solve", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc"]
+            "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -100,6 +100,9 @@ def load_library(path=None):
     L.dg_cg_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_double)]
     L.dg_apply_dot_noalloc.argtypes = [_vp, _vp, _vp, _vp]
+    L.dg_cg_solve_mixed.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double)]
     L.dg_destroy.argtypes = [_vp]
     L.dg_last_error.argtypes = [_vp]
     L.dg_last_error.restype = ctypes.c_char_p
@@ -183,6 +186,20 @@ def dg_cg_solve(handle, rhs_ptr, x_ptr, rtol, max_it, raise_on_error=True):
     if raise_on_error:
         _check(st, handle)
     return st, it.value, rr.value
+
+
+def dg_cg_solve_mixed(h64, h32, rhs_ptr, x_ptr, rtol, max_outer=50, inner_rtol=1e-3, max_inner=10000,
+                      raise_on_error=True):
+    """Returns (status, outer corrections, total FP32 iterations, final relative residual)."""
+    oi = ctypes.c_int(0)
+    ii = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load_library().dg_cg_solve_mixed(_vp(h64), _vp(h32), _vp(rhs_ptr), _vp(x_ptr), float(rtol), int(max_outer),
+                                          float(inner_rtol), int(max_inner), ctypes.byref(oi), ctypes.byref(ii),
+                                          ctypes.byref(rr))
+    if raise_on_error:
+        _check(st, h64)
+    return st, oi.value, ii.value, rr.value
 
 
 def dg_destroy(handle):

@@ -246,6 +246,8 @@ struct dg_handle {
   int64_t partial_len;
   double* scal;           // device scalars
   double* scal_host;      // pinned host copy
+  double* xw;             // extra work vectors (inner solution and right-hand side of
+  double* bw;             // the mixed-precision solve), allocated on first use
   // host-buffer apply staging
   void *stage_src, *stage_dst;
   std::string err;
@@ -553,15 +555,16 @@ __device__ void block_store_sum(double v, double* out) {
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// r = b - ap, p = r; partials of r.r and b.b
-__global__ void cg_init(int64_t n, const double* b, const double* ap, double* r, double* p, double* part) {
+// r = b - ap (ap may be null: r = b), p = r; partials of r.r and b.b (FP64)
+template <typename T>
+__global__ void cg_init(int64_t n, const T* b, const T* ap, T* r, T* p, double* part) {
   double rr = 0.0, bb = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double ri = b[i] - ap[i];
+    const T ri = ap ? b[i] - ap[i] : b[i];
     r[i] = ri;
     p[i] = ri;
-    rr += ri * ri;
-    bb += b[i] * b[i];
+    rr += (double)ri * (double)ri;
+    bb += (double)b[i] * (double)b[i];
   }
   block_store_sum(rr, part + blockIdx.x);
   block_store_sum(bb, part + kRedBlocks + blockIdx.x);
@@ -607,16 +610,16 @@ __global__ void cg_scalars_alpha(const double* part, int64_t nparts, double* sca
   }
 }
 
-// x += alpha p, r -= alpha ap; partials of r.r
-__global__ void cg_update(int64_t n, const double* scal, double* x, double* r, const double* p, const double* ap,
-                          double* part) {
-  const double a = scal[S_ALPHA];
+// x += alpha p, r -= alpha ap; partials of r.r (FP64)
+template <typename T>
+__global__ void cg_update(int64_t n, const double* scal, T* x, T* r, const T* p, const T* ap, double* part) {
+  const T a = (T)scal[S_ALPHA];
   double rr = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(a, p[i], x[i]);
-    const double ri = fma(-a, ap[i], r[i]);
+    const T ri = fma(-a, ap[i], r[i]);
     r[i] = ri;
-    rr += ri * ri;
+    rr += (double)ri * (double)ri;
   }
   block_store_sum(rr, part + blockIdx.x);
 }
@@ -633,10 +636,38 @@ __global__ void cg_scalars_beta(const double* part, int64_t nparts, double* scal
 }
 
 // p = r + beta p
-__global__ void cg_direction(int64_t n, const double* scal, const double* r, double* p) {
-  const double b = scal[S_BETA];
+template <typename T>
+__global__ void cg_direction(int64_t n, const double* scal, const T* r, T* p) {
+  const T b = (T)scal[S_BETA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fma(b, p[i], r[i]);
+}
+
+// defect correction: r64 = b - ap64 with partials of r.r; r32 = r64 * scale;
+// x += scale * d32
+__global__ void mp_residual(int64_t n, const double* b, const double* ap, double* r, double* part) {
+  double rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - ap[i];
+    r[i] = ri;
+    rr += ri * ri;
+  }
+  block_store_sum(rr, part + blockIdx.x);
+}
+
+__global__ void mp_to_float(int64_t n, const double* r, double scale, float* r32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r32[i] = (float)(r[i] * scale);
+}
+
+__global__ void mp_correct(int64_t n, double scale, const float* d, double* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(scale, (double)d[i], x[i]);
+}
+
+__global__ void sum_to_scalar(const double* part, int64_t nparts, double* out) {
+  const double v = reduce_partials(part, nparts);
+  if (threadIdx.x == 0) *out = v;
 }
 
 int64_t apply_blocks(const dg_handle* h) {
@@ -819,10 +850,94 @@ void free_handle(dg_handle* h) {
   if (h->scal_host) cudaFreeHost(h->scal_host);
   cudaFree(h->stage_src);
   cudaFree(h->stage_dst);
+  cudaFree(h->xw);
+  cudaFree(h->bw);
   delete h;
 }
 
 }  // namespace
+
+// CG work vectors (n doubles each, used as T* for the handle's precision),
+// partial-sum buffer [vector partials | apply partials] and scalars.
+dg_status ensure_cg_work(dg_handle* h, bool with_extra) {
+  const int64_t n = h->n_dofs;
+  dg_status st;
+  if (!h->r) {
+    if ((st = dev_alloc(h, (void**)&h->r, sizeof(double) * n)) != DG_OK) return st;
+    if ((st = dev_alloc(h, (void**)&h->p, sizeof(double) * n)) != DG_OK) return st;
+    if ((st = dev_alloc(h, (void**)&h->ap, sizeof(double) * n)) != DG_OK) return st;
+    h->partial_len = 2 * kRedBlocks + apply_blocks(h);
+    if ((st = dev_alloc(h, (void**)&h->partial, sizeof(double) * h->partial_len)) != DG_OK) return st;
+    if ((st = dev_alloc(h, (void**)&h->scal, sizeof(double) * S_COUNT)) != DG_OK) return st;
+    DG_CUDA(h, cudaMallocHost((void**)&h->scal_host, sizeof(double) * S_COUNT));
+  }
+  if (with_extra && !h->xw) {
+    if ((st = dev_alloc(h, (void**)&h->xw, sizeof(double) * n)) != DG_OK) return st;
+    if ((st = dev_alloc(h, (void**)&h->bw, sizeof(double) * n)) != DG_OK) return st;
+  }
+  return DG_OK;
+}
+
+// Conjugate gradients for A x = b in the handle's precision T (vectors of T,
+// every reduction in FP64, fixed order).  x holds the initial guess, or is
+// set to zero when x_zero.  Stops when |r| <= rtol |b| or after max_it
+// iterations (DG_ERR_NOT_CONVERGED).  Each iteration: the apply with p.Ap in
+// its epilogue, the fused update x += alpha p, r -= alpha Ap with r.r, and
+// p = r + beta p; the scalars are read back once per iteration.
+template <typename T>
+dg_status run_cg(dg_handle* h, const T* b, T* x, bool x_zero, double rtol, int max_it, int* iters, double* rel_out,
+                 double* bnorm_out) {
+  const int64_t n = h->n_dofs;
+  cudaStream_t s = h->stream;
+  const int vb = (int)std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads);
+  const int64_t nblk = apply_blocks(h);
+  double* part_vec = h->partial;
+  double* part_apply = h->partial + 2 * kRedBlocks;
+  T* r = reinterpret_cast<T*>(h->r);
+  T* p = reinterpret_cast<T*>(h->p);
+  T* ap = reinterpret_cast<T*>(h->ap);
+  dg_status st;
+  if (x_zero) {
+    DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(T) * n, s));
+    cg_init<T><<<vb, kRedThreads, 0, s>>>(n, b, nullptr, r, p, part_vec);
+  } else {
+    if ((st = launch_apply(h, x, ap, nullptr)) != DG_OK) return st;
+    cg_init<T><<<vb, kRedThreads, 0, s>>>(n, b, ap, r, p, part_vec);
+  }
+  cg_scalars_init<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
+  DG_CUDA(h, cudaGetLastError());
+  DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  DG_CUDA(h, cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(h->scal_host[S_BB] > 0 ? h->scal_host[S_BB] : 1.0);
+  double rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
+  int it = 0;
+  st = DG_OK;
+  while (rel > rtol) {
+    if (it >= max_it) {
+      st = fail(h, DG_ERR_NOT_CONVERGED, "CG reached max_it");
+      break;
+    }
+    // p.Ap is fused into the apply epilogue (per-block partials)
+    if ((st = launch_apply(h, p, ap, part_apply)) != DG_OK) return st;
+    cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply, nblk, h->scal);
+    cg_update<T><<<vb, kRedThreads, 0, s>>>(n, h->scal, x, r, p, ap, part_vec);
+    cg_scalars_beta<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
+    cg_direction<T><<<vb, kRedThreads, 0, s>>>(n, h->scal, r, p);
+    DG_CUDA(h, cudaGetLastError());
+    DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+    DG_CUDA(h, cudaStreamSynchronize(s));
+    ++it;
+    if (h->scal_host[S_FLAG] != 0.0) {
+      st = fail(h, DG_ERR_BREAKDOWN, "CG breakdown: p.Ap <= 0 or non-finite scalar");
+      break;
+    }
+    rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
+  }
+  *iters = it;
+  *rel_out = rel;
+  *bnorm_out = bnorm;
+  return st;
+}
 
 // Used by dg_noalloc.cu: the apply launch with caller-provided per-block
 // partials of src . dst, after the same argument checks as dg_apply.
@@ -865,7 +980,16 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
     return fail(nullptr, DG_ERR_ARG, "Cartesian geometry needs the identity mapping");
   const int64_t nc = (int64_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
   const int k = degree + 1;
-  if (nc * k * k * k > (int64_t)1 << 40) return fail(nullptr, DG_ERR_ARG, "mesh too large");
+  if (nc >= ((int64_t)1 << 31) || nc * k * k * k > (int64_t)1 << 40)
+    return fail(nullptr, DG_ERR_ARG, "mesh too large (at most 2^31 - 1 cells)");
+  {
+    // face ids of each direction are 32-bit in the kernels
+    for (int d = 0; d < 3; ++d) {
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      if ((int64_t)(mesh->n[d] + 1) * mesh->n[t1] * mesh->n[t2] >= ((int64_t)1 << 31))
+        return fail(nullptr, DG_ERR_ARG, "mesh too large (faces per direction must stay below 2^31)");
+    }
+  }
 
   dg_handle* h = new (std::nothrow) dg_handle();
   if (!h) return fail(nullptr, DG_ERR_OOM, "host allocation failed");
@@ -987,54 +1111,86 @@ dg_status dg_cg_solve(dg_handle* h, const double* rhs, double* x, double rtol, i
   if (h->prec != DG_FP64) return fail(h, DG_ERR_UNSUPPORTED, "CG runs on FP64 handles");
   if (!rhs || !x) return fail(h, DG_ERR_ARG, "rhs or x is NULL");
   if (!(rtol > 0.0) || max_it < 0) return fail(h, DG_ERR_ARG, "rtol must be > 0 and max_it >= 0");
-  const int64_t n = h->n_dofs;
-  dg_status st;
-  const int64_t nblk = apply_blocks(h);
-  if (!h->r) {
-    if ((st = dev_alloc(h, (void**)&h->r, sizeof(double) * n)) != DG_OK) return st;
-    if ((st = dev_alloc(h, (void**)&h->p, sizeof(double) * n)) != DG_OK) return st;
-    if ((st = dev_alloc(h, (void**)&h->ap, sizeof(double) * n)) != DG_OK) return st;
-    h->partial_len = 2 * kRedBlocks + nblk;  // [vector partials | apply partials]
-    if ((st = dev_alloc(h, (void**)&h->partial, sizeof(double) * h->partial_len)) != DG_OK) return st;
-    if ((st = dev_alloc(h, (void**)&h->scal, sizeof(double) * S_COUNT)) != DG_OK) return st;
-    DG_CUDA(h, cudaMallocHost((void**)&h->scal_host, sizeof(double) * S_COUNT));
-  }
-  cudaStream_t s = h->stream;
-  const int vb = (int)std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads);
-  double* part_vec = h->partial;
-  double* part_apply = h->partial + 2 * kRedBlocks;
-  if ((st = launch_apply(h, x, h->ap, nullptr)) != DG_OK) return st;
-  cg_init<<<vb, kRedThreads, 0, s>>>(n, rhs, h->ap, h->r, h->p, part_vec);
-  cg_scalars_init<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
-  DG_CUDA(h, cudaGetLastError());
-  DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
-  DG_CUDA(h, cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(h->scal_host[S_BB] > 0 ? h->scal_host[S_BB] : 1.0);
-  double rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
+  dg_status st = ensure_cg_work(h, false);
+  if (st != DG_OK) return st;
+  double rel = 0.0, bn = 0.0;
   int it = 0;
-  st = DG_OK;
-  while (rel > rtol) {
-    if (it >= max_it) {
-      st = fail(h, DG_ERR_NOT_CONVERGED, "CG reached max_it");
-      break;
-    }
-    // p.Ap is fused into the apply epilogue (per-block partials)
-    if ((st = launch_apply(h, h->p, h->ap, part_apply)) != DG_OK) return st;
-    cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply, nblk, h->scal);
-    cg_update<<<vb, kRedThreads, 0, s>>>(n, h->scal, x, h->r, h->p, h->ap, part_vec);
-    cg_scalars_beta<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
-    cg_direction<<<vb, kRedThreads, 0, s>>>(n, h->scal, h->r, h->p);
-    DG_CUDA(h, cudaGetLastError());
-    DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
-    DG_CUDA(h, cudaStreamSynchronize(s));
-    ++it;
-    if (h->scal_host[S_FLAG] != 0.0) {
-      st = fail(h, DG_ERR_BREAKDOWN, "CG breakdown: p.Ap <= 0 or non-finite scalar");
-      break;
-    }
-    rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
-  }
+  st = run_cg<double>(h, rhs, x, false, rtol, max_it, &it, &rel, &bn);
   if (iters) *iters = it;
+  if (final_rel_res) *final_rel_res = rel;
+  return st;
+}
+
+dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, double* x, double rtol, int max_outer,
+                            double inner_rtol, int max_inner, int* outer_iters, int* inner_iters,
+                            double* final_rel_res) {
+  if (!h64 || !h32) return DG_ERR_ARG;
+  if (h64->op != DG_OP_SIPG || h32->op != DG_OP_SIPG)
+    return fail(h64, DG_ERR_UNSUPPORTED, "mixed-precision CG needs the symmetric SIPG operator");
+  if (h64->prec != DG_FP64 || h32->prec != DG_FP32)
+    return fail(h64, DG_ERR_ARG, "mixed-precision CG needs an FP64 handle and an FP32 handle");
+  if (memcmp(&h64->mesh, &h32->mesh, sizeof(dg_mesh)) != 0 || h64->degree != h32->degree ||
+      h64->geom != h32->geom || h64->opts.coeff != h32->opts.coeff ||
+      h64->opts.penalty_scale != h32->opts.penalty_scale)
+    return fail(h64, DG_ERR_ARG, "the FP64 and FP32 handles describe different operators");
+  if (!rhs || !x) return fail(h64, DG_ERR_ARG, "rhs or x is NULL");
+  if (!(rtol > 0.0) || !(inner_rtol > 0.0) || inner_rtol >= 1.0 || max_outer < 0 || max_inner < 1)
+    return fail(h64, DG_ERR_ARG, "need rtol > 0, 0 < inner_rtol < 1, max_outer >= 0, max_inner >= 1");
+  dg_status st = ensure_cg_work(h64, false);
+  if (st == DG_OK) st = ensure_cg_work(h32, true);
+  if (st != DG_OK) return st;
+  cudaStream_t saved = h32->stream;
+  h32->stream = h64->stream;  // one stream orders the whole solve
+  cudaStream_t s = h64->stream;
+  const int64_t n = h64->n_dofs;
+  const int vb = (int)std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads);
+  float* b32 = reinterpret_cast<float*>(h32->bw);
+  float* d32 = reinterpret_cast<float*>(h32->xw);
+  int outer = 0, inner_total = 0;
+  double rel = 0.0, bnorm = 1.0;
+  while (true) {
+    // outer FP64 residual r = b - A x and its norm; |b| on the first pass
+    if ((st = launch_apply(h64, x, h64->ap, nullptr)) != DG_OK) break;
+    cg_init<double><<<vb, kRedThreads, 0, s>>>(n, rhs, h64->ap, h64->r, h64->p, h64->partial);
+    cg_scalars_init<<<1, kRedThreads, 0, s>>>(h64->partial, vb, h64->scal);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h64->scal_host, h64->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_fail(h64, e, "mixed-precision outer residual");
+      break;
+    }
+    const double rr = h64->scal_host[S_RR];
+    if (outer == 0) bnorm = std::sqrt(h64->scal_host[S_BB] > 0 ? h64->scal_host[S_BB] : 1.0);
+    rel = std::sqrt(rr) / bnorm;
+    if (!std::isfinite(rel)) {
+      st = fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG: non-finite residual");
+      break;
+    }
+    if (rel <= rtol) break;
+    if (outer >= max_outer) {
+      st = fail(h64, DG_ERR_NOT_CONVERGED, "mixed-precision CG reached max_outer");
+      break;
+    }
+    // inner FP32 CG on the normalized defect A d = r / |r|, from d = 0
+    const double rn = std::sqrt(rr);
+    mp_to_float<<<vb, kRedThreads, 0, s>>>(n, h64->r, 1.0 / rn, b32);
+    int it = 0;
+    double irel = 0.0, ib = 0.0;
+    st = run_cg<float>(h32, b32, d32, true, inner_rtol, max_inner, &it, &irel, &ib);
+    inner_total += it;
+    if (st == DG_ERR_NOT_CONVERGED) st = DG_OK;  // a partial correction still reduces the defect
+    if (st != DG_OK) {
+      h64->err = h32->err;
+      break;
+    }
+    mp_correct<<<vb, kRedThreads, 0, s>>>(n, rn, d32, x);
+    ++outer;
+  }
+  h32->stream = saved;
+  if (outer_iters) *outer_iters = outer;
+  if (inner_iters) *inner_iters = inner_total;
   if (final_rel_res) *final_rel_res = rel;
   return st;
 }

@@ -155,6 +155,39 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
     }
   }
 
+  int ijk[3];
+  {
+    // cell counts stay below 2^31 (checked at set-up): 32-bit division
+    const unsigned c = (unsigned)(active ? cell : cell0);
+    const unsigned q = c / (unsigned)gm.n[0];
+    ijk[0] = (int)(c - q * (unsigned)gm.n[0]);
+    ijk[1] = (int)(q % (unsigned)gm.n[1]);
+    ijk[2] = (int)(q / (unsigned)gm.n[1]);
+  }
+  // ... and of the six faces' geometry of each cell (read in phase 3)
+  if (GEO != GEO_CART && active) {
+    constexpr int NFA = OP == OP_SIPG ? 7 : 1;
+    constexpr int LPS = (K2 * (int)sizeof(T) + 127) / 128 + 1;  // lines per face segment
+    for (int t = ln; t < 6 * NFA * LPS; t += K2) {
+      const int face = t / (NFA * LPS), a = (t / LPS) % NFA, l = t % LPS;
+      const int d = face >> 1, sd = face & 1;
+      // selects instead of indexing ijk / n by d keep everything in registers
+      const int id = d == 0 ? ijk[0] : d == 1 ? ijk[1] : ijk[2];
+      const int it1 = d == 0 ? ijk[1] : ijk[0], it2 = d == 2 ? ijk[1] : ijk[2];
+      const int nd = d == 0 ? gm.n[0] : d == 1 ? gm.n[1] : gm.n[2];
+      const int nt1 = d == 0 ? gm.n[1] : gm.n[0];
+      const int Pd = d == 0 ? gm.P[0] : d == 1 ? gm.P[1] : gm.P[2];
+      const T* fbase = d == 0 ? gm.face[0] : d == 1 ? gm.face[1] : gm.face[2];
+      const int64_t nfqd = d == 0 ? gm.nfq[0] : d == 1 ? gm.nfq[1] : gm.nfq[2];
+      int pos = id + sd;
+      if (gm.periodic && pos == nd) pos = 0;
+      const int64_t fidp = (int64_t)(pos + Pd * (it1 + nt1 * it2));
+      const char* seg = reinterpret_cast<const char*>(fbase + a * nfqd + fidp * K2);
+      const char* p = seg + l * 128;
+      if (p < seg + K2 * (int)sizeof(T)) prefetch_l2(p);
+    }
+  }
+
   if (tid < 2 * K) sE[tid] = tb.E[tid / K][tid % K];
   if (tid < K) sW[tid] = tb.W[tid];
   if (!kLineFaces)
@@ -162,14 +195,6 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
       sS[i] = tb.S[i];
       sD[i] = tb.D[i];
     }
-
-  int ijk[3];
-  {
-    const int64_t c = active ? cell : cell0;
-    ijk[0] = (int)(c % gm.n[0]);
-    ijk[1] = (int)((c / gm.n[0]) % gm.n[1]);
-    ijk[2] = (int)(c / ((int64_t)gm.n[0] * gm.n[1]));
-  }
 
   // 1. gather (coalesced over the block's contiguous range)
   {
@@ -208,12 +233,12 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
       int pos = ijk[d] + s;
       bool inside = j[d] >= 0 && j[d] < gm.n[d];
       if (!inside && gm.periodic) {
-        j[d] = (j[d] + gm.n[d]) % gm.n[d];
+        j[d] = j[d] < 0 ? gm.n[d] - 1 : 0;
         inside = true;
       }
-      if (gm.periodic) pos = pos % gm.n[d];
-      nbc[s] = inside ? j[0] + (int64_t)gm.n[0] * (j[1] + (int64_t)gm.n[1] * j[2]) : -1;
-      fid[s] = pos + (int64_t)gm.P[d] * (ijk[t1] + (int64_t)gm.n[t1] * ijk[t2]);
+      if (gm.periodic && pos == gm.n[d]) pos = 0;
+      nbc[s] = inside ? (int64_t)(j[0] + gm.n[0] * (j[1] + gm.n[1] * j[2])) : -1;
+      fid[s] = (int64_t)(pos + gm.P[d] * (ijk[t1] + gm.n[t1] * ijk[t2]));
     }
     T* nba = NBa + lc * 2 * NBA * K2;  // [2][NBA][K2]
     T* nbb = NBb + lc * 2 * NBB * K2;  // [2][NBB][K2]
@@ -249,7 +274,7 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
       constexpr int NB1 = (OP == OP_SIPG) ? (GEO == GEO_CART ? 2 : 3) : 1;
       for (int task = ln; task < 2 * NB1 * K; task += K2) {
         const int s = task / (NB1 * K), f = (task / K) % NB1, j = task % K;
-        if (nbc[s] < 0) continue;
+        if ((s ? nbc[1] : nbc[0]) < 0) continue;
         const T* in = nba + (s * NBA + (f == 1 ? 1 : 0)) * K2;
         T* out = nbb + (s * NBB + f) * K2;
         if (OP == OP_SIPG && f == 2)
@@ -264,7 +289,7 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
     // outward normal, -j_n(nb) . grad_xi u_nb, at each face point
     if (active && ln < 2 * K) {
       const int s = ln / K, i = ln % K;
-      if (nbc[s] >= 0) {
+      if ((s ? nbc[1] : nbc[0]) >= 0) {
         const T* in = nbb + s * NBB * K2;
         T* out = nba + s * NBA * K2;
         T x0[K], val[K];
@@ -298,7 +323,7 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
 #pragma unroll
             for (int jj = 0; jj < K; ++jj) x2[jj] = in[2 * K2 + i + K * jj];
             const int64_t nfq = gm.nfq[d];
-            const T* fp = gm.face[d] + fid[s] * K2 + i;
+            const T* fp = gm.face[d] + (s ? fid[1] : fid[0]) * K2 + i;
 #pragma unroll
             for (int q = 0; q < K; ++q) {
               T dt1 = T(0), dt2 = T(0);
@@ -471,116 +496,289 @@ __global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_c
     __syncthreads();
   }
 
-  // 4. quadrature-point operation and injection of the face test coefficients
-  if (active) {
-    const T e0a = sE[la], e1a = sE[K + la], e0b = sE[lb], e1b = sE[K + lb];
-    const T* ftc = FT + lc * 6 * FTF * K2;
+  if (kLineFaces) {
+    // 4. (z-line owner) quadrature-point operation and the z faces' test
+    // coefficients, injected along the z line by the thread that formed them
+    if (active) {
+      const T* fz = FT + ((lc * 3 + 2) * 2) * FTF * K2 + ln;
+      T fa[FTF], fb[FTF];
 #pragma unroll
-    for (int z = 0; z < K; ++z) {
-      const int pt = la + K * (lb + K * z);
-      T fv, fg0 = T(0), fg1 = T(0), fg2 = T(0);
-      {
-        // x faces: along = la, proj = lb + K z; y faces: along = lb, proj = la + K z;
-        // z faces: along = z, proj = la + K lb
-        const T* fx0 = ftc + (0 * 2 + 0) * FTF * K2 + lb + K * z;
-        const T* fx1 = ftc + (0 * 2 + 1) * FTF * K2 + lb + K * z;
-        const T* fy0 = ftc + (1 * 2 + 0) * FTF * K2 + la + K * z;
-        const T* fy1 = ftc + (1 * 2 + 1) * FTF * K2 + la + K * z;
-        const T* fz0 = ftc + (2 * 2 + 0) * FTF * K2 + la + K * lb;
-        const T* fz1 = ftc + (2 * 2 + 1) * FTF * K2 + la + K * lb;
-        const T ez0 = tb.E[0][z], ez1 = tb.E[1][z];
-        fv = e0a * fx0[0] + e1a * fx1[0] + e0b * fy0[0] + e1b * fy1[0] + ez0 * fz0[0] + ez1 * fz1[0];
+      for (int f = 0; f < FTF; ++f) {
+        fa[f] = fz[f * K2];
+        fb[f] = fz[(FTF + f) * K2];
+      }
+#pragma unroll
+      for (int z = 0; z < K; ++z) {
+        const int pt = la + K * (lb + K * z);
+        const T e0 = tb.E[0][z], e1 = tb.E[1][z];
+        T t0, t1, t2;
+        const int64_t qi = cell * K3 + pt;
         if (OP == OP_SIPG) {
-          fg0 = e0a * fx0[K2] + e1a * fx1[K2] + e0b * fy0[K2] + e1b * fy1[K2] + ez0 * fz0[K2] + ez1 * fz1[K2];
-          fg1 = e0a * fx0[2 * K2] + e1a * fx1[2 * K2] + e0b * fy0[2 * K2] + e1b * fy1[2 * K2] +
-                ez0 * fz0[2 * K2] + ez1 * fz1[2 * K2];
-          fg2 = e0a * fx0[3 * K2] + e1a * fx1[3 * K2] + e0b * fy0[3 * K2] + e1b * fy1[3 * K2] +
-                ez0 * fz0[3 * K2] + ez1 * fz1[3 * K2];
-        }
-      }
-      T t0, t1, t2;
-      const int64_t qi = cell * K3 + pt;
-      if (OP == OP_SIPG) {
-        const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
-        if (GEO == GEO_CART) {
-          T w = sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
-          if (gm.kq) w *= gm.kq[ijk[0] * K + la];
-          t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
-          t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
-          t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
-        } else if (GEO == GEO_FULL) {
-          const T* cp = gm.cell + qi;
-          const int64_t n = gm.ncq;
-          T J[9];
-#pragma unroll
-          for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-          const T jw = cp[9 * n];
-          // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
-          const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
-          const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
-          const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
-          t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
-          t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
-          t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+          const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
+          if (GEO == GEO_CART) {
+            T w = sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
+            if (gm.kq) w *= gm.kq[ijk[0] * K + la];
+            t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+            t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+            t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+          } else if (GEO == GEO_FULL) {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            T J[9];
+  #pragma unroll
+            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+            const T jw = cp[9 * n];
+            // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
+            const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
+            const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
+            const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+            t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
+            t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
+            t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+          } else {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
+            t0 = a00 * g0 + a01 * g1 + a02 * g2;
+            t1 = a01 * g0 + a11 * g1 + a12 * g2;
+            t2 = a02 * g0 + a12 * g1 + a22 * g2;
+          }
         } else {
-          const T* cp = gm.cell + qi;
-          const int64_t n = gm.ncq;
-          const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
-          t0 = a00 * g0 + a01 * g1 + a02 * g2;
-          t1 = a01 * g0 + a11 * g1 + a12 * g2;
-          t2 = a02 * g0 + a12 * g1 + a22 * g2;
+          const T uq = Uc[pt];
+          T b0, b1, b2;
+          if (GEO == GEO_CART) {
+            const T w = -sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
+            b0 = w * gm.cart_jinv[0] * gm.vel[0];
+            b1 = w * gm.cart_jinv[1] * gm.vel[1];
+            b2 = w * gm.cart_jinv[2] * gm.vel[2];
+          } else if (GEO == GEO_FULL) {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            T J[9];
+  #pragma unroll
+            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+            const T jw = -cp[9 * n];
+            b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
+            b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
+            b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+          } else {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            b0 = cp[0];
+            b1 = cp[n];
+            b2 = cp[2 * n];
+          }
+          t0 = b0 * uq;
+          t1 = b1 * uq;
+          t2 = b2 * uq;
         }
-      } else {
-        const T uq = Uc[pt];
-        T b0, b1, b2;
-        if (GEO == GEO_CART) {
-          const T w = -sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
-          b0 = w * gm.cart_jinv[0] * gm.vel[0];
-          b1 = w * gm.cart_jinv[1] * gm.vel[1];
-          b2 = w * gm.cart_jinv[2] * gm.vel[2];
-        } else if (GEO == GEO_FULL) {
-          const T* cp = gm.cell + qi;
-          const int64_t n = gm.ncq;
-          T J[9];
-#pragma unroll
-          for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-          const T jw = -cp[9 * n];
-          b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
-          b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
-          b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
-        } else {
-          const T* cp = gm.cell + qi;
-          const int64_t n = gm.ncq;
-          b0 = cp[0];
-          b1 = cp[n];
-          b2 = cp[2 * n];
+        if (OP == OP_SIPG) {
+          t0 += e0 * fa[1] + e1 * fb[1];
+          t1 += e0 * fa[2] + e1 * fb[2];
+          t2 += e0 * fa[3] + e1 * fb[3];
         }
-        t0 = b0 * uq;
-        t1 = b1 * uq;
-        t2 = b2 * uq;
+        G0[pt] = t0;
+        G1[pt] = t1;
+        G2[pt] = t2;
+        Uc[pt] = e0 * fa[0] + e1 * fb[0];
       }
-      G0[pt] = t0 + fg0;
-      G1[pt] = t1 + fg1;
-      G2[pt] = t2 + fg2;
-      Uc[pt] = fv;
     }
-  }
-  __syncthreads();
+    __syncthreads();
+    // (y-line owner) the y faces' contributions to the x and z gradient fields
+    if (OP == OP_SIPG) {
+      if (active) {
+        const T* fy = FT + ((lc * 3 + 1) * 2) * FTF * K2 + ln;
+        const T a0 = fy[K2], a2 = fy[3 * K2], b0 = fy[(FTF + 1) * K2], b2 = fy[(FTF + 3) * K2];
+#pragma unroll
+        for (int y = 0; y < K; ++y) {
+          const int pt = la + K * (y + K * lb);
+          const T e0 = tb.E[0][y], e1 = tb.E[1][y];
+          G0[pt] += e0 * a0 + e1 * b0;
+          G2[pt] += e0 * a2 + e1 * b2;
+        }
+      }
+      __syncthreads();
+    }
+    // 5. integration.  x-line owner: V += D^T (T_x + x-face part) + x-face value
+    // part; the x faces' contributions to T_y, T_z are added along the line
+    if (active) {
+      const T* fx = FT + ((lc * 3 + 0) * 2) * FTF * K2 + ln;
+      T fa[FTF], fb[FTF];
+#pragma unroll
+      for (int f = 0; f < FTF; ++f) {
+        fa[f] = fx[f * K2];
+        fb[f] = fx[(FTF + f) * K2];
+      }
+      const int base = K * (la + K * lb);
+      T t[K], v[K];
+#pragma unroll
+      for (int x = 0; x < K; ++x) {
+        const T e0 = tb.E[0][x], e1 = tb.E[1][x];
+        t[x] = G0[base + x];
+        v[x] = Uc[base + x] + e0 * fa[0] + e1 * fb[0];
+        if (OP == OP_SIPG) {
+          t[x] += e0 * fa[1] + e1 * fb[1];
+          G1[base + x] += e0 * fa[2] + e1 * fb[2];
+          G2[base + x] += e0 * fa[3] + e1 * fb[3];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        T acc = v[j];
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc = fma(tb.D[q * K + j], t[q], acc);
+        Uc[base + j] = acc;
+      }
+    }
+    __syncthreads();
+    // y-line owner: V += D^T (T_y + y-face part) + y-face value part
+    if (active) {
+      const T* fy = FT + ((lc * 3 + 1) * 2) * FTF * K2 + ln;
+      const T va = fy[0], vb = fy[FTF * K2];
+      T ga = T(0), gb = T(0);
+      if (OP == OP_SIPG) {
+        ga = fy[2 * K2];
+        gb = fy[(FTF + 2) * K2];
+      }
+      const int base = la + K2 * lb;
+      T t[K], v[K];
+#pragma unroll
+      for (int y = 0; y < K; ++y) {
+        const T e0 = tb.E[0][y], e1 = tb.E[1][y];
+        t[y] = G1[base + K * y] + e0 * ga + e1 * gb;
+        v[y] = Uc[base + K * y] + e0 * va + e1 * vb;
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        T acc = v[j];
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc = fma(tb.D[q * K + j], t[q], acc);
+        Uc[base + K * j] = acc;
+      }
+    }
+    __syncthreads();
+    // z-line owner: V += D^T T_z, then S^T along z, y, x
+    if (active) {
+      line_add_transposed<K>(tb.D, G2, Uc, la + K * lb, K2);
+      line_apply<K, true>(tb.S, Uc, la + K * lb, K2);
+    }
+    __syncthreads();
+    if (active) line_apply<K, true>(tb.S, Uc, la + K2 * lb, K);
+    __syncthreads();
+    if (active) line_apply<K, true>(tb.S, Uc, K * (la + K * lb), 1);
+    __syncthreads();
+  } else {
+    // 4. quadrature-point operation and injection of the face test coefficients
+    if (active) {
+      const T e0a = sE[la], e1a = sE[K + la], e0b = sE[lb], e1b = sE[K + lb];
+      const T* ftc = FT + lc * 6 * FTF * K2;
+  #pragma unroll
+      for (int z = 0; z < K; ++z) {
+        const int pt = la + K * (lb + K * z);
+        T fv, fg0 = T(0), fg1 = T(0), fg2 = T(0);
+        {
+          // x faces: along = la, proj = lb + K z; y faces: along = lb, proj = la + K z;
+          // z faces: along = z, proj = la + K lb
+          const T* fx0 = ftc + (0 * 2 + 0) * FTF * K2 + lb + K * z;
+          const T* fx1 = ftc + (0 * 2 + 1) * FTF * K2 + lb + K * z;
+          const T* fy0 = ftc + (1 * 2 + 0) * FTF * K2 + la + K * z;
+          const T* fy1 = ftc + (1 * 2 + 1) * FTF * K2 + la + K * z;
+          const T* fz0 = ftc + (2 * 2 + 0) * FTF * K2 + la + K * lb;
+          const T* fz1 = ftc + (2 * 2 + 1) * FTF * K2 + la + K * lb;
+          const T ez0 = tb.E[0][z], ez1 = tb.E[1][z];
+          fv = e0a * fx0[0] + e1a * fx1[0] + e0b * fy0[0] + e1b * fy1[0] + ez0 * fz0[0] + ez1 * fz1[0];
+          if (OP == OP_SIPG) {
+            fg0 = e0a * fx0[K2] + e1a * fx1[K2] + e0b * fy0[K2] + e1b * fy1[K2] + ez0 * fz0[K2] + ez1 * fz1[K2];
+            fg1 = e0a * fx0[2 * K2] + e1a * fx1[2 * K2] + e0b * fy0[2 * K2] + e1b * fy1[2 * K2] +
+                  ez0 * fz0[2 * K2] + ez1 * fz1[2 * K2];
+            fg2 = e0a * fx0[3 * K2] + e1a * fx1[3 * K2] + e0b * fy0[3 * K2] + e1b * fy1[3 * K2] +
+                  ez0 * fz0[3 * K2] + ez1 * fz1[3 * K2];
+          }
+        }
+        T t0, t1, t2;
+        const int64_t qi = cell * K3 + pt;
+        if (OP == OP_SIPG) {
+          const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
+          if (GEO == GEO_CART) {
+            T w = sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
+            if (gm.kq) w *= gm.kq[ijk[0] * K + la];
+            t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+            t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+            t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+          } else if (GEO == GEO_FULL) {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            T J[9];
+  #pragma unroll
+            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+            const T jw = cp[9 * n];
+            // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
+            const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
+            const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
+            const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+            t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
+            t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
+            t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+          } else {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
+            t0 = a00 * g0 + a01 * g1 + a02 * g2;
+            t1 = a01 * g0 + a11 * g1 + a12 * g2;
+            t2 = a02 * g0 + a12 * g1 + a22 * g2;
+          }
+        } else {
+          const T uq = Uc[pt];
+          T b0, b1, b2;
+          if (GEO == GEO_CART) {
+            const T w = -sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
+            b0 = w * gm.cart_jinv[0] * gm.vel[0];
+            b1 = w * gm.cart_jinv[1] * gm.vel[1];
+            b2 = w * gm.cart_jinv[2] * gm.vel[2];
+          } else if (GEO == GEO_FULL) {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            T J[9];
+  #pragma unroll
+            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+            const T jw = -cp[9 * n];
+            b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
+            b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
+            b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+          } else {
+            const T* cp = gm.cell + qi;
+            const int64_t n = gm.ncq;
+            b0 = cp[0];
+            b1 = cp[n];
+            b2 = cp[2 * n];
+          }
+          t0 = b0 * uq;
+          t1 = b1 * uq;
+          t2 = b2 * uq;
+        }
+        G0[pt] = t0 + fg0;
+        G1[pt] = t1 + fg1;
+        G2[pt] = t2 + fg2;
+        Uc[pt] = fv;
+      }
+    }
+    __syncthreads();
 
-  // 5. integration: V += D^T T_x, D^T T_y, D^T T_z, then S^T along z, y, x
-  if (active) line_add_transposed<K>(tb.D, G0, Uc, K * (la + K * lb), 1);
-  __syncthreads();
-  if (active) line_add_transposed<K>(tb.D, G1, Uc, la + K2 * lb, K);
-  __syncthreads();
-  if (active) {
-    line_add_transposed<K>(tb.D, G2, Uc, la + K * lb, K2);
-    line_apply<K, true>(tb.S, Uc, la + K * lb, K2);
+    // 5. integration: V += D^T T_x, D^T T_y, D^T T_z, then S^T along z, y, x
+    if (active) line_add_transposed<K>(tb.D, G0, Uc, K * (la + K * lb), 1);
+    __syncthreads();
+    if (active) line_add_transposed<K>(tb.D, G1, Uc, la + K2 * lb, K);
+    __syncthreads();
+    if (active) {
+      line_add_transposed<K>(tb.D, G2, Uc, la + K * lb, K2);
+      line_apply<K, true>(tb.S, Uc, la + K * lb, K2);
+    }
+    __syncthreads();
+    if (active) line_apply<K, true>(tb.S, Uc, la + K2 * lb, K);
+    __syncthreads();
+    if (active) line_apply<K, true>(tb.S, Uc, K * (la + K * lb), 1);
+    __syncthreads();
   }
-  __syncthreads();
-  if (active) line_apply<K, true>(tb.S, Uc, la + K2 * lb, K);
-  __syncthreads();
-  if (active) line_apply<K, true>(tb.S, Uc, K * (la + K * lb), 1);
-  __syncthreads();
 
   // write (set) the block's contiguous range; optional src . dst partial
   {

@@ -1,0 +1,64 @@
+"""Solvers through the C ABI: plain FP64 CG and mixed-precision defect
+correction (FP32 CG inside, FP64 residual/update/inner products), checked
+against the FP64 oracle's assembled matrix and against each other."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1711_03590_gb300 as dgp  # noqa: E402
+
+
+def _ops(n, p, geom="full", mapping=1, coeff=1):
+    o64 = dgp.Operator(n, p, geom=geom, prec="fp64", mapping=mapping, coeff=coeff)
+    o32 = dgp.Operator(n, p, geom=geom, prec="fp32", mapping=mapping, coeff=coeff)
+    return o64, o32
+
+
+@pytest.mark.parametrize("n,p", [((5, 4, 6), 3), ((4, 4, 4), 5)])
+def test_mixed_precision_reaches_fp64_accuracy(n, p):
+    dgp.build()
+    mesh = dict(n=n, periodic=False, mapping=1, amplitude=0.1)
+    A = oracle.assemble(mesh, p, dict(op="sipg", coeff=1))
+    b = oracle.rhs(mesh, p, 1)
+    o64, o32 = _ops(n, p)
+    rhs = torch.tensor(b, device="cuda")
+    x64, it64, rr64, st = o64.cg(rhs, rtol=1e-10, max_it=20000)
+    assert st == dgp.DG_OK
+    xm = torch.zeros_like(rhs)
+    st, outer, inner, rrm = dgp.dg_cg_solve_mixed(o64.handle, o32.handle, rhs.data_ptr(), xm.data_ptr(), 1e-10)
+    assert st == dgp.DG_OK and rrm <= 1e-10 and outer >= 2
+    xs = xm.cpu().numpy()
+    # residual of the mixed solution measured with the oracle's FP64 matrix
+    assert np.linalg.norm(b - A @ xs) <= 3e-10 * np.linalg.norm(b)
+    x64n = x64.cpu().numpy()
+    assert np.linalg.norm(xs - x64n) <= 1e-7 * np.linalg.norm(x64n)
+    e_m, e_64 = oracle.l2_error(mesh, p, xs), oracle.l2_error(mesh, p, x64n)
+    assert abs(e_m - e_64) <= 1e-6 * e_64
+    # reproducible bit for bit
+    xm2 = torch.zeros_like(rhs)
+    st2, outer2, inner2, _ = dgp.dg_cg_solve_mixed(o64.handle, o32.handle, rhs.data_ptr(), xm2.data_ptr(), 1e-10)
+    assert (outer2, inner2) == (outer, inner) and torch.equal(xm, xm2)
+
+
+def test_mixed_precision_argument_checks():
+    dgp.build()
+    o64, o32 = _ops((3, 3, 3), 2)
+    other = dgp.Operator((3, 3, 4), 2, geom="full", prec="fp32", mapping=1, coeff=1)
+    rhs = o64.rhs(1)
+    x = torch.zeros_like(rhs)
+    with pytest.raises(dgp.DGError) as e:
+        dgp.dg_cg_solve_mixed(o64.handle, other.handle, rhs.data_ptr(), x.data_ptr(), 1e-10)
+    assert e.value.status == dgp.DG_ERR_ARG
+    with pytest.raises(dgp.DGError) as e:
+        dgp.dg_cg_solve_mixed(o32.handle, o64.handle, rhs.data_ptr(), x.data_ptr(), 1e-10)
+    assert e.value.status == dgp.DG_ERR_ARG
+    st, outer, inner, rr = dgp.dg_cg_solve_mixed(o64.handle, o32.handle, rhs.data_ptr(), x.data_ptr(), 1e-12,
+                                                 max_outer=1, raise_on_error=False)
+    assert st == dgp.DG_ERR_NOT_CONVERGED and outer == 1
