@@ -134,6 +134,18 @@ dg_status dg_info(const dg_handle *h, dg_info_t *info);
 /* Change the stream used by later calls. */
 dg_status dg_set_stream(dg_handle *h, void *stream);
 
+/* Tile shape of the apply kernel: cells per CUDA block (k^2 threads each),
+ * 1 .. floor(256 / k^2); 0 restores the default (the maximum).  Results do
+ * not depend on it (each cell's arithmetic is the same).  Synchronous. */
+dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
+
+/* Autotuner: times the apply for every candidate cells-per-block value on
+ * the handle's stream (CUDA events, warm-up first) and keeps the fastest.
+ * Uses handle-owned staging buffers (allocated on first use).  best_cpb and
+ * best_ms (may be NULL) receive the choice and its time per apply.
+ * Synchronous. */
+dg_status dg_autotune(dg_handle *h, int *best_cpb, double *best_ms);
+
 /* dst = A src on the device (Algorithm 1 steps (ii)-(iv); one kernel launch:
  * each cell computes its cell integral and its six face integrals tested on
  * itself and sets its dst entries).  src and dst: device pointers to n_dofs

@@ -45,7 +45,8 @@ OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
 PRECS = {"fp64": DG_FP64, "fp32": DG_FP32}
 
 EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
-            "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc"]
+            "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
+            "dg_set_cells_per_block", "dg_autotune"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -100,6 +101,8 @@ def load_library(path=None):
     L.dg_cg_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_double)]
     L.dg_apply_dot_noalloc.argtypes = [_vp, _vp, _vp, _vp]
+    L.dg_set_cells_per_block.argtypes = [_vp, ctypes.c_int]
+    L.dg_autotune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.dg_cg_solve_mixed.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_double)]
@@ -202,6 +205,18 @@ def dg_cg_solve_mixed(h64, h32, rhs_ptr, x_ptr, rtol, max_outer=50, inner_rtol=1
     return st, oi.value, ii.value, rr.value
 
 
+def dg_set_cells_per_block(handle, cells_per_block):
+    _check(load_library().dg_set_cells_per_block(_vp(handle), int(cells_per_block)), handle)
+
+
+def dg_autotune(handle):
+    """Returns (cells per block chosen, ms per apply)."""
+    c = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(load_library().dg_autotune(_vp(handle), ctypes.byref(c), ctypes.byref(ms)), handle)
+    return c.value, ms.value
+
+
 def dg_destroy(handle):
     if handle:
         load_library().dg_destroy(_vp(handle))
@@ -271,6 +286,12 @@ class Operator:
 
     def info(self):
         return dg_info(self.handle)
+
+    def set_cells_per_block(self, cpb):
+        dg_set_cells_per_block(self.handle, cpb)
+
+    def autotune(self):
+        return dg_autotune(self.handle)
 
     def close(self):
         if self.handle:

@@ -228,6 +228,7 @@ struct dg_handle {
   dg_mesh mesh;
   dg_opts opts;
   int degree, k, geom, prec, op;
+  int cpb;  // cells per block of the apply kernel
   int64_t n_cells, n_dofs;
   cudaStream_t stream;
   Tables64 t64;
@@ -671,7 +672,7 @@ __global__ void sum_to_scalar(const double* part, int64_t nparts, double* out) {
 }
 
 int64_t apply_blocks(const dg_handle* h) {
-  const int C = dg::cells_per_block(h->k);
+  const int C = h->cpb;
   return (h->n_cells + C - 1) / C;
 }
 
@@ -687,6 +688,7 @@ dg_status launch_apply(dg_handle* h, const void* src, void* dst, double* dot_par
   L.geometry = h->prec == DG_FP64 ? (const void*)&h->geod : (const void*)&h->geof;
   L.dot_partial = dot_partial;
   L.stream = h->stream;
+  L.cpb = h->cpb;
   cudaError_t e;
   switch (h->k) {
     case 2: e = dg::launch_apply_k2(L, h->n_cells); break;
@@ -866,7 +868,7 @@ dg_status ensure_cg_work(dg_handle* h, bool with_extra) {
     if ((st = dev_alloc(h, (void**)&h->r, sizeof(double) * n)) != DG_OK) return st;
     if ((st = dev_alloc(h, (void**)&h->p, sizeof(double) * n)) != DG_OK) return st;
     if ((st = dev_alloc(h, (void**)&h->ap, sizeof(double) * n)) != DG_OK) return st;
-    h->partial_len = 2 * kRedBlocks + apply_blocks(h);
+    h->partial_len = 2 * kRedBlocks + h->n_cells;  // apply partials for any block size
     if ((st = dev_alloc(h, (void**)&h->partial, sizeof(double) * h->partial_len)) != DG_OK) return st;
     if ((st = dev_alloc(h, (void**)&h->scal, sizeof(double) * S_COUNT)) != DG_OK) return st;
     DG_CUDA(h, cudaMallocHost((void**)&h->scal_host, sizeof(double) * S_COUNT));
@@ -1002,6 +1004,7 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   h->op = opts->op;
   h->n_cells = nc;
   h->n_dofs = nc * k * k * k;
+  h->cpb = dg::cells_per_block(k);
   h->stream = static_cast<cudaStream_t>(stream);
   build_tables(k, h->t64);
   h->tabd = cast_tables<double>(k, h->t64);
@@ -1036,9 +1039,9 @@ dg_status dg_info(const dg_handle* h, dg_info_t* info) {
   info->op = h->op;
   info->cell_geometry_bytes = h->cell_bytes;
   info->face_geometry_bytes = h->face_bytes;
-  info->cells_per_block = dg::cells_per_block(h->k);
-  info->threads_per_block = info->cells_per_block * h->k * h->k;
-  info->shared_bytes_per_block = dg::smem_bytes_per_block(h->k, h->op, h->prec == DG_FP64 ? 8 : 4);
+  info->cells_per_block = h->cpb;
+  info->threads_per_block = h->cpb * h->k * h->k;
+  info->shared_bytes_per_block = dg::smem_bytes_per_block(h->k, h->op, h->prec == DG_FP64 ? 8 : 4, h->cpb);
   info->blocks = apply_blocks(h);
   return DG_OK;
 }
@@ -1192,6 +1195,61 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
   if (outer_iters) *outer_iters = outer;
   if (inner_iters) *inner_iters = inner_total;
   if (final_rel_res) *final_rel_res = rel;
+  return st;
+}
+
+dg_status dg_set_cells_per_block(dg_handle* h, int cpb) {
+  if (!h) return DG_ERR_ARG;
+  if (cpb == 0) cpb = dg::cells_per_block(h->k);
+  if (cpb < 1 || cpb > dg::cells_per_block(h->k))
+    return fail(h, DG_ERR_ARG, "cells per block must be in 1.." + std::to_string(dg::cells_per_block(h->k)));
+  h->cpb = cpb;
+  return DG_OK;
+}
+
+dg_status dg_autotune(dg_handle* h, int* best_cpb, double* best_ms) {
+  if (!h) return DG_ERR_ARG;
+  const size_t bytes = (size_t)h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  dg_status st;
+  if (!h->stage_src && (st = dev_alloc(h, &h->stage_src, bytes)) != DG_OK) return st;
+  if (!h->stage_dst && (st = dev_alloc(h, &h->stage_dst, bytes)) != DG_OK) return st;
+  DG_CUDA(h, cudaMemsetAsync(h->stage_src, 0, bytes, h->stream));
+  cudaEvent_t e0, e1;
+  DG_CUDA(h, cudaEventCreate(&e0));
+  DG_CUDA(h, cudaEventCreate(&e1));
+  const int cands[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64};
+  const int saved = h->cpb;
+  int best = saved;
+  float best_t = 1e30f;
+  st = DG_OK;
+  for (int c : cands) {
+    if (c > dg::cells_per_block(h->k)) break;
+    h->cpb = c;
+    for (int w = 0; w < 2 && st == DG_OK; ++w) st = launch_apply(h, h->stage_src, h->stage_dst, nullptr);
+    if (st != DG_OK) break;
+    cudaEventRecord(e0, h->stream);
+    const int reps = 5;
+    for (int r = 0; r < reps && st == DG_OK; ++r) st = launch_apply(h, h->stage_src, h->stage_dst, nullptr);
+    cudaEventRecord(e1, h->stream);
+    if (st != DG_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(h, e, "autotune timing");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_t) {
+      best_t = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->cpb = st == DG_OK ? best : saved;
+  if (best_cpb) *best_cpb = h->cpb;
+  if (best_ms) *best_ms = best_t;
   return st;
 }
 

@@ -36,12 +36,12 @@ struct ApplyParams {
   const T* src;
   T* dst;
   double* dot_partial;
+  int C;  // cells per block
 };
 
 template <int K>
 struct Shape {
-  static constexpr int C = cells_per_block(K);
-  static constexpr int threads = C * K * K;
+  static constexpr int max_threads = cells_per_block(K) * K * K;
 };
 
 template <int K, int OP>
@@ -111,8 +111,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 
 template <int K, typename T, int GEO, int OP>
-__global__ void __launch_bounds__(Shape<K>::threads) apply_kernel(const __grid_constant__ ApplyParams<T> P) {
-  constexpr int K2 = K * K, K3 = K2 * K, C = Shape<K>::C;
+__global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __grid_constant__ ApplyParams<T> P) {
+  constexpr int K2 = K * K, K3 = K2 * K;
+  const int C = P.C;
   constexpr int NBA = Smem<K, OP>::NBA, NBB = Smem<K, OP>::NBB, FTF = Smem<K, OP>::FTF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3] u -> u at Gauss points -> test value field
@@ -812,18 +813,19 @@ cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
   P.src = static_cast<const T*>(L.src);
   P.dst = static_cast<T*>(L.dst);
   P.dot_partial = L.dot_partial;
-  constexpr int C = Shape<K>::C;
-  const int smem = smem_bytes_per_block(K, OP, (int)sizeof(T));
+  const int C = (L.cpb >= 1 && L.cpb <= cells_per_block(K)) ? L.cpb : cells_per_block(K);
+  P.C = C;
+  const int smem = smem_bytes_per_block(K, OP, (int)sizeof(T), C);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel<K, T, GEO, OP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<K, T, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes_per_block(K, OP, (int)sizeof(T), cells_per_block(K)));
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const int64_t grid = (n_cells + C - 1) / C;
   if (grid <= 0) return cudaSuccess;
-  apply_kernel<K, T, GEO, OP><<<(unsigned)grid, Shape<K>::threads, smem, L.stream>>>(P);
+  apply_kernel<K, T, GEO, OP><<<(unsigned)grid, C * K * K, smem, L.stream>>>(P);
   return cudaGetLastError();
 }
 

@@ -67,10 +67,13 @@ struct ApplyLaunch {
   const void* geometry;  // Geometry<T>*
   double* dot_partial;   // optional: per-block partial of src . dst (FP64)
   cudaStream_t stream;
+  int cpb;               // cells per block (1 .. cells_per_block(k))
 };
 
-// Cells per block of the apply kernel for k points per direction: about
-// 256 threads (k^2 per cell).
+// Largest number of cells per block of the apply kernel for k points per
+// direction (about 256 threads, k^2 per cell); also the default.  The block
+// size is a launch parameter: any value 1 .. cells_per_block(k) is valid and
+// the autotuner picks one per operator by timing.
 __host__ __device__ constexpr int cells_per_block(int k) {
   return k == 2 ? 64 : k == 3 ? 28 : k == 4 ? 16 : k == 5 ? 10 : k == 6 ? 7 : k == 7 ? 5 : k == 8 ? 4 : 3;
 }
@@ -83,8 +86,8 @@ __host__ __device__ constexpr int smem_scalars_per_cell(int k, int op) {
   return 4 * k * k * k + 2 * ((op == OP_SIPG ? 2 : 1) + (op == OP_SIPG ? 3 : 1)) * k * k +
          6 * (op == OP_SIPG ? 4 : 1) * k * k;
 }
-__host__ __device__ constexpr int smem_bytes_per_block(int k, int op, int scalar_bytes) {
-  return (cells_per_block(k) * smem_scalars_per_cell(k, op) + 3 * k + 2 * k * k) * scalar_bytes;
+__host__ __device__ constexpr int smem_bytes_per_block(int k, int op, int scalar_bytes, int cpb) {
+  return (cpb * smem_scalars_per_cell(k, op) + 3 * k + 2 * k * k) * scalar_bytes;
 }
 
 // Implemented per degree in dg_apply_k<K>.cu.

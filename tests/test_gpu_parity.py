@@ -196,3 +196,24 @@ def test_error_paths():
     with pytest.raises(dgp.DGError) as e:
         dgp.Operator(2, 2, geom="full", mapping=1, amplitude=0.9)  # det J < 0 somewhere
     assert e.value.status == dgp.DG_ERR_ARG
+
+
+@pytest.mark.parametrize("p", [1, 4, 8])
+def test_tile_shape_does_not_change_results(p):
+    """Cells per block is a launch parameter only: every value gives the same
+    bits; the autotuner keeps one of them."""
+    for prec in ("fp64", "fp32"):
+        op = dgp.Operator((5, 4, 3), p, geom="full", prec=prec, mapping=1, coeff=1)
+        u = torch.tensor(dg_inputs.src_vector(op.n_dofs, 5), dtype=op.dtype, device="cuda")
+        ref = op.apply(u).clone()
+        cmax = op.info()["cells_per_block"]
+        for c in sorted({1, 2, max(1, cmax // 2), cmax}):
+            op.set_cells_per_block(c)
+            assert op.info()["cells_per_block"] == c
+            assert torch.equal(op.apply(u), ref), (prec, c)
+        c, ms = op.autotune()
+        assert 1 <= c <= cmax and ms > 0
+        assert torch.equal(op.apply(u), ref)
+        with pytest.raises(dgp.DGError):
+            op.set_cells_per_block(cmax + 1)
+        op.close()
