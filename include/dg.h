@@ -24,7 +24,8 @@
  * Conventions for every call:
  *   - Device pointers are CUDA device addresses of the current device with
  *     n_dofs contiguous scalars of the handle's precision (double for
- *     DG_FP64, float for DG_FP32), 16-byte aligned.  The caller owns them.
+ *     DG_FP64 and DG_FP64_EMU, float for DG_FP32), 16-byte aligned.  The
+ *     caller owns them.
  *   - Calls are stream-ordered on the handle's stream and asynchronous,
  *     unless stated otherwise.
  *   - Errors are returned as dg_status codes, never by aborting; a message is
@@ -75,7 +76,15 @@ typedef enum {
   DG_GEOM_MERGED = 3
 } dg_geom;
 
-typedef enum { DG_FP64 = 0, DG_FP32 = 1 } dg_prec;
+/* Arithmetic of the apply.
+ *  DG_FP64:     IEEE binary64 vectors and arithmetic (the FP64 pipe).
+ *  DG_FP32:     binary32 vectors and arithmetic.
+ *  DG_FP64_EMU: binary64 vectors; arithmetic in double-float (pairs of
+ *               binary32 numbers, ~48-bit significand) on the FP32 pipe, which
+ *               GB300 runs 64x faster than its FP64 pipe.  Accuracy is held to
+ *               the same 1e-12 relative tolerance as DG_FP64; values keep full
+ *               accuracy for magnitudes in about [1e-30, 1e38]. */
+typedef enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP64_EMU = 2 } dg_prec;
 
 typedef struct {
   int n[3];         /* cells per direction, each >= 1 */
@@ -174,7 +183,8 @@ dg_status dg_rhs(dg_handle *h, int which_f, double *rhs);
  * one fused vector update x += alpha p, r -= alpha Ap with r.r, then
  * p = r + beta p.  All reductions are two-stage in a fixed order, so results
  * are bitwise reproducible on a given device and size.  An FP32 handle
- * returns DG_ERR_UNSUPPORTED.
+ * returns DG_ERR_UNSUPPORTED (see dg_cg_solve_mixed); DG_FP64_EMU handles
+ * run the same CG with their emulated-FP64 apply.
  * Stops when |r| <= rtol |rhs|.  Returns DG_ERR_NOT_CONVERGED after max_it
  * iterations and DG_ERR_BREAKDOWN on p.Ap <= 0 or non-finite scalars.
  * iters and final_rel_res (may be NULL) receive the count and |r|/|rhs|.

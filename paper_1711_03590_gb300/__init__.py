@@ -38,11 +38,12 @@ DG_GEOM_FULL_JAC = 2
 DG_GEOM_MERGED = 3
 DG_FP64 = 0
 DG_FP32 = 1
+DG_FP64_EMU = 2
 
 GEOMS = {"cartesian": DG_GEOM_CARTESIAN, "affine": DG_GEOM_AFFINE, "full": DG_GEOM_FULL_JAC,
          "merged": DG_GEOM_MERGED}
 OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
-PRECS = {"fp64": DG_FP64, "fp32": DG_FP32}
+PRECS = {"fp64": DG_FP64, "fp32": DG_FP32, "fp64emu": DG_FP64_EMU}
 
 EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
             "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
@@ -244,7 +245,7 @@ class Operator:
         self.mesh = make_mesh(n, periodic, mapping, amplitude)
         self.opts = make_opts(op, prec, velocity, coeff, penalty_scale)
         self.degree = degree
-        self.dtype = torch.float64 if PRECS.get(prec, prec) == DG_FP64 else torch.float32
+        self.dtype = torch.float32 if PRECS.get(prec, prec) == DG_FP32 else torch.float64
         self.handle = None
         self.handle = dg_setup(self.mesh, degree, geom, self.opts, stream)
         self.n_dofs = dg_n_dofs(self.handle)

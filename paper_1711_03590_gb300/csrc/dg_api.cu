@@ -11,8 +11,10 @@
 #include <vector>
 
 #include "../../include/dg.h"
+#include "dg_df64.cuh"
 #include "dg_internal.cuh"
 
+using dg::df64;
 using dg::kMaxK;
 
 // ---------------------------------------------------------------------------
@@ -234,8 +236,10 @@ struct dg_handle {
   Tables64 t64;
   dg::Tables<double> tabd;
   dg::Tables<float> tabf;
+  dg::Tables<df64> tabdf;
   dg::Geometry<double> geod;
   dg::Geometry<float> geof;
+  dg::Geometry<df64> geodf;
   void* cell_geo;         // device: per-quadrature-point cell arrays
   void* face_geo[3];      // device: per-face-point arrays
   void* face_tau[3];      // device: penalty per face
@@ -684,8 +688,12 @@ dg_status launch_apply(dg_handle* h, const void* src, void* dst, double* dot_par
   L.op = h->op;
   L.src = src;
   L.dst = dst;
-  L.tables = h->prec == DG_FP64 ? (const void*)&h->tabd : (const void*)&h->tabf;
-  L.geometry = h->prec == DG_FP64 ? (const void*)&h->geod : (const void*)&h->geof;
+  L.tables = h->prec == DG_FP64 ? (const void*)&h->tabd
+             : h->prec == DG_FP32 ? (const void*)&h->tabf
+                                  : (const void*)&h->tabdf;
+  L.geometry = h->prec == DG_FP64 ? (const void*)&h->geod
+               : h->prec == DG_FP32 ? (const void*)&h->geof
+                                    : (const void*)&h->geodf;
   L.dot_partial = dot_partial;
   L.stream = h->stream;
   L.cpb = h->cpb;
@@ -946,7 +954,7 @@ dg_status run_cg(dg_handle* h, const T* b, T* x, bool x_zero, double rtol, int m
 dg_status dg_internal_apply_with_partials(dg_handle* h, const void* src, void* dst, double* partials,
                                           int64_t* n_blocks, cudaStream_t* stream) {
   if (!src || !dst) return fail(h, DG_ERR_ARG, "src or dst is NULL");
-  const int64_t bytes = h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  const int64_t bytes = h->n_dofs * (h->prec == DG_FP32 ? 4 : 8);
   const char* a = static_cast<const char*>(src);
   const char* b = static_cast<const char*>(dst);
   if (a < b + bytes && b < a + bytes) return fail(h, DG_ERR_ARG, "src and dst overlap");
@@ -973,7 +981,8 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
     if (mesh->n[d] < 1 || mesh->n[d] > (1 << 20)) return fail(nullptr, DG_ERR_ARG, "cells per direction must be >= 1");
   if (mesh->mapping != 0 && mesh->mapping != 1) return fail(nullptr, DG_ERR_ARG, "mapping must be 0 or 1");
   if (opts->op != DG_OP_SIPG && opts->op != DG_OP_ADVECTION) return fail(nullptr, DG_ERR_ARG, "unknown operator");
-  if (opts->prec != DG_FP64 && opts->prec != DG_FP32) return fail(nullptr, DG_ERR_ARG, "unknown precision");
+  if (opts->prec != DG_FP64 && opts->prec != DG_FP32 && opts->prec != DG_FP64_EMU)
+    return fail(nullptr, DG_ERR_ARG, "unknown precision");
   if (opts->coeff != 0 && opts->coeff != 1) return fail(nullptr, DG_ERR_ARG, "coeff must be 0 or 1");
   if (geom == DG_GEOM_AFFINE) return fail(nullptr, DG_ERR_UNSUPPORTED, "affine geometry storage is not implemented");
   if (geom != DG_GEOM_CARTESIAN && geom != DG_GEOM_FULL_JAC && geom != DG_GEOM_MERGED)
@@ -1009,9 +1018,15 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   build_tables(k, h->t64);
   h->tabd = cast_tables<double>(k, h->t64);
   h->tabf = cast_tables<float>(k, h->t64);
+  h->tabdf = cast_tables<df64>(k, h->t64);
 
-  dg_status st = h->prec == DG_FP64 ? setup_geometry<double>(h) : setup_geometry<float>(h);
-  if (st == DG_OK) st = h->prec == DG_FP64 ? setup_kappa_table<double>(h) : setup_kappa_table<float>(h);
+  dg_status st = h->prec == DG_FP64   ? setup_geometry<double>(h)
+                 : h->prec == DG_FP32 ? setup_geometry<float>(h)
+                                      : setup_geometry<df64>(h);
+  if (st == DG_OK)
+    st = h->prec == DG_FP64   ? setup_kappa_table<double>(h)
+         : h->prec == DG_FP32 ? setup_kappa_table<float>(h)
+                              : setup_kappa_table<df64>(h);
   if (st != DG_OK) {
     g_setup_error = h->err;
     free_handle(h);
@@ -1019,6 +1034,7 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   }
   fill_geometry<double>(h, h->geod);
   fill_geometry<float>(h, h->geof);
+  fill_geometry<df64>(h, h->geodf);
   *out = h;
   return DG_OK;
 }
@@ -1041,7 +1057,7 @@ dg_status dg_info(const dg_handle* h, dg_info_t* info) {
   info->face_geometry_bytes = h->face_bytes;
   info->cells_per_block = h->cpb;
   info->threads_per_block = h->cpb * h->k * h->k;
-  info->shared_bytes_per_block = dg::smem_bytes_per_block(h->k, h->op, h->prec == DG_FP64 ? 8 : 4, h->cpb);
+  info->shared_bytes_per_block = dg::smem_bytes_per_block(h->k, h->op, h->prec == DG_FP32 ? 4 : 8, h->cpb);
   info->blocks = apply_blocks(h);
   return DG_OK;
 }
@@ -1055,7 +1071,7 @@ dg_status dg_set_stream(dg_handle* h, void* stream) {
 dg_status dg_apply(dg_handle* h, const void* src, void* dst) {
   if (!h) return DG_ERR_ARG;
   if (!src || !dst) return fail(h, DG_ERR_ARG, "src or dst is NULL");
-  const int64_t bytes = h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  const int64_t bytes = h->n_dofs * (h->prec == DG_FP32 ? 4 : 8);
   const char* a = static_cast<const char*>(src);
   const char* b = static_cast<const char*>(dst);
   if (a < b + bytes && b < a + bytes) return fail(h, DG_ERR_ARG, "src and dst overlap");
@@ -1067,7 +1083,7 @@ dg_status dg_apply(dg_handle* h, const void* src, void* dst) {
 dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
   if (!h) return DG_ERR_ARG;
   if (!src_host || !dst_host) return fail(h, DG_ERR_ARG, "src or dst is NULL");
-  const size_t bytes = (size_t)h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  const size_t bytes = (size_t)h->n_dofs * (h->prec == DG_FP32 ? 4 : 8);
   dg_status st;
   if (!h->stage_src && (st = dev_alloc(h, &h->stage_src, bytes)) != DG_OK) return st;
   if (!h->stage_dst && (st = dev_alloc(h, &h->stage_dst, bytes)) != DG_OK) return st;
@@ -1111,7 +1127,7 @@ dg_status dg_cg_solve(dg_handle* h, const double* rhs, double* x, double rtol, i
                       double* final_rel_res) {
   if (!h) return DG_ERR_ARG;
   if (h->op != DG_OP_SIPG) return fail(h, DG_ERR_UNSUPPORTED, "CG needs the symmetric SIPG operator");
-  if (h->prec != DG_FP64) return fail(h, DG_ERR_UNSUPPORTED, "CG runs on FP64 handles");
+  if (h->prec == DG_FP32) return fail(h, DG_ERR_UNSUPPORTED, "CG runs on FP64 handles (see dg_cg_solve_mixed)");
   if (!rhs || !x) return fail(h, DG_ERR_ARG, "rhs or x is NULL");
   if (!(rtol > 0.0) || max_it < 0) return fail(h, DG_ERR_ARG, "rtol must be > 0 and max_it >= 0");
   dg_status st = ensure_cg_work(h, false);
@@ -1130,7 +1146,7 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
   if (!h64 || !h32) return DG_ERR_ARG;
   if (h64->op != DG_OP_SIPG || h32->op != DG_OP_SIPG)
     return fail(h64, DG_ERR_UNSUPPORTED, "mixed-precision CG needs the symmetric SIPG operator");
-  if (h64->prec != DG_FP64 || h32->prec != DG_FP32)
+  if (h64->prec == DG_FP32 || h32->prec != DG_FP32)
     return fail(h64, DG_ERR_ARG, "mixed-precision CG needs an FP64 handle and an FP32 handle");
   if (memcmp(&h64->mesh, &h32->mesh, sizeof(dg_mesh)) != 0 || h64->degree != h32->degree ||
       h64->geom != h32->geom || h64->opts.coeff != h32->opts.coeff ||
@@ -1209,7 +1225,7 @@ dg_status dg_set_cells_per_block(dg_handle* h, int cpb) {
 
 dg_status dg_autotune(dg_handle* h, int* best_cpb, double* best_ms) {
   if (!h) return DG_ERR_ARG;
-  const size_t bytes = (size_t)h->n_dofs * (h->prec == DG_FP64 ? 8 : 4);
+  const size_t bytes = (size_t)h->n_dofs * (h->prec == DG_FP32 ? 4 : 8);
   dg_status st;
   if (!h->stage_src && (st = dev_alloc(h, &h->stage_src, bytes)) != DG_OK) return st;
   if (!h->stage_dst && (st = dev_alloc(h, &h->stage_dst, bytes)) != DG_OK) return st;

@@ -25,16 +25,50 @@
 // position (E, W) are copied to shared memory first.
 #pragma once
 
+#include <type_traits>
+
+#include "dg_df64.cuh"
 #include "dg_internal.cuh"
 
 namespace dg {
+
+// Vector storage type and conversions for each arithmetic type: float and
+// double vectors are used as they are; the double-float arithmetic reads and
+// writes binary64 vectors.
+template <typename T>
+struct Arith {
+  using V = T;
+  static __device__ __forceinline__ T load(const V* p) { return *p; }
+  static __device__ __forceinline__ void store(V* p, T v) { *p = v; }
+  static __device__ __forceinline__ double to_double(T v) { return (double)v; }
+};
+template <>
+struct Arith<df64> {
+  using V = double;
+  static __device__ __forceinline__ df64 load(const double* p) { return dfp::df_from_double(*p); }
+  static __device__ __forceinline__ void store(double* p, df64 v) { *p = dfp::df_to_double(v); }
+  static __device__ __forceinline__ double to_double(df64 v) { return dfp::df_to_double(v); }
+};
+
+// Dot-product accumulation: a chain of FMAs, or for double-float a
+// compensated sum renormalized once.
+template <typename T>
+struct Acc {
+  T v;
+  __device__ __forceinline__ void init() { v = T(0); }
+  __device__ __forceinline__ void init(T c) { v = c; }
+  __device__ __forceinline__ void add(T a, T b) { v = fma(a, b, v); }
+  __device__ __forceinline__ T get() const { return v; }
+};
+template <>
+struct Acc<df64> : DfAcc {};
 
 template <typename T>
 struct ApplyParams {
   Tables<T> tab;
   Geometry<T> geo;
-  const T* src;
-  T* dst;
+  const typename Arith<T>::V* src;
+  typename Arith<T>::V* dst;
   double* dot_partial;
   int C;  // cells per block
 };
@@ -61,10 +95,11 @@ __device__ __forceinline__ void line_apply(const T* __restrict__ M, T* v, int ba
   for (int i = 0; i < K; ++i) in[i] = v[base + i * stride];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    T s = T(0);
+    Acc<T> s;
+    s.init();
 #pragma unroll
-    for (int i = 0; i < K; ++i) s = fma(TR ? M[i * K + q] : M[q * K + i], in[i], s);
-    v[base + q * stride] = s;
+    for (int i = 0; i < K; ++i) s.add(TR ? M[i * K + q] : M[q * K + i], in[i]);
+    v[base + q * stride] = s.get();
   }
 }
 
@@ -77,10 +112,11 @@ __device__ __forceinline__ void line_apply_to(const T* __restrict__ M, const T* 
   for (int i = 0; i < K; ++i) x[i] = in[ib + i * is];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    T s = T(0);
+    Acc<T> s;
+    s.init();
 #pragma unroll
-    for (int i = 0; i < K; ++i) s = fma(M[q * K + i], x[i], s);
-    out[ob + q * os] = s;
+    for (int i = 0; i < K; ++i) s.add(M[q * K + i], x[i]);
+    out[ob + q * os] = s.get();
   }
 }
 
@@ -93,10 +129,11 @@ __device__ __forceinline__ void line_add_transposed(const T* __restrict__ M, con
   for (int q = 0; q < K; ++q) x[q] = t[base + q * stride];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    T s = v[base + j * stride];
+    Acc<T> s;
+    s.init(v[base + j * stride]);
 #pragma unroll
-    for (int q = 0; q < K; ++q) s = fma(M[q * K + j], x[q], s);
-    v[base + j * stride] = s;
+    for (int q = 0; q < K; ++q) s.add(M[q * K + j], x[q]);
+    v[base + j * stride] = s.get();
   }
 }
 
@@ -125,7 +162,8 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   T* sW = sE + 2 * K;                     // [K]
   T* sS = sW + K;                         // [K][K] (rows indexed by thread position)
   T* sD = sS + K2;                        // [K][K]
-  constexpr bool kLineFaces = sizeof(T) == 4;
+  constexpr bool kLineFaces = std::is_same<T, float>::value;
+  using A = Arith<T>;
 
   const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
@@ -199,8 +237,8 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
 
   // 1. gather (coalesced over the block's contiguous range)
   {
-    const T* s = P.src + cell0 * K3;
-    for (int i = tid; i < nloc * K3; i += blockDim.x) U[i] = s[i];
+    const typename A::V* s = P.src + cell0 * K3;
+    for (int i = tid; i < nloc * K3; i += blockDim.x) U[i] = A::load(s + i);
   }
   __syncthreads();
 
@@ -249,16 +287,17 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         if (nbc[s] < 0) continue;
-        const T* un = P.src + nbc[s] * K3 + line_base<K>(d, la, lb);
+        const typename A::V* un = P.src + nbc[s] * K3 + line_base<K>(d, la, lb);
         T v[K];
 #pragma unroll
-        for (int l = 0; l < K; ++l) v[l] = un[l * strd];
+        for (int l = 0; l < K; ++l) v[l] = A::load(un + l * strd);
         nba[(s * NBA) * K2 + ln] = s ? v[0] : v[K - 1];
         if (OP == OP_SIPG) {
-          T dv = T(0);
+          Acc<T> dv;
+          dv.init();
 #pragma unroll
-          for (int l = 0; l < K; ++l) dv = fma(tb.DF[1 - s][l], v[l], dv);
-          nba[(s * NBA + 1) * K2 + ln] = dv;
+          for (int l = 0; l < K; ++l) dv.add(tb.DF[1 - s][l], v[l]);
+          nba[(s * NBA + 1) * K2 + ln] = dv.get();
         }
       }
     }
@@ -267,7 +306,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
     // points.  FP32 (LSU-limited): line sweeps, one thread per line, matrices
     // with compile-time indices.  FP64 (FP64-pipe-limited, charged per warp
     // instruction): one thread per face point so that every lane works.
-    if (kLineFaces) {
+    if constexpr (kLineFaces) {
       // along t1 at fixed t2 index j: the value with S and with DS = d/dt1,
       // the normal derivative with S (Cartesian meshes need no tangential
       // derivative)
@@ -356,10 +395,11 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
 #pragma unroll
           for (int f = 0; f < NBA; ++f) {
             const T* in = nba + (s * NBA + f) * K2;
-            T acc = T(0);
+            Acc<T> acc;
+            acc.init();
 #pragma unroll
-            for (int i = 0; i < K; ++i) acc = fma(sS[la * K + i], in[i + K * lb], acc);
-            nbb[(s * NBB + f) * K2 + ln] = acc;
+            for (int i = 0; i < K; ++i) acc.add(sS[la * K + i], in[i + K * lb]);
+            nbb[(s * NBB + f) * K2 + ln] = acc.get();
           }
         }
       }
@@ -371,10 +411,11 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
 #pragma unroll
           for (int f = 0; f < NBA; ++f) {
             const T* in = nbb + (s * NBB + f) * K2;
-            T acc = T(0);
+            Acc<T> acc;
+            acc.init();
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc = fma(sS[lb * K + j], in[la + K * j], acc);
-            nba[(s * NBA + f) * K2 + ln] = acc;
+            for (int j = 0; j < K; ++j) acc.add(sS[lb * K + j], in[la + K * j]);
+            nba[(s * NBA + f) * K2 + ln] = acc.get();
           }
         }
       }
@@ -389,16 +430,18 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           if (GEO == GEO_CART) {
             dnn[s] = (s ? T(1) : T(-1)) * gm.cart_jinv[d] * nbt[K2 + ln];
           } else {
-            T a1 = T(0), a2 = T(0);
+            Acc<T> a1, a2;
+            a1.init();
+            a2.init();
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-              a1 = fma(sD[la * K + i], nbt[i + K * lb], a1);
-              a2 = fma(sD[lb * K + i], nbt[la + K * i], a2);
+              a1.add(sD[la * K + i], nbt[i + K * lb]);
+              a2.add(sD[lb * K + i], nbt[la + K * i]);
             }
             T gn[3];
             gn[d] = nbt[K2 + ln];
-            gn[t1] = a1;
-            gn[t2] = a2;
+            gn[t1] = a1.get();
+            gn[t2] = a2.get();
             const int64_t nfq = gm.nfq[d];
             const T* fp = gm.face[d] + fid[s] * K2 + ln;
             dnn[s] = -(fp[(s * 3 + 0) * nfq] * gn[0] + fp[(s * 3 + 1) * nfq] * gn[1] + fp[(s * 3 + 2) * nfq] * gn[2]);
@@ -432,21 +475,27 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
       for (int s = 0; s < 2; ++s) {
         const bool interior = nbc[s] >= 0;
         const T sg = s ? T(1) : T(-1);
-        T u = T(0);
+        Acc<T> au;
+        au.init();
 #pragma unroll
-        for (int j = 0; j < K; ++j) u = fma(tb.E[s][j], lu[j], u);
+        for (int j = 0; j < K; ++j) au.add(tb.E[s][j], lu[j]);
+        const T u = au.get();
         const T* nbt = nba + s * NBA * K2;
         const T un = interior ? nbt[ln] : T(0);
         T* ft = FT + (((lc * 3 + d) * 2 + s) * FTF) * K2 + ln;
         if (OP == OP_SIPG) {
-          T g[3] = {T(0), T(0), T(0)};
+          Acc<T> ag0, ag1, ag2;
+          ag0.init();
+          ag1.init();
+          ag2.init();
 #pragma unroll
           for (int j = 0; j < K; ++j) {
             const T e = tb.E[s][j];
-            g[0] = fma(e, lg0[j], g[0]);
-            g[1] = fma(e, lg1[j], g[1]);
-            g[2] = fma(e, lg2[j], g[2]);
+            ag0.add(e, lg0[j]);
+            ag1.add(e, lg1[j]);
+            ag2.add(e, lg2[j]);
           }
+          T g[3] = {ag0.get(), ag1.get(), ag2.get()};
           const T dnn = interior ? nbt[K2 + ln] : T(0);
           T jo[3], dno, fjxw, tau;
           if (GEO == GEO_CART) {
@@ -497,7 +546,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
     __syncthreads();
   }
 
-  if (kLineFaces) {
+  if constexpr (kLineFaces) {
     // 4. (z-line owner) quadrature-point operation and the z faces' test
     // coefficients, injected along the z line by the thread that formed them
     if (active) {
@@ -687,13 +736,22 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           const T* fz0 = ftc + (2 * 2 + 0) * FTF * K2 + la + K * lb;
           const T* fz1 = ftc + (2 * 2 + 1) * FTF * K2 + la + K * lb;
           const T ez0 = tb.E[0][z], ez1 = tb.E[1][z];
-          fv = e0a * fx0[0] + e1a * fx1[0] + e0b * fy0[0] + e1b * fy1[0] + ez0 * fz0[0] + ez1 * fz1[0];
+          auto inj = [&](int f) {
+            Acc<T> a;
+            a.init();
+            a.add(e0a, fx0[f * K2]);
+            a.add(e1a, fx1[f * K2]);
+            a.add(e0b, fy0[f * K2]);
+            a.add(e1b, fy1[f * K2]);
+            a.add(ez0, fz0[f * K2]);
+            a.add(ez1, fz1[f * K2]);
+            return a.get();
+          };
+          fv = inj(0);
           if (OP == OP_SIPG) {
-            fg0 = e0a * fx0[K2] + e1a * fx1[K2] + e0b * fy0[K2] + e1b * fy1[K2] + ez0 * fz0[K2] + ez1 * fz1[K2];
-            fg1 = e0a * fx0[2 * K2] + e1a * fx1[2 * K2] + e0b * fy0[2 * K2] + e1b * fy1[2 * K2] +
-                  ez0 * fz0[2 * K2] + ez1 * fz1[2 * K2];
-            fg2 = e0a * fx0[3 * K2] + e1a * fx1[3 * K2] + e0b * fy0[3 * K2] + e1b * fy1[3 * K2] +
-                  ez0 * fz0[3 * K2] + ez1 * fz1[3 * K2];
+            fg0 = inj(1);
+            fg1 = inj(2);
+            fg2 = inj(3);
           }
         }
         T t0, t1, t2;
@@ -783,14 +841,14 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
 
   // write (set) the block's contiguous range; optional src . dst partial
   {
-    T* o = P.dst + cell0 * K3;
+    typename A::V* o = P.dst + cell0 * K3;
     double acc = 0.0;
-    const T* s = P.src + cell0 * K3;
+    const typename A::V* s = P.src + cell0 * K3;
     const bool dot = P.dot_partial != nullptr;
     for (int i = tid; i < nloc * K3; i += blockDim.x) {
       const T v = U[i];
-      o[i] = v;
-      if (dot) acc += (double)v * (double)s[i];
+      A::store(o + i, v);
+      if (dot) acc += A::to_double(v) * (double)s[i];
     }
     if (dot) {
       double* red = reinterpret_cast<double*>(G);
@@ -810,8 +868,8 @@ cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
   ApplyParams<T> P;
   P.tab = *static_cast<const Tables<T>*>(L.tables);
   P.geo = *static_cast<const Geometry<T>*>(L.geometry);
-  P.src = static_cast<const T*>(L.src);
-  P.dst = static_cast<T*>(L.dst);
+  P.src = static_cast<const typename Arith<T>::V*>(L.src);
+  P.dst = static_cast<typename Arith<T>::V*>(L.dst);
   P.dot_partial = L.dot_partial;
   const int C = (L.cpb >= 1 && L.cpb <= cells_per_block(K)) ? L.cpb : cells_per_block(K);
   P.C = C;
@@ -843,7 +901,9 @@ cudaError_t launch_prec(const ApplyLaunch& L, int64_t n_cells) {
 
 template <int K>
 cudaError_t launch_apply(const ApplyLaunch& L, int64_t n_cells) {
-  return L.prec == 0 ? launch_prec<K, double>(L, n_cells) : launch_prec<K, float>(L, n_cells);
+  if (L.prec == 0) return launch_prec<K, double>(L, n_cells);
+  if (L.prec == 1) return launch_prec<K, float>(L, n_cells);
+  return launch_prec<K, df64>(L, n_cells);
 }
 
 }  // namespace dg

@@ -20,7 +20,7 @@ if not torch.cuda.is_available():
 
 import paper_1711_03590_gb300 as dgp  # noqa: E402
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp64emu": 1e-12}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -72,6 +72,8 @@ def test_config1_cartesian_periodic_p2_vs_assembled():
     for geom in ("cartesian", "full", "merged"):
         got = _gpu_apply(mesh, p, geom, form, "fp64", u)
         assert _rel(got, ref) < TOL["fp64"], geom
+        gote = _gpu_apply(mesh, p, geom, form, "fp64emu", u)
+        assert _rel(gote, ref) < TOL["fp64emu"], geom
         got32 = _gpu_apply(mesh, p, geom, form, "fp32", u)
         assert _rel(got32, ref) < TOL["fp32"], geom
 
@@ -88,13 +90,13 @@ def test_small_meshes_all_degrees(p, case, op):
     form = dict(op=op, coeff=1 if (op == "sipg" and case % 2 == 1) else 0, velocity=dg_inputs.VELOCITY)
     u = dg_inputs.src_vector(n, seed=100 + p)
     ref = oracle.apply(mesh, p, form, u)
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp64emu"):
         got = _gpu_apply(mesh, p, geom, form, prec, u)
         assert _rel(got, ref) < TOL[prec], (prec, _rel(got, ref))
 
 
 @pytest.mark.parametrize("p", [1, 2, 4, 8])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp64emu"])
 def test_full_size_deformed_sampled(p, prec):
     """32^3 deformed mesh, full per-point Jacobians, kappa variable,
     Dirichlet: full-size GPU apply, compared on sampled cells (all eight
@@ -202,7 +204,7 @@ def test_error_paths():
 def test_tile_shape_does_not_change_results(p):
     """Cells per block is a launch parameter only: every value gives the same
     bits; the autotuner keeps one of them."""
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp64emu"):
         op = dgp.Operator((5, 4, 3), p, geom="full", prec=prec, mapping=1, coeff=1)
         u = torch.tensor(dg_inputs.src_vector(op.n_dofs, 5), dtype=op.dtype, device="cuda")
         ref = op.apply(u).clone()
@@ -217,3 +219,31 @@ def test_tile_shape_does_not_change_results(p):
         with pytest.raises(dgp.DGError):
             op.set_cells_per_block(cmax + 1)
         op.close()
+
+
+def test_emulated_fp64_range_and_special_values():
+    """Double-float loads: zeros, tiny and large magnitudes and mixed signs
+    in the input vector keep the FP64 tolerance against the FP64 apply."""
+    for scale in (1e-20, 1.0, 1e20):
+        op = dgp.Operator((3, 3, 3), 3, geom="full", prec="fp64emu", mapping=1, coeff=1)
+        o64 = dgp.Operator((3, 3, 3), 3, geom="full", prec="fp64", mapping=1, coeff=1)
+        u = dg_inputs.src_vector(op.n_dofs, 9) * scale
+        u[::7] = 0.0
+        src = torch.tensor(u, device="cuda")
+        ye, y64 = op.apply(src), o64.apply(src)
+        rel = float((ye - y64).norm() / y64.norm())
+        assert rel < 1e-12, (scale, rel)
+        op.close()
+        o64.close()
+
+
+def test_emulated_fp64_cg_matches_fp64_cg():
+    mesh = dict(n=(4, 4, 4), periodic=False, mapping=1, amplitude=0.1)
+    p = 3
+    b = oracle.rhs(mesh, p, 1)
+    A = oracle.assemble(mesh, p, dict(op="sipg", coeff=1))
+    rhs = torch.tensor(b, device="cuda")
+    oe = dgp.Operator(mesh["n"], p, geom="full", prec="fp64emu", mapping=1, coeff=1)
+    xe, ite, rre, st = oe.cg(rhs, rtol=1e-11, max_it=20000)
+    assert st == dgp.DG_OK
+    assert np.linalg.norm(b - A @ xe.cpu().numpy()) <= 3e-11 * np.linalg.norm(b)
