@@ -288,7 +288,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--degree", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision of the headline apply")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp64emu"],
+                    help="precision of the headline apply")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
@@ -321,7 +322,7 @@ def main():
     op = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec=args.prec, coeff=w["coeff"], **common)
     n = op.n_dofs
     n_cells = op.info()["n_cells"]
-    ssz = 8 if args.prec == "fp64" else 4
+    ssz = 4 if args.prec == "fp32" else 8
     src = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank), dtype=op.dtype, device="cuda")
     dst = torch.empty_like(src)
     for _ in range(args.warmup):
@@ -352,7 +353,7 @@ def main():
     achieved_tf = flops / (launch_ms / 1e3) / 1e12
     bpd = bytes_per_dof(k, ssz, "sipg", w["geom"])
     achieved_gbs = bpd * n / (launch_ms / 1e3) / 1e9
-    kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, "double" if args.prec == "fp64" else "float")
+    kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, {"fp64": "double", "fp32": "float", "fp64emu": "df64"}[args.prec])
     hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": kname, "bytes_per_dof": bpd,
            "peak_source": peaks.get("source")}
@@ -413,7 +414,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp64emu": "f64 (double-float arithmetic)"}[args.prec], "data": "synthetic",
                 "config": {"workload": wname, "degree": p, "cells": n_cells,
                            "dofs": n, "geometry": "full per-point Jacobians (G3)", "operator": "SIPG",
                            "boundary": "Dirichlet", "coefficient": "1+0.5 sin(2 pi x)",

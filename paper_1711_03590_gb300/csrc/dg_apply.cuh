@@ -87,13 +87,19 @@ struct Smem {
   static constexpr int per_cell = smem_scalars_per_cell(K, OP);
 };
 
+// The outer (output) loops of the line helpers unroll UQ times: fully for
+// binary32/binary64 (matrix entries become constant-bank operands), not at
+// all for double-float, whose 12-instruction products would otherwise
+// overflow the instruction cache (its matrices are then read from shared
+// memory).
+
 // v[base + q stride] = sum_i M[q][i] v[base + i stride]   (TR: M[i][q])
-template <int K, bool TR, typename T>
+template <int K, bool TR, int UQ, typename T>
 __device__ __forceinline__ void line_apply(const T* __restrict__ M, T* v, int base, int stride) {
   T in[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) in[i] = v[base + i * stride];
-#pragma unroll
+#pragma unroll(UQ)
   for (int q = 0; q < K; ++q) {
     Acc<T> s;
     s.init();
@@ -104,13 +110,13 @@ __device__ __forceinline__ void line_apply(const T* __restrict__ M, T* v, int ba
 }
 
 // out[ob + q os] = sum_i M[q][i] in[ib + i is]
-template <int K, typename T>
+template <int K, int UQ, typename T>
 __device__ __forceinline__ void line_apply_to(const T* __restrict__ M, const T* in, int ib, int is, T* out, int ob,
                                               int os) {
   T x[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) x[i] = in[ib + i * is];
-#pragma unroll
+#pragma unroll(UQ)
   for (int q = 0; q < K; ++q) {
     Acc<T> s;
     s.init();
@@ -121,13 +127,13 @@ __device__ __forceinline__ void line_apply_to(const T* __restrict__ M, const T* 
 }
 
 // v[base + j stride] += sum_q M[q][j] t[base + q stride]
-template <int K, typename T>
+template <int K, int UQ, typename T>
 __device__ __forceinline__ void line_add_transposed(const T* __restrict__ M, const T* t, T* v, int base,
                                                     int stride) {
   T x[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) x[q] = t[base + q * stride];
-#pragma unroll
+#pragma unroll(UQ)
   for (int j = 0; j < K; ++j) {
     Acc<T> s;
     s.init(v[base + j * stride]);
@@ -163,6 +169,9 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   T* sS = sW + K;                         // [K][K] (rows indexed by thread position)
   T* sD = sS + K2;                        // [K][K]
   constexpr bool kLineFaces = std::is_same<T, float>::value;
+  constexpr bool kCompact = std::is_same<T, df64>::value;
+  constexpr int kUq = kCompact ? 1 : K;     // unroll of the sweep output loops
+  constexpr int kUd = kCompact ? 1 : 3;     // unroll of the face-direction loop
   using A = Arith<T>;
 
   const Tables<T>& tb = P.tab;
@@ -243,41 +252,56 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   __syncthreads();
 
   // 2. basis change to the Gauss points, x then y then z; collocation derivatives
-  if (active) line_apply<K, false>(tb.S, Uc, K * (la + K * lb), 1);
+  const T* mS = kCompact ? sS : tb.S;
+  const T* mD = kCompact ? sD : tb.D;
+  if (active) line_apply<K, false, kUq>(mS, Uc, K * (la + K * lb), 1);
   __syncthreads();
-  if (active) line_apply<K, false>(tb.S, Uc, la + K2 * lb, K);
+  if (active) line_apply<K, false, kUq>(mS, Uc, la + K2 * lb, K);
   __syncthreads();
-  if (active) line_apply<K, false>(tb.S, Uc, la + K * lb, K2);
+  if (active) line_apply<K, false, kUq>(mS, Uc, la + K * lb, K2);
   __syncthreads();
   if (OP == OP_SIPG) {
     if (active) {
-      line_apply_to<K>(tb.D, Uc, K * (la + K * lb), 1, G0, K * (la + K * lb), 1);
-      line_apply_to<K>(tb.D, Uc, la + K2 * lb, K, G1, la + K2 * lb, K);
-      line_apply_to<K>(tb.D, Uc, la + K * lb, K2, G2, la + K * lb, K2);
+      line_apply_to<K, kUq>(mD, Uc, K * (la + K * lb), 1, G0, K * (la + K * lb), 1);
+      line_apply_to<K, kUq>(mD, Uc, la + K2 * lb, K, G1, la + K2 * lb, K);
+      line_apply_to<K, kUq>(mD, Uc, la + K * lb, K2, G2, la + K * lb, K2);
     }
     __syncthreads();
   }
 
-  // 3. faces, one direction at a time (the loop is unrolled: d is constant)
-#pragma unroll
+  // 3. faces, one direction at a time.  The loop is unrolled (d constant)
+  // except for double-float; direction-dependent values are selects, so the
+  // body is valid for a runtime d.
+#pragma unroll(kUd)
   for (int d = 0; d < 3; ++d) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     const int strd = d == 0 ? 1 : d == 1 ? K : K2;
+    const int id = d == 0 ? ijk[0] : d == 1 ? ijk[1] : ijk[2];
+    const int it1 = d == 0 ? ijk[1] : ijk[0], it2 = d == 2 ? ijk[1] : ijk[2];
+    const int nd = d == 0 ? gm.n[0] : d == 1 ? gm.n[1] : gm.n[2];
+    const int nt1 = d == 0 ? gm.n[1] : gm.n[0];
+    const int Pd = d == 0 ? gm.P[0] : d == 1 ? gm.P[1] : gm.P[2];
+    const T* fgeo = d == 0 ? gm.face[0] : d == 1 ? gm.face[1] : gm.face[2];
+    const T* ftau = d == 0 ? gm.tau[0] : d == 1 ? gm.tau[1] : gm.tau[2];
+    const int64_t nfqd = d == 0 ? gm.nfq[0] : d == 1 ? gm.nfq[1] : gm.nfq[2];
+    const T cjd = d == 0 ? gm.cart_jinv[0] : d == 1 ? gm.cart_jinv[1] : gm.cart_jinv[2];
+    const T ctaud = d == 0 ? gm.cart_tau[0] : d == 1 ? gm.cart_tau[1] : gm.cart_tau[2];
+    const T veld = d == 0 ? gm.vel[0] : d == 1 ? gm.vel[1] : gm.vel[2];
     int64_t nbc[2];
     int64_t fid[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      int j[3] = {ijk[0], ijk[1], ijk[2]};
-      j[d] += s ? 1 : -1;
-      int pos = ijk[d] + s;
-      bool inside = j[d] >= 0 && j[d] < gm.n[d];
+      int jd = id + (s ? 1 : -1);
+      int pos = id + s;
+      bool inside = jd >= 0 && jd < nd;
       if (!inside && gm.periodic) {
-        j[d] = j[d] < 0 ? gm.n[d] - 1 : 0;
+        jd = jd < 0 ? nd - 1 : 0;
         inside = true;
       }
-      if (gm.periodic && pos == gm.n[d]) pos = 0;
-      nbc[s] = inside ? (int64_t)(j[0] + gm.n[0] * (j[1] + gm.n[1] * j[2])) : -1;
-      fid[s] = (int64_t)(pos + gm.P[d] * (ijk[t1] + gm.n[t1] * ijk[t2]));
+      if (gm.periodic && pos == nd) pos = 0;
+      const int j0 = d == 0 ? jd : ijk[0], j1 = d == 1 ? jd : ijk[1], j2 = d == 2 ? jd : ijk[2];
+      nbc[s] = inside ? (int64_t)(j0 + gm.n[0] * (j1 + gm.n[1] * j2)) : -1;
+      fid[s] = (int64_t)(pos + Pd * (it1 + nt1 * it2));
     }
     T* nba = NBa + lc * 2 * NBA * K2;  // [2][NBA][K2]
     T* nbb = NBb + lc * 2 * NBB * K2;  // [2][NBB][K2]
@@ -318,9 +342,9 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
         const T* in = nba + (s * NBA + (f == 1 ? 1 : 0)) * K2;
         T* out = nbb + (s * NBB + f) * K2;
         if (OP == OP_SIPG && f == 2)
-          line_apply_to<K>(tb.DS, in, K * j, 1, out, K * j, 1);
+          line_apply_to<K, K>(tb.DS, in, K * j, 1, out, K * j, 1);
         else
-          line_apply_to<K>(tb.S, in, K * j, 1, out, K * j, 1);
+          line_apply_to<K, K>(tb.S, in, K * j, 1, out, K * j, 1);
       }
     }
     __syncthreads();
@@ -428,7 +452,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           if (nbc[s] < 0) continue;
           const T* nbt = nba + s * NBA * K2;
           if (GEO == GEO_CART) {
-            dnn[s] = (s ? T(1) : T(-1)) * gm.cart_jinv[d] * nbt[K2 + ln];
+            dnn[s] = (s ? T(1) : T(-1)) * cjd * nbt[K2 + ln];
           } else {
             Acc<T> a1, a2;
             a1.init();
@@ -438,13 +462,14 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
               a1.add(sD[la * K + i], nbt[i + K * lb]);
               a2.add(sD[lb * K + i], nbt[la + K * i]);
             }
-            T gn[3];
-            gn[d] = nbt[K2 + ln];
-            gn[t1] = a1.get();
-            gn[t2] = a2.get();
-            const int64_t nfq = gm.nfq[d];
-            const T* fp = gm.face[d] + fid[s] * K2 + ln;
-            dnn[s] = -(fp[(s * 3 + 0) * nfq] * gn[0] + fp[(s * 3 + 1) * nfq] * gn[1] + fp[(s * 3 + 2) * nfq] * gn[2]);
+            // reference-axis components: d carries the normal derivative,
+            // t1 < t2 the two tangential ones
+            const T gdn = nbt[K2 + ln], ga1 = a1.get(), ga2 = a2.get();
+            const T gx = d == 0 ? gdn : ga1;
+            const T gy = d == 1 ? gdn : (d == 0 ? ga1 : ga2);
+            const T gz = d == 2 ? gdn : ga2;
+            const T* fp = fgeo + fid[s] * K2 + ln;
+            dnn[s] = -(fp[(s * 3 + 0) * nfqd] * gx + fp[(s * 3 + 1) * nfqd] * gy + fp[(s * 3 + 2) * nfqd] * gz);
           }
         }
       }
@@ -499,24 +524,24 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           const T dnn = interior ? nbt[K2 + ln] : T(0);
           T jo[3], dno, fjxw, tau;
           if (GEO == GEO_CART) {
-            const T jn = sg * gm.cart_jinv[d];
-            jo[0] = jo[1] = jo[2] = T(0);
-            jo[d] = jn;
-            dno = jn * g[d];
+            const T jn = sg * cjd;
+            jo[0] = d == 0 ? jn : T(0);
+            jo[1] = d == 1 ? jn : T(0);
+            jo[2] = d == 2 ? jn : T(0);
+            dno = jn * (d == 0 ? g[0] : d == 1 ? g[1] : g[2]);
             T kap = T(1);
             if (gm.kq) kap = d == 0 ? gm.kf[ijk[0] + s] : gm.kq[ijk[0] * K + la];
-            fjxw = kap * sW[la] * sW[lb] * gm.cart_detj * gm.cart_jinv[d];
-            tau = gm.cart_tau[d];
+            fjxw = kap * sW[la] * sW[lb] * gm.cart_detj * cjd;
+            tau = ctaud;
           } else {
-            const int64_t nfq = gm.nfq[d];
-            const T* fp = gm.face[d] + fid[s] * K2 + ln;
+            const T* fp = fgeo + fid[s] * K2 + ln;
             const int so = 1 - s;  // own slot: the lower side of the face is slot 0
-            jo[0] = fp[(so * 3 + 0) * nfq];
-            jo[1] = fp[(so * 3 + 1) * nfq];
-            jo[2] = fp[(so * 3 + 2) * nfq];
+            jo[0] = fp[(so * 3 + 0) * nfqd];
+            jo[1] = fp[(so * 3 + 1) * nfqd];
+            jo[2] = fp[(so * 3 + 2) * nfqd];
             dno = jo[0] * g[0] + jo[1] * g[1] + jo[2] * g[2];
-            fjxw = fp[6 * nfq];
-            tau = gm.tau[d][fid[s]];
+            fjxw = fp[6 * nfqd];
+            tau = ftau[fid[s]];
           }
           T tv, tg;
           if (interior) {
@@ -534,9 +559,9 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
         } else {
           T cn;
           if (GEO == GEO_CART) {
-            cn = gm.vel[d] * sW[la] * sW[lb] * gm.cart_detj * gm.cart_jinv[d];
+            cn = veld * sW[la] * sW[lb] * gm.cart_detj * cjd;
           } else {
-            cn = gm.face[d][fid[s] * K2 + ln];
+            cn = fgeo[fid[s] * K2 + ln];
           }
           const T cno = s ? cn : -cn;  // c.n da w with n the own outward normal
           ft[0] = interior ? T(0.5) * cno * (u + un) + T(0.5) * fabs(cno) * (u - un) : fabs(cno) * u;
@@ -709,20 +734,20 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
     __syncthreads();
     // z-line owner: V += D^T T_z, then S^T along z, y, x
     if (active) {
-      line_add_transposed<K>(tb.D, G2, Uc, la + K * lb, K2);
-      line_apply<K, true>(tb.S, Uc, la + K * lb, K2);
+      line_add_transposed<K, K>(tb.D, G2, Uc, la + K * lb, K2);
+      line_apply<K, true, K>(tb.S, Uc, la + K * lb, K2);
     }
     __syncthreads();
-    if (active) line_apply<K, true>(tb.S, Uc, la + K2 * lb, K);
+    if (active) line_apply<K, true, K>(tb.S, Uc, la + K2 * lb, K);
     __syncthreads();
-    if (active) line_apply<K, true>(tb.S, Uc, K * (la + K * lb), 1);
+    if (active) line_apply<K, true, K>(tb.S, Uc, K * (la + K * lb), 1);
     __syncthreads();
   } else {
     // 4. quadrature-point operation and injection of the face test coefficients
     if (active) {
       const T e0a = sE[la], e1a = sE[K + la], e0b = sE[lb], e1b = sE[K + lb];
       const T* ftc = FT + lc * 6 * FTF * K2;
-  #pragma unroll
+  #pragma unroll(kCompact ? 1 : K)
       for (int z = 0; z < K; ++z) {
         const int pt = la + K * (lb + K * z);
         T fv, fg0 = T(0), fg1 = T(0), fg2 = T(0);
@@ -735,7 +760,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           const T* fy1 = ftc + (1 * 2 + 1) * FTF * K2 + la + K * z;
           const T* fz0 = ftc + (2 * 2 + 0) * FTF * K2 + la + K * lb;
           const T* fz1 = ftc + (2 * 2 + 1) * FTF * K2 + la + K * lb;
-          const T ez0 = tb.E[0][z], ez1 = tb.E[1][z];
+          const T ez0 = kCompact ? sE[z] : tb.E[0][z], ez1 = kCompact ? sE[K + z] : tb.E[1][z];
           auto inj = [&](int f) {
             Acc<T> a;
             a.init();
@@ -759,7 +784,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
         if (OP == OP_SIPG) {
           const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
           if (GEO == GEO_CART) {
-            T w = sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
+            T w = sW[la] * sW[lb] * (kCompact ? sW[z] : tb.W[z]) * gm.cart_detj;
             if (gm.kq) w *= gm.kq[ijk[0] * K + la];
             t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
             t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
@@ -790,7 +815,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           const T uq = Uc[pt];
           T b0, b1, b2;
           if (GEO == GEO_CART) {
-            const T w = -sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
+            const T w = -sW[la] * sW[lb] * (kCompact ? sW[z] : tb.W[z]) * gm.cart_detj;
             b0 = w * gm.cart_jinv[0] * gm.vel[0];
             b1 = w * gm.cart_jinv[1] * gm.vel[1];
             b2 = w * gm.cart_jinv[2] * gm.vel[2];
@@ -824,18 +849,18 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
     __syncthreads();
 
     // 5. integration: V += D^T T_x, D^T T_y, D^T T_z, then S^T along z, y, x
-    if (active) line_add_transposed<K>(tb.D, G0, Uc, K * (la + K * lb), 1);
+    if (active) line_add_transposed<K, kUq>(mD, G0, Uc, K * (la + K * lb), 1);
     __syncthreads();
-    if (active) line_add_transposed<K>(tb.D, G1, Uc, la + K2 * lb, K);
+    if (active) line_add_transposed<K, kUq>(mD, G1, Uc, la + K2 * lb, K);
     __syncthreads();
     if (active) {
-      line_add_transposed<K>(tb.D, G2, Uc, la + K * lb, K2);
-      line_apply<K, true>(tb.S, Uc, la + K * lb, K2);
+      line_add_transposed<K, kUq>(mD, G2, Uc, la + K * lb, K2);
+      line_apply<K, true, kUq>(mS, Uc, la + K * lb, K2);
     }
     __syncthreads();
-    if (active) line_apply<K, true>(tb.S, Uc, la + K2 * lb, K);
+    if (active) line_apply<K, true, kUq>(mS, Uc, la + K2 * lb, K);
     __syncthreads();
-    if (active) line_apply<K, true>(tb.S, Uc, K * (la + K * lb), 1);
+    if (active) line_apply<K, true, kUq>(mS, Uc, K * (la + K * lb), 1);
     __syncthreads();
   }
 
