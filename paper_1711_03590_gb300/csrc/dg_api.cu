@@ -251,6 +251,8 @@ struct dg_handle {
   int64_t partial_len;
   double* scal;           // device scalars
   double* scal_host;      // pinned host copy
+  cudaStream_t cg_stream;  // solver stream (non-blocking, capturable) and ordering event
+  cudaEvent_t cg_event;
   double* xw;             // extra work vectors (inner solution and right-hand side of
   double* bw;             // the mixed-precision solve), allocated on first use
   // host-buffer apply staging
@@ -546,8 +548,10 @@ __global__ void rhs_kernel(const __grid_constant__ RhsParams R, int64_t n_cells,
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 1024;
 
-// device scalars: 0 rr, 1 bb, 2 pAp, 3 alpha, 4 beta, 5 rr_new, 6 breakdown flag
-enum { S_RR = 0, S_BB, S_PAP, S_ALPHA, S_BETA, S_RRNEW, S_FLAG, S_COUNT };
+// device scalars: 0 rr, 1 bb, 2 pAp, 3 alpha, 4 beta, 5 rr_new, 6 breakdown flag,
+// 7 stop flag (converged, breakdown or max_it), 8 iterations done,
+// 9 (rtol |b|)^2, 10 max_it, 11 converged flag
+enum { S_RR = 0, S_BB, S_PAP, S_ALPHA, S_BETA, S_RRNEW, S_FLAG, S_STOP, S_ITER, S_TOL2, S_MAXIT, S_DONE, S_COUNT };
 
 __device__ void block_store_sum(double v, double* out) {
   __shared__ double red[kRedThreads];
@@ -591,13 +595,23 @@ __device__ double reduce_partials(const double* part, int64_t n) {
   return r;
 }
 
-__global__ void cg_scalars_init(const double* part, int64_t nparts, double* scal) {
+// Scalars of the CG iteration, kept on the device so that iterations need no
+// host round trip.  Once converged (r.r <= (rtol |b|)^2), broken down or at
+// max_it, alpha and beta are forced to zero: later iterations leave x and r
+// unchanged, so the host may check only every few iterations.
+__global__ void cg_scalars_init(const double* part, int64_t nparts, double* scal, double rtol, double max_it) {
   const double rr = reduce_partials(part, nparts);
   const double bb = reduce_partials(part + kRedBlocks, nparts);
   if (threadIdx.x == 0) {
     scal[S_RR] = rr;
     scal[S_BB] = bb;
     scal[S_FLAG] = 0.0;
+    scal[S_ITER] = 0.0;
+    scal[S_MAXIT] = max_it;
+    const double tol2 = rtol * rtol * (bb > 0.0 ? bb : 1.0);
+    scal[S_TOL2] = tol2;
+    scal[S_DONE] = rr <= tol2 ? 1.0 : 0.0;
+    scal[S_STOP] = (rr <= tol2 || max_it <= 0.0) ? 1.0 : 0.0;
   }
 }
 
@@ -605,9 +619,14 @@ __global__ void cg_scalars_alpha(const double* part, int64_t nparts, double* sca
   const double pap = reduce_partials(part, nparts);
   if (threadIdx.x == 0) {
     scal[S_PAP] = pap;
+    if (scal[S_STOP] != 0.0) {
+      scal[S_ALPHA] = 0.0;
+      return;
+    }
     const double a = scal[S_RR] / pap;
     if (!(pap > 0.0) || !isfinite(a)) {
       scal[S_FLAG] = 1.0;
+      scal[S_STOP] = 1.0;
       scal[S_ALPHA] = 0.0;
     } else {
       scal[S_ALPHA] = a;
@@ -633,10 +652,23 @@ __global__ void cg_scalars_beta(const double* part, int64_t nparts, double* scal
   const double rr = reduce_partials(part, nparts);
   if (threadIdx.x == 0) {
     scal[S_RRNEW] = rr;
+    if (scal[S_STOP] != 0.0) {
+      scal[S_BETA] = 0.0;
+      return;
+    }
     const double b = rr / scal[S_RR];
     scal[S_BETA] = isfinite(b) ? b : 0.0;
-    if (!isfinite(rr)) scal[S_FLAG] = 1.0;
     scal[S_RR] = rr;
+    scal[S_ITER] += 1.0;
+    if (!isfinite(rr)) {
+      scal[S_FLAG] = 1.0;
+      scal[S_STOP] = 1.0;
+    } else if (rr <= scal[S_TOL2]) {
+      scal[S_DONE] = 1.0;
+      scal[S_STOP] = 1.0;
+    } else if (scal[S_ITER] >= scal[S_MAXIT]) {
+      scal[S_STOP] = 1.0;
+    }
   }
 }
 
@@ -862,6 +894,8 @@ void free_handle(dg_handle* h) {
   cudaFree(h->stage_dst);
   cudaFree(h->xw);
   cudaFree(h->bw);
+  if (h->cg_stream) cudaStreamDestroy(h->cg_stream);
+  if (h->cg_event) cudaEventDestroy(h->cg_event);
   delete h;
 }
 
@@ -898,7 +932,6 @@ template <typename T>
 dg_status run_cg(dg_handle* h, const T* b, T* x, bool x_zero, double rtol, int max_it, int* iters, double* rel_out,
                  double* bnorm_out) {
   const int64_t n = h->n_dofs;
-  cudaStream_t s = h->stream;
   const int vb = (int)std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads);
   const int64_t nblk = apply_blocks(h);
   double* part_vec = h->partial;
@@ -906,43 +939,89 @@ dg_status run_cg(dg_handle* h, const T* b, T* x, bool x_zero, double rtol, int m
   T* r = reinterpret_cast<T*>(h->r);
   T* p = reinterpret_cast<T*>(h->p);
   T* ap = reinterpret_cast<T*>(h->ap);
-  dg_status st;
-  if (x_zero) {
-    DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(T) * n, s));
-    cg_init<T><<<vb, kRedThreads, 0, s>>>(n, b, nullptr, r, p, part_vec);
-  } else {
-    if ((st = launch_apply(h, x, ap, nullptr)) != DG_OK) return st;
-    cg_init<T><<<vb, kRedThreads, 0, s>>>(n, b, ap, r, p, part_vec);
-  }
-  cg_scalars_init<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
-  DG_CUDA(h, cudaGetLastError());
-  DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
-  DG_CUDA(h, cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(h->scal_host[S_BB] > 0 ? h->scal_host[S_BB] : 1.0);
-  double rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
+  // run on a handle-owned stream (capturable), ordered after the caller's
+  cudaStream_t user = h->stream;
+  if (!h->cg_stream) DG_CUDA(h, cudaStreamCreateWithFlags(&h->cg_stream, cudaStreamNonBlocking));
+  if (!h->cg_event) DG_CUDA(h, cudaEventCreateWithFlags(&h->cg_event, cudaEventDisableTiming));
+  DG_CUDA(h, cudaEventRecord(h->cg_event, user));
+  DG_CUDA(h, cudaStreamWaitEvent(h->cg_stream, h->cg_event, 0));
+  cudaStream_t s = h->cg_stream;
+  h->stream = s;
+  dg_status st = DG_OK;
+  cudaGraphExec_t exec = nullptr;
   int it = 0;
-  st = DG_OK;
-  while (rel > rtol) {
-    if (it >= max_it) {
-      st = fail(h, DG_ERR_NOT_CONVERGED, "CG reached max_it");
+  double rel = 0.0, bnorm = 1.0;
+  do {
+    if (x_zero) {
+      DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(T) * n, s));
+      cg_init<T><<<vb, kRedThreads, 0, s>>>(n, b, nullptr, r, p, part_vec);
+    } else {
+      if ((st = launch_apply(h, x, ap, nullptr)) != DG_OK) break;
+      cg_init<T><<<vb, kRedThreads, 0, s>>>(n, b, ap, r, p, part_vec);
+    }
+    cg_scalars_init<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal, rtol, (double)max_it);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      st = cuda_fail(h, e, "CG set-up");
       break;
     }
-    // p.Ap is fused into the apply epilogue (per-block partials)
-    if ((st = launch_apply(h, p, ap, part_apply)) != DG_OK) return st;
-    cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply, nblk, h->scal);
-    cg_update<T><<<vb, kRedThreads, 0, s>>>(n, h->scal, x, r, p, ap, part_vec);
-    cg_scalars_beta<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
-    cg_direction<T><<<vb, kRedThreads, 0, s>>>(n, h->scal, r, p);
-    DG_CUDA(h, cudaGetLastError());
-    DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
-    DG_CUDA(h, cudaStreamSynchronize(s));
-    ++it;
-    if (h->scal_host[S_FLAG] != 0.0) {
-      st = fail(h, DG_ERR_BREAKDOWN, "CG breakdown: p.Ap <= 0 or non-finite scalar");
-      break;
+    // a block of kIterBlock iterations: apply with p.Ap fused into its
+    // epilogue, fused x/r update with r.r, direction update; captured once
+    // as a CUDA graph when the solve may be long
+    const int kIterBlock = 8;
+    auto enqueue_block = [&]() -> dg_status {
+      for (int j = 0; j < kIterBlock; ++j) {
+        dg_status s2 = launch_apply(h, p, ap, part_apply);
+        if (s2 != DG_OK) return s2;
+        cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply, nblk, h->scal);
+        cg_update<T><<<vb, kRedThreads, 0, s>>>(n, h->scal, x, r, p, ap, part_vec);
+        cg_scalars_beta<<<1, kRedThreads, 0, s>>>(part_vec, vb, h->scal);
+        cg_direction<T><<<vb, kRedThreads, 0, s>>>(n, h->scal, r, p);
+      }
+      return DG_OK;
+    };
+    if (max_it >= 4 * kIterBlock) {
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        dg_status s2 = enqueue_block();
+        cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        if (s2 == DG_OK && ec == cudaSuccess && graph) {
+          if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();  // a failed capture falls back to direct launches
     }
-    rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
-  }
+    while (true) {
+      DG_CUDA(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+      DG_CUDA(h, cudaStreamSynchronize(s));
+      if (it == 0 && rel == 0.0) bnorm = std::sqrt(h->scal_host[S_BB] > 0 ? h->scal_host[S_BB] : 1.0);
+      it = (int)h->scal_host[S_ITER];
+      rel = std::sqrt(h->scal_host[S_RR]) / bnorm;
+      if (h->scal_host[S_FLAG] != 0.0) {
+        st = fail(h, DG_ERR_BREAKDOWN, "CG breakdown: p.Ap <= 0 or non-finite scalar");
+        break;
+      }
+      if (h->scal_host[S_DONE] != 0.0) break;
+      if (h->scal_host[S_STOP] != 0.0 || it >= max_it) {
+        st = fail(h, DG_ERR_NOT_CONVERGED, "CG reached max_it");
+        break;
+      }
+      if (exec) {
+        cudaError_t e2 = cudaGraphLaunch(exec, s);
+        if (e2 != cudaSuccess) {
+          st = cuda_fail(h, e2, "CG graph launch");
+          break;
+        }
+      } else if ((st = enqueue_block()) != DG_OK) {
+        break;
+      }
+    }
+  } while (false);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaEventRecord(h->cg_event, s);
+  cudaStreamWaitEvent(user, h->cg_event, 0);
+  h->stream = user;
   *iters = it;
   *rel_out = rel;
   *bnorm_out = bnorm;
@@ -1171,7 +1250,7 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
     // outer FP64 residual r = b - A x and its norm; |b| on the first pass
     if ((st = launch_apply(h64, x, h64->ap, nullptr)) != DG_OK) break;
     cg_init<double><<<vb, kRedThreads, 0, s>>>(n, rhs, h64->ap, h64->r, h64->p, h64->partial);
-    cg_scalars_init<<<1, kRedThreads, 0, s>>>(h64->partial, vb, h64->scal);
+    cg_scalars_init<<<1, kRedThreads, 0, s>>>(h64->partial, vb, h64->scal, rtol, 0.0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h64->scal_host, h64->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
