@@ -220,6 +220,70 @@ def solve_metrics(torch, dgp, args, n=16, p=3, rtol=1e-10, repeats=20):
             "solves_per_s": 1.0 / float(np.mean(lat))}
 
 
+def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget_gb=40.0, seed=4):
+    """Many independent operators in one graph launch: count deformed-cube
+    meshes with n^3 cells, n log-uniform in [8, 48], degrees uniform in 1..7
+    (G3 geometry, kappa variable, Dirichlet).  Compares one dg_batch_launch
+    (autotuned tile shapes, 8 graph branches) with the same applies issued one
+    by one on a stream.  Meshes beyond the device-memory budget are dropped
+    (their count is reported)."""
+    rng = np.random.default_rng(seed)
+    ns = np.round(np.exp(rng.uniform(np.log(8), np.log(48), count))).astype(int)
+    ps = rng.integers(1, 8, count)
+    out = {"workload": "%d meshes, n^3 cells with n log-uniform in [8, 48], degree uniform in 1..7, G3" % count}
+    for prec in prec_list:
+        s = 4 if prec == "fp32" else 8
+        ops, srcs, dsts, used = [], [], [], 0.0
+        skipped = 0
+        for n, p in zip(ns, ps):
+            k = int(p) + 1
+            dofs = int(n) ** 3 * k ** 3
+            need = dofs * (bytes_per_dof(k, s, "sipg", "full") + 2 * s) / 1e9
+            if used + need > budget_gb:
+                skipped += 1
+                continue
+            used += need
+            op = dgp.Operator(int(n), int(p), geom="full", prec=prec, mapping=1, amplitude=0.1, coeff=1)
+            ops.append(op)
+            srcs.append(torch.tensor(dg_inputs.src_vector(op.n_dofs, int(n) * 31 + int(p)), dtype=op.dtype,
+                                     device="cuda"))
+            dsts.append(torch.empty_like(srcs[-1]))
+        total = sum(o.n_dofs for o in ops)
+        b = dgp.dg_batch_create([o.handle for o in ops], [x.data_ptr() for x in srcs], [x.data_ptr() for x in dsts],
+                                autotune=True, branches=8, stream=torch.cuda.current_stream().cuda_stream)
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            dgp.dg_batch_launch(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            dgp.dg_batch_launch(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) / reps
+        e0.record(stream)
+        for _ in range(reps):
+            for o, x, y in zip(ops, srcs, dsts):
+                o.apply(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_seq = e0.elapsed_time(e1) / reps
+        dgp.dg_batch_destroy(b)
+        out[prec] = {"operators": len(ops), "skipped_for_memory": skipped, "dofs": total,
+                     "ms_per_batch_launch": t_batch, "dofs_per_s": total / (t_batch / 1e3),
+                     "ms_sequential_applies": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+                     "cells_per_block_by_degree": {
+                         str(d): sorted({o.info()["cells_per_block"] for o in ops if o.degree == d})
+                         for d in sorted({o.degree for o in ops})}}
+        for o in ops:
+            o.close()
+        del srcs, dsts
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(workload, form, target_s=12.0):
     """The FP64 oracle (cell-by-cell brute-force quadrature, OpenMP on the
     host cores) on a seeded sample of cells of the same workload; DoFs/s =
@@ -396,6 +460,18 @@ def main():
                                        "frac": gbs / peaks["hbm_gbs"], "bytes_per_dof": b32,
                                        "alu_tflops": tf32, "alu_peak_tflops": FP32_PEAK_TFLOPS}}
         op32.close()
+        # emulated FP64 (double-float on the FP32 pipe), same workload and vectors
+        ope = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64emu", coeff=w["coeff"], **common)
+        for _ in range(args.warmup):
+            ope.apply(src, dst)
+        tote, le = time_applies(torch, ope, src, dst, args.steps)
+        extras["fp64_emulated"] = {
+            "value": n / (tote / args.steps / 1e3), "unit": UNIT, "ms_per_step": tote / args.steps,
+            "arithmetic": "double-float (pairs of binary32, error-free transformations) on the FP32 pipe; "
+                          "FP64 vectors; parity with the FP64 oracle at 1e-12",
+            "speedup_vs_fp64": (total_ms / args.steps) / (tote / args.steps),
+            "hbm": {"achieved": bpd * n / (le / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}}
+        ope.close()
         # advection, FP64
         opa = dgp.Operator(mesh["n"], p, geom=w["geom"], op="advection", prec="fp64", **common)
         for _ in range(args.warmup):
@@ -406,6 +482,7 @@ def main():
 
     if not args.no_extras and args.prec == "fp64":
         extras["solve"] = solve_metrics(torch, dgp, args)
+        extras["batch"] = batch_metrics(torch, dgp, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

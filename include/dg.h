@@ -210,6 +210,26 @@ dg_status dg_cg_solve_mixed(dg_handle *h64, dg_handle *h32, const double *rhs, d
                             int max_outer, double inner_rtol, int max_inner, int *outer_iters, int *inner_iters,
                             double *final_rel_res);
 
+/* Batched evaluation (spec extension; the paper evaluates one operator
+ * at a time).  A batch applies count set-up operators -- any mix of meshes,
+ * degrees, geometries and precisions -- with one CUDA graph launch.
+ * handles[i], srcs[i], dsts[i]: operator i and its device vectors (as for
+ * dg_apply); the pointers are fixed at creation.  autotune != 0 runs
+ * dg_autotune on every operator first (tile shape per operator).  branches
+ * (1..32): independent graph branches the applies are dealt to, largest
+ * first, so that small and large applies overlap on the device.  stream: the
+ * cudaStream_t dg_batch_launch launches on.  Creation performs one plain
+ * apply per operator, captures the graph and blocks until done.  The handles
+ * must outlive the batch and must not change tile shape afterwards. */
+typedef struct dg_batch dg_batch;
+dg_status dg_batch_create(dg_handle *const *handles, const void *const *srcs, void *const *dsts, int count,
+                          int autotune, int branches, void *stream, dg_batch **out);
+/* All applies of the batch, asynchronously on the batch's stream. */
+dg_status dg_batch_launch(dg_batch *b);
+dg_status dg_batch_destroy(dg_batch *b);
+/* Message of the last batch error of the calling thread. */
+const char *dg_batch_last_error(void);
+
 /* No counterpart in the paper: an allocation-free variant of the apply with
  * the FP64 product src . dst that the CG iteration fuses into the apply.
  *

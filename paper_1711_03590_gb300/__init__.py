@@ -47,7 +47,8 @@ PRECS = {"fp64": DG_FP64, "fp32": DG_FP32, "fp64emu": DG_FP64_EMU}
 
 EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
             "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
-            "dg_set_cells_per_block", "dg_autotune"]
+            "dg_set_cells_per_block", "dg_autotune", "dg_batch_create", "dg_batch_launch", "dg_batch_destroy",
+            "dg_batch_last_error"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -103,6 +104,11 @@ def load_library(path=None):
                               ctypes.POINTER(ctypes.c_double)]
     L.dg_apply_dot_noalloc.argtypes = [_vp, _vp, _vp, _vp]
     L.dg_set_cells_per_block.argtypes = [_vp, ctypes.c_int]
+    L.dg_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+    L.dg_batch_launch.argtypes = [_vp]
+    L.dg_batch_destroy.argtypes = [_vp]
+    L.dg_batch_last_error.argtypes = []
     L.dg_autotune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.dg_cg_solve_mixed.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -111,7 +117,7 @@ def load_library(path=None):
     L.dg_last_error.argtypes = [_vp]
     L.dg_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        getattr(L, name).restype = ctypes.c_int if name != "dg_last_error" else ctypes.c_char_p
+        getattr(L, name).restype = ctypes.c_char_p if name.endswith("last_error") else ctypes.c_int
     _lib = L
     return L
 
@@ -216,6 +222,33 @@ def dg_autotune(handle):
     ms = ctypes.c_double(0.0)
     _check(load_library().dg_autotune(_vp(handle), ctypes.byref(c), ctypes.byref(ms)), handle)
     return c.value, ms.value
+
+
+def dg_batch_create(handles, src_ptrs, dst_ptrs, autotune=True, branches=8, stream=None):
+    """Capture the applies of several operators into one CUDA graph; returns
+    the batch handle (an int)."""
+    L = load_library()
+    n = len(handles)
+    H = (_vp * n)(*handles)
+    S = (_vp * n)(*src_ptrs)
+    D = (_vp * n)(*dst_ptrs)
+    b = _vp()
+    st = L.dg_batch_create(H, S, D, n, int(bool(autotune)), int(branches), _vp(stream or 0), ctypes.byref(b))
+    if st != DG_OK:
+        raise DGError(st, L.dg_batch_last_error().decode())
+    return b.value
+
+
+def dg_batch_launch(batch):
+    L = load_library()
+    st = L.dg_batch_launch(_vp(batch))
+    if st != DG_OK:
+        raise DGError(st, L.dg_batch_last_error().decode())
+
+
+def dg_batch_destroy(batch):
+    if batch:
+        load_library().dg_batch_destroy(_vp(batch))
 
 
 def dg_destroy(handle):

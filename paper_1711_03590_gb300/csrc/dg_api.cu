@@ -1045,6 +1045,16 @@ dg_status dg_internal_apply_with_partials(dg_handle* h, const void* src, void* d
 }
 
 dg_status dg_internal_fail(dg_handle* h, dg_status s, const char* msg) { return fail(h, s, msg); }
+// Used by dg_batch.cu: dg_apply on a given stream (for graph capture).
+dg_status dg_internal_apply_on_stream(dg_handle* h, const void* src, void* dst, void* stream) {
+  if (!h) return DG_ERR_ARG;
+  cudaStream_t saved = h->stream;
+  h->stream = static_cast<cudaStream_t>(stream);
+  dg_status st = dg_apply(h, src, dst);
+  h->stream = saved;
+  return st;
+}
+
 
 // ---------------------------------------------------------------------------
 // C ABI
