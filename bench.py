@@ -284,6 +284,53 @@ def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget
     return out
 
 
+def serve_requests(dgp, count, seed, dof_lo=1e4, dof_hi=2e7, rtol=1e-8):
+    """Request mix: dofs lognormal over [dof_lo, dof_hi] (the interval is
+    +-2 standard deviations, clipped), degree uniform in 2..6, every other
+    request on a Cartesian mesh (kappa = 1) and the others on the sine-mapped
+    mesh with G3 geometry and kappa = 1 + 0.5 sin(2 pi x)."""
+    rng = np.random.default_rng(seed)
+    mu, sig = 0.5 * (np.log(dof_lo) + np.log(dof_hi)), (np.log(dof_hi) - np.log(dof_lo)) / 4
+    reqs = []
+    for i in range(count):
+        dofs = float(np.clip(np.exp(rng.normal(mu, sig)), dof_lo, dof_hi))
+        p = int(rng.integers(2, 7))
+        n = max(2, int(round((dofs / (p + 1) ** 3) ** (1.0 / 3.0))))
+        reqs.append(dgp.make_request(n, p, mapping=i % 2, rtol=rtol))
+    return reqs
+
+
+def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rates=(0.5, 0.9)):
+    """Continuous-batching solve server under Poisson arrivals: first all
+    requests at once (capacity in solves/s), then Poisson arrivals at given
+    fractions of that capacity; p50/p99 latency (submit to done) per rate."""
+    budget = int(budget_gb * (1 << 30))
+    reqs = serve_requests(dgp, count, seed, dof_hi=dof_hi)
+    out = {"requests": count, "slots": slots, "budget_gb": budget_gb,
+           "mix": "dofs lognormal over [1e4, %.0e], degree 2..6, half Cartesian / half deformed G3, "
+                  "mixed-precision CG to 1e-8" % dof_hi,
+           "total_dofs": int(sum(dgp.dg_request_device_bytes(r) * 0 + r.n[0] * r.n[1] * r.n[2] *
+                                 (r.degree + 1) ** 3 for r in reqs))}
+    res = dgp.serve_arrivals(reqs, [0.0] * count, budget, slots)
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    cap = count / span
+    out["saturated"] = {"solves_per_s": cap, "seconds": span,
+                        "all_converged": all(r["status"] == 0 and r["rel_res"] <= 1e-8 for r in res)}
+    rng = np.random.default_rng(seed + 1)
+    for frac in rates:
+        lam = frac * cap
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, count))
+        arrivals -= arrivals[0]
+        res = dgp.serve_arrivals(reqs, list(arrivals), budget, slots)
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        out["rate_%.2f_of_capacity" % frac] = {
+            "arrival_rate_per_s": lam, "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)), "solves_per_s": count / span,
+            "all_converged": all(r["status"] == 0 and r["rel_res"] <= 1e-8 for r in res)}
+    return out
+
+
 def cpu_baseline(workload, form, target_s=12.0):
     """The FP64 oracle (cell-by-cell brute-force quadrature, OpenMP on the
     host cores) on a seeded sample of cells of the same workload; DoFs/s =
@@ -483,6 +530,7 @@ def main():
     if not args.no_extras and args.prec == "fp64":
         extras["solve"] = solve_metrics(torch, dgp, args)
         extras["batch"] = batch_metrics(torch, dgp, args)
+        extras["serve"] = serve_metrics(dgp)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

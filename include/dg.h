@@ -102,6 +102,7 @@ typedef struct {
 } dg_opts;
 
 typedef struct dg_handle dg_handle;
+typedef struct dg_server dg_server;
 
 /* Static sizes of a set-up operator, for bandwidth accounting. */
 typedef struct {
@@ -229,6 +230,51 @@ dg_status dg_batch_launch(dg_batch *b);
 dg_status dg_batch_destroy(dg_batch *b);
 /* Message of the last batch error of the calling thread. */
 const char *dg_batch_last_error(void);
+
+/* Solve server (spec extension: serving with continuous batching).
+ * A request is a Poisson problem -div(kappa grad u) = f with the
+ * manufactured u = sin(pi x) sin(pi y) sin(pi z), Dirichlet boundary,
+ * solved by dg_cg_solve_mixed on its own FP64/FP32 operators.  Requests are
+ * queued in arrival order; `slots` worker threads (one CUDA stream each)
+ * admit the oldest request as soon as a slot is free and its estimated
+ * device memory (dg_request_device_bytes) fits into the remaining budget, so
+ * the work of all admitted requests overlaps on the device.  A result does
+ * not depend on the other requests (fixed-order reductions): it is the same
+ * alone and in the mix, bit for bit.  Device memory comes from the
+ * stream-ordered pool, which keeps freed memory for later requests. */
+typedef struct {
+  int n[3];            /* cells per direction */
+  int periodic;        /* 0 (Dirichlet) for the manufactured problem */
+  int mapping;         /* 0 identity, 1 sine map */
+  double amplitude;
+  int degree;          /* 1..8 */
+  int geom;            /* dg_geom (CARTESIAN needs mapping 0) */
+  int coeff;           /* kappa variant, as dg_opts.coeff */
+  int which_f;         /* right-hand side, as dg_rhs: 0 for coeff 0, 1 for coeff 1 */
+  double rtol;         /* outer relative residual */
+  double inner_rtol;   /* FP32 inner reduction per correction */
+  int max_outer, max_inner;
+  double *x_host;      /* optional: receives the n_dofs solution values (host memory) */
+} dg_request;
+
+typedef struct {
+  int status;          /* dg_status of the solve */
+  int outer_iters, inner_iters;
+  double rel_res;
+  int64_t n_dofs;
+  int64_t device_bytes;        /* the admission estimate */
+  double t_submit, t_admit, t_done;  /* seconds since the server was created */
+  char message[160];           /* error message when status != DG_OK */
+} dg_result;
+
+int64_t dg_request_device_bytes(const dg_request *r);
+dg_status dg_server_create(int device, int64_t budget_bytes, int slots, dg_server **out);
+dg_status dg_server_submit(dg_server *s, const dg_request *r, int64_t *ticket);
+/* Blocks until the request is done; each ticket can be waited for once. */
+dg_status dg_server_wait(dg_server *s, int64_t ticket, dg_result *out);
+/* Finishes every submitted request, then stops the workers. */
+dg_status dg_server_destroy(dg_server *s);
+const char *dg_server_last_error(void);
 
 /* No counterpart in the paper: an allocation-free variant of the apply with
  * the FP64 product src . dst that the CG iteration fuses into the apply.

@@ -48,7 +48,8 @@ PRECS = {"fp64": DG_FP64, "fp32": DG_FP32, "fp64emu": DG_FP64_EMU}
 EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
             "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
             "dg_set_cells_per_block", "dg_autotune", "dg_batch_create", "dg_batch_launch", "dg_batch_destroy",
-            "dg_batch_last_error"]
+            "dg_batch_last_error", "dg_request_device_bytes", "dg_server_create", "dg_server_submit",
+            "dg_server_wait", "dg_server_destroy", "dg_server_last_error"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -77,6 +78,21 @@ class dg_info_t(ctypes.Structure):
                 ("cell_geometry_bytes", ctypes.c_int64), ("face_geometry_bytes", ctypes.c_int64),
                 ("cells_per_block", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("shared_bytes_per_block", ctypes.c_int), ("blocks", ctypes.c_int64)]
+
+
+class dg_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("periodic", ctypes.c_int), ("mapping", ctypes.c_int),
+                ("amplitude", ctypes.c_double), ("degree", ctypes.c_int), ("geom", ctypes.c_int),
+                ("coeff", ctypes.c_int), ("which_f", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("x_host", ctypes.c_void_p)]
+
+
+class dg_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("n_dofs", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("message", ctypes.c_char * 160)]
 
 
 _lib = None
@@ -109,6 +125,12 @@ def load_library(path=None):
     L.dg_batch_launch.argtypes = [_vp]
     L.dg_batch_destroy.argtypes = [_vp]
     L.dg_batch_last_error.argtypes = []
+    L.dg_request_device_bytes.argtypes = [ctypes.POINTER(dg_request)]
+    L.dg_server_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(_vp)]
+    L.dg_server_submit.argtypes = [_vp, ctypes.POINTER(dg_request), ctypes.POINTER(ctypes.c_int64)]
+    L.dg_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(dg_result)]
+    L.dg_server_destroy.argtypes = [_vp]
+    L.dg_server_last_error.argtypes = []
     L.dg_autotune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.dg_cg_solve_mixed.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -118,6 +140,7 @@ def load_library(path=None):
     L.dg_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         getattr(L, name).restype = ctypes.c_char_p if name.endswith("last_error") else ctypes.c_int
+    L.dg_request_device_bytes.restype = ctypes.c_int64
     _lib = L
     return L
 
@@ -249,6 +272,78 @@ def dg_batch_launch(batch):
 def dg_batch_destroy(batch):
     if batch:
         load_library().dg_batch_destroy(_vp(batch))
+
+
+def make_request(n, degree, mapping=1, geom=None, coeff=None, rtol=1e-8, inner_rtol=1e-3, max_outer=50,
+                 max_inner=20000, x_host_ptr=None, amplitude=0.1):
+    """A manufactured Poisson solve request: deformed meshes use G3 geometry
+    and kappa = 1 + 0.5 sin(2 pi x), Cartesian meshes kappa = 1."""
+    if isinstance(n, int):
+        n = (n, n, n)
+    if geom is None:
+        geom = "full" if mapping else "cartesian"
+    if coeff is None:
+        coeff = 1 if mapping else 0
+    return dg_request((ctypes.c_int * 3)(*n), 0, int(mapping), float(amplitude), int(degree), GEOMS.get(geom, geom),
+                      int(coeff), int(coeff), float(rtol), float(inner_rtol), int(max_outer), int(max_inner),
+                      _vp(x_host_ptr or 0))
+
+
+def dg_request_device_bytes(req):
+    return load_library().dg_request_device_bytes(ctypes.byref(req))
+
+
+def dg_server_create(budget_bytes, slots, device=0):
+    L = load_library()
+    s = _vp()
+    st = L.dg_server_create(int(device), int(budget_bytes), int(slots), ctypes.byref(s))
+    if st != DG_OK:
+        raise DGError(st, L.dg_server_last_error().decode())
+    return s.value
+
+
+def dg_server_submit(server, req):
+    L = load_library()
+    t = ctypes.c_int64(0)
+    st = L.dg_server_submit(_vp(server), ctypes.byref(req), ctypes.byref(t))
+    if st != DG_OK:
+        raise DGError(st, L.dg_server_last_error().decode())
+    return t.value
+
+
+def dg_server_wait(server, ticket):
+    L = load_library()
+    r = dg_result()
+    st = L.dg_server_wait(_vp(server), int(ticket), ctypes.byref(r))
+    if st != DG_OK:
+        raise DGError(st, L.dg_server_last_error().decode())
+    out = {f: getattr(r, f) for f, _ in dg_result._fields_}
+    out["message"] = out["message"].decode(errors="replace")
+    return out
+
+
+def dg_server_destroy(server):
+    if server:
+        load_library().dg_server_destroy(_vp(server))
+
+
+def serve_arrivals(requests, arrivals, budget_bytes, slots):
+    """Submit requests at the given arrival times (seconds from now, sorted)
+    to a fresh server and wait for all; returns the result dicts in request
+    order (latency = t_done - t_submit)."""
+    import time
+    server = dg_server_create(budget_bytes, slots)
+    try:
+        tickets = []
+        start = time.perf_counter()
+        for req, t in zip(requests, arrivals):
+            delay = start + t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(dg_server_submit(server, req))
+        return [dg_server_wait(server, t) for t in tickets]
+    finally:
+        dg_server_destroy(server)
 
 
 def dg_destroy(handle):

@@ -250,7 +250,8 @@ struct dg_handle {
   double* partial;        // per-block partials
   int64_t partial_len;
   double* scal;           // device scalars
-  double* scal_host;      // pinned host copy
+  double* scal_host;      // host copy of the solver scalars (points into scal_buf)
+  double scal_buf[16];
   cudaStream_t cg_stream;  // solver stream (non-blocking, capturable) and ordering event
   cudaEvent_t cg_event;
   double* xw;             // extra work vectors (inner solution and right-hand side of
@@ -280,16 +281,25 @@ dg_status cuda_fail(dg_handle* h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
+// Device memory comes from the stream-ordered allocator (cudaMallocAsync on
+// the handle's stream): unlike cudaMalloc/cudaFree it does not synchronize the
+// device, so operators set up and torn down in one thread do not stall work
+// running on other streams.
 dg_status dev_alloc(dg_handle* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return DG_OK;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
-    return fail(h, DG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    *p = nullptr;
+    return fail(h, DG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   }
-  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMallocAsync");
   return DG_OK;
+}
+
+void dev_free(dg_handle* h, void* p) {
+  if (p) cudaFreeAsync(p, h->stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -806,8 +816,12 @@ dg_status setup_geometry(dg_handle* h) {
   dg_status st;
   if ((st = dev_alloc(h, (void**)&bad, sizeof(int))) != DG_OK) return st;
   DG_CUDA(h, cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
-  if ((st = dev_alloc(h, (void**)&part, sizeof(double) * ncq)) != DG_OK) { cudaFree(bad); return st; }
-  if ((st = dev_alloc(h, (void**)&vol, sizeof(double) * h->n_cells)) != DG_OK) { cudaFree(bad); cudaFree(part); return st; }
+  if ((st = dev_alloc(h, (void**)&part, sizeof(double) * ncq)) != DG_OK) { dev_free(h, bad); return st; }
+  if ((st = dev_alloc(h, (void**)&vol, sizeof(double) * h->n_cells)) != DG_OK) {
+    dev_free(h, bad);
+    dev_free(h, part);
+    return st;
+  }
 
   const bool cart = h->geom == DG_GEOM_CARTESIAN;
   int ncell_arrays = 0;
@@ -845,7 +859,7 @@ dg_status setup_geometry(dg_handle* h) {
       setup_face_tau<T><<<(unsigned)std::min<int64_t>((nf + threads - 1) / threads, 4096), threads, 0, h->stream>>>(
           S, d, nf, daw, vol, static_cast<T*>(h->face_tau[d]));
     cudaError_t e = cudaStreamSynchronize(h->stream);
-    cudaFree(daw);
+    dev_free(h, daw);
     if (e != cudaSuccess) st = cuda_fail(h, e, "face geometry kernels");
   }
   if (st == DG_OK) {
@@ -855,9 +869,9 @@ dg_status setup_geometry(dg_handle* h) {
     if (e != cudaSuccess) st = cuda_fail(h, e, "geometry set-up");
     else if (hbad) st = fail(h, DG_ERR_ARG, "mapping has a non-positive Jacobian determinant");
   }
-  cudaFree(bad);
-  cudaFree(part);
-  cudaFree(vol);
+  dev_free(h, bad);
+  dev_free(h, part);
+  dev_free(h, vol);
   return st;
 }
 
@@ -872,28 +886,28 @@ dg_status setup_kappa_table(dg_handle* h) {
   for (int i = 0; i <= n0; ++i) tab[(size_t)n0 * k + i] = (T)(1.0 + 0.5 * std::sin(2.0 * M_PI * i / n0));
   dg_status st = dev_alloc(h, &h->kappa_tab, sizeof(T) * tab.size());
   if (st != DG_OK) return st;
-  DG_CUDA(h, cudaMemcpy(h->kappa_tab, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice));
+  DG_CUDA(h, cudaMemcpyAsync(h->kappa_tab, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice, h->stream));
+  DG_CUDA(h, cudaStreamSynchronize(h->stream));
   return DG_OK;
 }
 
 void free_handle(dg_handle* h) {
   if (!h) return;
-  cudaFree(h->cell_geo);
+  dev_free(h, h->cell_geo);
   for (int d = 0; d < 3; ++d) {
-    cudaFree(h->face_geo[d]);
-    cudaFree(h->face_tau[d]);
+    dev_free(h, h->face_geo[d]);
+    dev_free(h, h->face_tau[d]);
   }
-  cudaFree(h->kappa_tab);
-  cudaFree(h->r);
-  cudaFree(h->p);
-  cudaFree(h->ap);
-  cudaFree(h->partial);
-  cudaFree(h->scal);
-  if (h->scal_host) cudaFreeHost(h->scal_host);
-  cudaFree(h->stage_src);
-  cudaFree(h->stage_dst);
-  cudaFree(h->xw);
-  cudaFree(h->bw);
+  dev_free(h, h->kappa_tab);
+  dev_free(h, h->r);
+  dev_free(h, h->p);
+  dev_free(h, h->ap);
+  dev_free(h, h->partial);
+  dev_free(h, h->scal);
+  dev_free(h, h->stage_src);
+  dev_free(h, h->stage_dst);
+  dev_free(h, h->xw);
+  dev_free(h, h->bw);
   if (h->cg_stream) cudaStreamDestroy(h->cg_stream);
   if (h->cg_event) cudaEventDestroy(h->cg_event);
   delete h;
@@ -913,12 +927,19 @@ dg_status ensure_cg_work(dg_handle* h, bool with_extra) {
     h->partial_len = 2 * kRedBlocks + h->n_cells;  // apply partials for any block size
     if ((st = dev_alloc(h, (void**)&h->partial, sizeof(double) * h->partial_len)) != DG_OK) return st;
     if ((st = dev_alloc(h, (void**)&h->scal, sizeof(double) * S_COUNT)) != DG_OK) return st;
-    DG_CUDA(h, cudaMallocHost((void**)&h->scal_host, sizeof(double) * S_COUNT));
   }
   if (with_extra && !h->xw) {
     if ((st = dev_alloc(h, (void**)&h->xw, sizeof(double) * n)) != DG_OK) return st;
     if ((st = dev_alloc(h, (void**)&h->bw, sizeof(double) * n)) != DG_OK) return st;
   }
+  // Scalars are read back into handle memory (a small pageable copy after a
+  // stream synchronization anyway); no page-locked allocation, which would
+  // synchronize the whole device and disturb solves captured as graphs in
+  // other threads.
+  h->scal_host = h->scal_buf;
+  // the work vectors are used on other streams (the solver's); make the
+  // stream-ordered allocations complete first
+  DG_CUDA(h, cudaStreamSynchronize(h->stream));
   return DG_OK;
 }
 

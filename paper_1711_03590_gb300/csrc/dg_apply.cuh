@@ -876,7 +876,10 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
       if (dot) acc += A::to_double(v) * (double)s[i];
     }
     if (dot) {
-      double* red = reinterpret_cast<double*>(G);
+      // the gradient region is free now; its start rounded up to 8 bytes
+      // (C k^3 binary32 values can be an odd count) holds blockDim doubles
+      double* red = reinterpret_cast<double*>(
+          smem_raw + ((size_t)C * K3 * sizeof(T) + 7) / 8 * 8);
       red[tid] = acc;
       __syncthreads();
       if (tid == 0) {

@@ -62,3 +62,29 @@ def test_mixed_precision_argument_checks():
     st, outer, inner, rr = dgp.dg_cg_solve_mixed(o64.handle, o32.handle, rhs.data_ptr(), x.data_ptr(), 1e-12,
                                                  max_outer=1, raise_on_error=False)
     assert st == dgp.DG_ERR_NOT_CONVERGED and outer == 1
+
+
+@pytest.mark.parametrize("p,cpb", [(6, 5), (4, 5), (2, 1)])
+def test_fp32_dot_epilogue_with_odd_block_storage(p, cpb):
+    """The apply's src.dst epilogue reduces in shared memory behind an odd
+    number of binary32 values (C k^3 odd): the reduction buffer must be
+    8-byte aligned.  Checked through the mixed solve on a Cartesian mesh and
+    the allocation-free dot entry point."""
+    dgp.build()
+    o32 = dgp.Operator((4, 3, 5), p, geom="cartesian", prec="fp32")
+    o64 = dgp.Operator((4, 3, 5), p, geom="cartesian", prec="fp64")
+    o32.set_cells_per_block(cpb)
+    assert (o32.info()["cells_per_block"] * (p + 1) ** 3) % 2 == 1
+    src = torch.tensor(np.random.default_rng(p).uniform(-1, 1, o32.n_dofs), dtype=torch.float32, device="cuda")
+    dst = torch.empty_like(src)
+    dot = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dgp.dg_apply_dot_noalloc(o32.handle, src.data_ptr(), dst.data_ptr(), dot.data_ptr())
+    torch.cuda.synchronize()
+    want = float(torch.dot(src.double(), dst.double()))
+    assert abs(float(dot.item()) - want) <= 1e-5 * float(src.double().norm() * dst.double().norm())
+    rhs = o64.rhs(0)
+    x = torch.zeros_like(rhs)
+    st, outer, inner, rr = dgp.dg_cg_solve_mixed(o64.handle, o32.handle, rhs.data_ptr(), x.data_ptr(), 1e-8)
+    assert st == dgp.DG_OK and rr <= 1e-8
+    o32.close()
+    o64.close()
