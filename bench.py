@@ -157,6 +157,18 @@ def summarize_clocks(rows, t0, t1):
             "power_w_max": max(float(r[4]) for r in sel if r[4].replace(".", "").isdigit()) if sel else None}
 
 
+def aggregate_ranks(torch, dist, total_ms, steps, units_per_step, world, device):
+    """Whole-job throughput over independent replicas: the slowest rank's
+    time (all-reduce MAX) and all ranks' units over it.  Returns
+    (max total ms, units per second)."""
+    t_max = total_ms
+    if dist is not None and world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, world * units_per_step * steps / (t_max / 1e3)
+
+
 def time_applies(torch, op, src, dst, steps, per_launch=True):
     """Device time of `steps` applies on the operator's stream (CUDA events),
     and the average duration of one apply launch from per-launch events."""
@@ -451,13 +463,8 @@ def main():
     rows = sampler.stop()
     clocks = summarize_clocks(rows, t0, t1)
     torch.cuda.synchronize()
-    t_max = total_ms
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max, value = aggregate_ranks(torch, dist, total_ms, args.steps, n, world, "cuda")
     ms_per_step = t_max / args.steps
-    value = world * n / (ms_per_step / 1e3)
 
     # roofline of the apply kernel (the only kernel of a step)
     flops = kernel_flops_per_cell(k, "sipg", w["geom"]) * n_cells
