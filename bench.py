@@ -343,6 +343,45 @@ def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rat
     return out
 
 
+def config3_metrics(torch, dgp, rtol=1e-10, cases=(("cartesian_64^3_p3", 64, 3, 0), ("deformed_48^3_p3", 48, 3, 1),
+                                                   ("deformed_48^3_p5", 48, 5, 1))):
+    """Mixed precision at full size: manufactured Poisson problems solved to
+    rtol by plain FP64 CG, by the mixed solver (FP64 outer residual) and by
+    the mixed solver with the emulated-FP64 outer residual; wall time,
+    iterations, L2 errors against the exact solution and the difference
+    between the mixed and the FP64 solutions."""
+    out = {}
+    for name, n, p, mapping in cases:
+        kw = dict(geom="full" if mapping else "cartesian", mapping=mapping, amplitude=0.1, coeff=mapping)
+        o64 = dgp.Operator(n, p, prec="fp64", **kw)
+        o32 = dgp.Operator(n, p, prec="fp32", **kw)
+        oe = dgp.Operator(n, p, prec="fp64emu", **kw)
+        rhs = o64.rhs(mapping)
+        res = {"dofs": o64.n_dofs, "rtol": rtol}
+        x64 = torch.zeros_like(rhs)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, it, rr, st = o64.cg(rhs, x64, rtol=rtol, max_it=200000, raise_on_error=False)
+        res["fp64_cg"] = {"seconds": time.perf_counter() - t, "iterations": it, "rel_res": rr, "status": st,
+                          "l2_error": o64.l2_error(x64)}
+        for label, oh in (("mixed_fp64_outer", o64), ("mixed_emulated_fp64_outer", oe)):
+            xm = torch.zeros_like(rhs)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st, outer, inner, rr = dgp.dg_cg_solve_mixed(oh.handle, o32.handle, rhs.data_ptr(), xm.data_ptr(), rtol,
+                                                         max_outer=100, max_inner=200000, raise_on_error=False)
+            secs = time.perf_counter() - t
+            res[label] = {"seconds": secs, "outer": outer, "inner_fp32_iterations": inner, "rel_res": rr,
+                          "status": st, "l2_error": o64.l2_error(xm),
+                          "rel_diff_to_fp64_solution": float((xm - x64).norm() / x64.norm()),
+                          "speedup_vs_fp64_cg": res["fp64_cg"]["seconds"] / secs}
+        out[name] = res
+        for o in (o64, o32, oe):
+            o.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(workload, form, target_s=12.0):
     """The FP64 oracle (cell-by-cell brute-force quadrature, OpenMP on the
     host cores) on a seeded sample of cells of the same workload; DoFs/s =
@@ -415,6 +454,8 @@ def main():
                     help="precision of the headline apply")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--solve-config3", action="store_true",
+                    help="only run the full-size mixed-precision solves and print their JSON")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -434,6 +475,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+
+    if args.solve_config3:
+        if rank == 0:
+            print(json.dumps({"solve_config3": config3_metrics(torch, dgp)}), flush=True)
+        return
 
     wname = "deformed_dirichlet_32^3_p%d" % args.degree
     w = dg_inputs.workload(wname)

@@ -177,6 +177,12 @@ dg_status dg_apply_host(dg_handle *h, const void *src_host, void *dst_host);
  * rhs: device pointer to n_dofs doubles.  Asynchronous. */
 dg_status dg_rhs(dg_handle *h, int which_f, double *rhs);
 
+/* err = || u_h - u ||_{L2(Omega)} for the coefficient vector x (device, n_dofs
+ * doubles) against the manufactured u = sin(pi x) sin(pi y) sin(pi z), by the
+ * (k+2)-point Gauss rule per direction on the mapped cells.  Synchronous.
+ * (Evaluation aid for the solvers; the paper reports no solves.) */
+dg_status dg_l2_error(dg_handle *h, const double *x, double *err);
+
 /* Conjugate gradients for A x = rhs (SIPG only; DG_ERR_UNSUPPORTED for
  * advection, which is not symmetric).  rhs, x: device pointers to n_dofs
  * doubles; x holds the initial guess on entry and the last iterate on exit.

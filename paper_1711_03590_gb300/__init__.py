@@ -49,7 +49,7 @@ EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg
             "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
             "dg_set_cells_per_block", "dg_autotune", "dg_batch_create", "dg_batch_launch", "dg_batch_destroy",
             "dg_batch_last_error", "dg_request_device_bytes", "dg_server_create", "dg_server_submit",
-            "dg_server_wait", "dg_server_destroy", "dg_server_last_error"]
+            "dg_server_wait", "dg_server_destroy", "dg_server_last_error", "dg_l2_error"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -126,6 +126,7 @@ def load_library(path=None):
     L.dg_batch_destroy.argtypes = [_vp]
     L.dg_batch_last_error.argtypes = []
     L.dg_request_device_bytes.argtypes = [ctypes.POINTER(dg_request)]
+    L.dg_l2_error.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double)]
     L.dg_server_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(_vp)]
     L.dg_server_submit.argtypes = [_vp, ctypes.POINTER(dg_request), ctypes.POINTER(ctypes.c_int64)]
     L.dg_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(dg_result)]
@@ -204,6 +205,12 @@ def dg_apply_dot_noalloc(handle, src_ptr, dst_ptr, dot_ptr):
     """dst = A src and *dot = src . dst without any device allocation (the
     partial sums live in a fixed static device array of the library)."""
     _check(load_library().dg_apply_dot_noalloc(_vp(handle), _vp(src_ptr), _vp(dst_ptr), _vp(dot_ptr)), handle)
+
+
+def dg_l2_error(handle, x_ptr):
+    e = ctypes.c_double(0.0)
+    _check(load_library().dg_l2_error(_vp(handle), _vp(x_ptr), ctypes.byref(e)), handle)
+    return e.value
 
 
 def dg_rhs(handle, which_f, rhs_ptr):
@@ -415,6 +422,11 @@ class Operator:
 
     def info(self):
         return dg_info(self.handle)
+
+    def l2_error(self, x):
+        import torch
+        self._check_tensor(x, torch.float64)
+        return dg_l2_error(self.handle, x.data_ptr())
 
     def set_cells_per_block(self, cpb):
         dg_set_cells_per_block(self.handle, cpb)

@@ -552,6 +552,47 @@ __global__ void rhs_kernel(const __grid_constant__ RhsParams R, int64_t n_cells,
 }
 
 // ---------------------------------------------------------------------------
+// L2 error against the manufactured solution u = sin(pi x) sin(pi y) sin(pi z),
+// (k+2)-point Gauss rule, one block per cell, one partial per block
+// ---------------------------------------------------------------------------
+__global__ void l2_error_kernel(const __grid_constant__ RhsParams R, int64_t n_cells, const double* x,
+                                double* part) {
+  extern __shared__ double xs[];  // the cell's k^3 coefficients
+  __shared__ double red[128];
+  const int k = R.S.k, kq = R.kq, nq = kq * kq * kq, k3 = k * k * k;
+  double acc = 0.0;
+  for (int64_t c = blockIdx.x; c < n_cells; c += gridDim.x) {
+    for (int i = threadIdx.x; i < k3; i += blockDim.x) xs[i] = x[c * k3 + i];
+    __syncthreads();
+    int ijk[3];
+    cell_of(R.S, c, ijk);
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      const int q0 = q % kq, q1 = (q / kq) % kq, q2 = q / (kq * kq);
+      const double xi[3] = {R.xq[q0], R.xq[q1], R.xq[q2]};
+      double xp[3], J[9], Ji[9];
+      map_point(R.S, ijk, xi, xp, J);
+      const double det = invert3(J, Ji);
+      double uh = 0.0;
+      for (int i2 = 0; i2 < k; ++i2)
+        for (int i1 = 0; i1 < k; ++i1) {
+          const double f12 = R.phi[q1 * k + i1] * R.phi[q2 * k + i2];
+          for (int i0 = 0; i0 < k; ++i0) uh += xs[i0 + k * (i1 + k * i2)] * R.phi[q0 * k + i0] * f12;
+        }
+      const double e = uh - sinpi(xp[0]) * sinpi(xp[1]) * sinpi(xp[2]);
+      acc += e * e * det * R.wq[q0] * R.wq[q1] * R.wq[q2];
+    }
+    __syncthreads();
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// ---------------------------------------------------------------------------
 // CG vector kernels.  Reductions: per-block partials in a fixed order, then a
 // single-block fixed-order pass, so every sum is reproducible bit for bit.
 // ---------------------------------------------------------------------------
@@ -1204,11 +1245,7 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
   return DG_OK;
 }
 
-dg_status dg_rhs(dg_handle* h, int which_f, double* rhs) {
-  if (!h) return DG_ERR_ARG;
-  if (!rhs) return fail(h, DG_ERR_ARG, "rhs is NULL");
-  if (which_f != 0 && which_f != 1) return fail(h, DG_ERR_ARG, "which_f must be 0 or 1");
-  RhsParams R;
+static void fill_rhs_params(const dg_handle* h, int which_f, RhsParams& R) {
   memset(&R, 0, sizeof(R));
   for (int d = 0; d < 3; ++d) R.S.n[d] = h->mesh.n[d];
   R.S.periodic = h->mesh.periodic;
@@ -1225,6 +1262,36 @@ dg_status dg_rhs(dg_handle* h, int which_f, double* rhs) {
     R.wq[q] = wq[q];
     bary_values(h->k, h->t64.gl, lam, xq[q], R.phi + q * h->k);
   }
+}
+
+dg_status dg_l2_error(dg_handle* h, const double* x, double* err) {
+  if (!h) return DG_ERR_ARG;
+  if (!x || !err) return fail(h, DG_ERR_ARG, "x or err is NULL");
+  RhsParams R;
+  fill_rhs_params(h, 0, R);
+  const int nblk = (int)std::min<int64_t>(h->n_cells, 152 * 16);
+  double* part = nullptr;
+  dg_status st = dev_alloc(h, (void**)&part, sizeof(double) * nblk);
+  if (st != DG_OK) return st;
+  l2_error_kernel<<<nblk, 128, sizeof(double) * h->k * h->k * h->k, h->stream>>>(R, h->n_cells, x, part);
+  std::vector<double> hp(nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * nblk, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, part);
+  if (e != cudaSuccess) return cuda_fail(h, e, "L2 error kernel");
+  double sum = 0.0;
+  for (double v : hp) sum += v;
+  *err = std::sqrt(sum);
+  return DG_OK;
+}
+
+dg_status dg_rhs(dg_handle* h, int which_f, double* rhs) {
+  if (!h) return DG_ERR_ARG;
+  if (!rhs) return fail(h, DG_ERR_ARG, "rhs is NULL");
+  if (which_f != 0 && which_f != 1) return fail(h, DG_ERR_ARG, "which_f must be 0 or 1");
+  RhsParams R;
+  fill_rhs_params(h, which_f, R);
   const int nq = R.kq * R.kq * R.kq;
   rhs_kernel<<<(unsigned)std::min<int64_t>(h->n_cells, 152 * 16), 128, sizeof(double) * nq, h->stream>>>(R, h->n_cells,
                                                                                                          rhs);

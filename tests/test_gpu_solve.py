@@ -88,3 +88,18 @@ def test_fp32_dot_epilogue_with_odd_block_storage(p, cpb):
     assert st == dgp.DG_OK and rr <= 1e-8
     o32.close()
     o64.close()
+
+
+def test_l2_error_matches_oracle():
+    dgp.build()
+    for mesh, p in ((dict(n=(3, 4, 2), periodic=False, mapping=1, amplitude=0.1), 3),
+                    (dict(n=(4, 4, 4), periodic=False, mapping=0, amplitude=0.1), 5)):
+        op = dgp.Operator(mesh["n"], p, geom="full" if mesh["mapping"] else "cartesian", mapping=mesh["mapping"],
+                          coeff=mesh["mapping"])
+        x = np.random.default_rng(2).uniform(-1, 1, op.n_dofs) * 0.1
+        pts = oracle.dof_points(mesh, p)
+        x += np.sin(np.pi * pts[:, 0]) * np.sin(np.pi * pts[:, 1]) * np.sin(np.pi * pts[:, 2])
+        got = op.l2_error(torch.tensor(x, device="cuda"))
+        ref = oracle.l2_error(mesh, p, x)
+        assert abs(got - ref) <= 1e-12 * ref
+        op.close()
