@@ -69,13 +69,17 @@ def kernel_flops_per_cell(k, op, geom):
 def bytes_per_dof(k, s, op, geom):
     """Algorithmic bytes per dof of one apply: src read and dst write, the
     cell geometry per point, the face geometry per face point (3 faces per
-    cell, k^2 points each) and the penalty per face."""
+    cell, k^2 points each) and the penalty per face.  SIPG face arrays: both
+    sides' J^{-T} n and kappa da w (7 values) in binary64; in binary32 one
+    J^{-T} e_d (the two sides' vectors differ only in sign) and kappa da w
+    (4 values)."""
     vec = 2 * s
     if geom == "cartesian":
         return vec
     cell = {("sipg", "full"): 10, ("advection", "full"): 10, ("sipg", "merged"): 6,
             ("advection", "merged"): 3}[(op, geom)] * s
-    face = (7 * s * 3 / k + 3 * s / k ** 3) if op == "sipg" else (1 * s * 3 / k)
+    nfa = (4 if s == 4 else 7) if op == "sipg" else 1
+    face = nfa * s * 3 / k + (3 * s / k ** 3 if op == "sipg" else 0)
     return vec + cell + face
 
 

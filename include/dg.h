@@ -118,6 +118,7 @@ typedef struct {
   int threads_per_block;
   int shared_bytes_per_block;
   int64_t blocks;               /* blocks of one apply launch */
+  int tile_choices[24];         /* valid cells_per_block values, ascending, 0-terminated */
 } dg_info_t;
 
 /* Build an operator: 1D tables, geometry arrays and work buffers on the
@@ -144,12 +145,15 @@ dg_status dg_info(const dg_handle *h, dg_info_t *info);
 /* Change the stream used by later calls. */
 dg_status dg_set_stream(dg_handle *h, void *stream);
 
-/* Tile shape of the apply kernel: cells per CUDA block (k^2 threads each),
- * 1 .. floor(256 / k^2); 0 restores the default (the maximum).  Results do
- * not depend on it (each cell's arithmetic is the same).  Synchronous. */
+/* Tile shape of the apply kernel: cells per CUDA block (k^2 threads each).
+ * Valid values are listed in dg_info_t.tile_choices: for DG_FP64 and
+ * DG_FP64_EMU any value 1 .. floor(256 / k^2) (the autotuner tries a subset),
+ * for DG_FP32 one of the two compiled shapes.  0 restores the default.
+ * Results do not depend on it (each cell's arithmetic is the same); an
+ * invalid value returns DG_ERR_ARG.  Synchronous. */
 dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
 
-/* Autotuner: times the apply for every candidate cells-per-block value on
+/* Autotuner: times the apply for every value in tile_choices on
  * the handle's stream (CUDA events, warm-up first) and keeps the fastest.
  * Uses handle-owned staging buffers (allocated on first use).  best_cpb and
  * best_ms (may be NULL) receive the choice and its time per apply.
@@ -211,13 +215,13 @@ dg_status dg_cg_solve(dg_handle *h, const double *rhs, double *x, double rtol, i
  * on h64's stream.  Returns DG_ERR_NOT_CONVERGED after max_outer corrections,
  * DG_ERR_BREAKDOWN on a non-finite residual or an inner CG breakdown.
  * outer_iters, inner_iters (total FP32 iterations), final_rel_res may be
- * NULL.  Synchronous.  (North-star extension; the paper's solvers are only
+ * NULL.  Synchronous.  (Beyond the paper, whose solvers are only
  * referred to in Sec. 1 and Sec. 6.) */
 dg_status dg_cg_solve_mixed(dg_handle *h64, dg_handle *h32, const double *rhs, double *x, double rtol,
                             int max_outer, double inner_rtol, int max_inner, int *outer_iters, int *inner_iters,
                             double *final_rel_res);
 
-/* Batched evaluation (spec extension; the paper evaluates one operator
+/* Batched evaluation (beyond the paper, which evaluates one operator
  * at a time).  A batch applies count set-up operators -- any mix of meshes,
  * degrees, geometries and precisions -- with one CUDA graph launch.
  * handles[i], srcs[i], dsts[i]: operator i and its device vectors (as for
@@ -237,7 +241,7 @@ dg_status dg_batch_destroy(dg_batch *b);
 /* Message of the last batch error of the calling thread. */
 const char *dg_batch_last_error(void);
 
-/* Solve server (spec extension: serving with continuous batching).
+/* Solve server (beyond the paper: serving with continuous batching).
  * A request is a Poisson problem -div(kappa grad u) = f with the
  * manufactured u = sin(pi x) sin(pi y) sin(pi z), Dirichlet boundary,
  * solved by dg_cg_solve_mixed on its own FP64/FP32 operators.  Requests are

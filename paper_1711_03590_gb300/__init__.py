@@ -77,7 +77,8 @@ class dg_info_t(ctypes.Structure):
                 ("prec", ctypes.c_int), ("geom", ctypes.c_int), ("op", ctypes.c_int),
                 ("cell_geometry_bytes", ctypes.c_int64), ("face_geometry_bytes", ctypes.c_int64),
                 ("cells_per_block", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-                ("shared_bytes_per_block", ctypes.c_int), ("blocks", ctypes.c_int64)]
+                ("shared_bytes_per_block", ctypes.c_int), ("blocks", ctypes.c_int64),
+                ("tile_choices", ctypes.c_int * 24)]
 
 
 class dg_request(ctypes.Structure):
@@ -186,7 +187,9 @@ def dg_n_dofs(handle):
 def dg_info(handle):
     info = dg_info_t()
     _check(load_library().dg_info(_vp(handle), ctypes.byref(info)), handle)
-    return {f: getattr(info, f) for f, _ in dg_info_t._fields_}
+    out = {f: getattr(info, f) for f, _ in dg_info_t._fields_}
+    out["tile_choices"] = [c for c in info.tile_choices if c > 0]
+    return out
 
 
 def dg_set_stream(handle, stream):

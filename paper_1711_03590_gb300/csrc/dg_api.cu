@@ -316,7 +316,20 @@ struct SetupParams {
   int op, coeff, geom;
   double vel[3];
   double penalty;  // penalty_scale (p+1)^2
+  int cblk;        // cell arrays: 0 = structure of arrays, else cell-blocked with this width
+  int ncomp;       // number of cell arrays
+  int face_minor;  // face arrays: 0 = [array][face][point], 1 = [array][point][face] with faces
+                   // numbered like cells (x fastest; the face position replaces the index along d)
+  int face_pair;   // binary32 SIPG: both sides' J^{-T} n (else one vector, see setup_face_geometry)
 };
+
+// Position of face f (numbered pos + P_d (i_t1 + n_t1 i_t2)) and point q in
+// a face array of direction d, for the layout selected by S.face_minor.
+__device__ int64_t face_slot(const SetupParams& S, int d, int64_t f, int q, int64_t n_faces) {
+  const int k2 = S.k * S.k;
+  if (!S.face_minor) return f * k2 + q;
+  return (int64_t)q * n_faces + dg::face_minor_id(S.n, S.P, d, f);
+}
 
 // x = X + a s(X)(1,1,1), s = sin(pi X) sin(pi Y) sin(pi Z); J = dx/dxi includes 1/n_d
 __device__ void map_point(const SetupParams& S, const int ijk[3], const double xi[3], double x[3], double J[9]) {
@@ -384,20 +397,24 @@ __global__ void setup_cell_geometry(const SetupParams S, int64_t n_cells, T* out
     const double jxw = det * S.gw[q0] * S.gw[q1] * S.gw[q2];
     vol_part[idx] = jxw;
     if (!out) continue;
+    // element index of array m at this point
+    auto at = [&](int m) -> int64_t {
+      return S.cblk ? (((c / S.cblk) * S.ncomp + m) * (int64_t)k3 + q) * S.cblk + c % S.cblk : m * ncq + idx;
+    };
     if (S.geom == dg::GEO_FULL) {
-      for (int m = 0; m < 9; ++m) out[m * ncq + idx] = (T)Ji[m];
-      out[9 * ncq + idx] = (T)(S.op == dg::OP_SIPG ? kappa_of(S, x) * jxw : jxw);
+      for (int m = 0; m < 9; ++m) out[at(m)] = (T)Ji[m];
+      out[at(9)] = (T)(S.op == dg::OP_SIPG ? kappa_of(S, x) * jxw : jxw);
     } else if (S.op == dg::OP_SIPG) {
       const double kw = kappa_of(S, x) * jxw;
       const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
       for (int m = 0; m < 6; ++m) {
         double g = 0.0;
         for (int c2 = 0; c2 < 3; ++c2) g += Ji[ia[m] * 3 + c2] * Ji[ib[m] * 3 + c2];
-        out[m * ncq + idx] = (T)(kw * g);
+        out[at(m)] = (T)(kw * g);
       }
     } else {
       for (int a = 0; a < 3; ++a)
-        out[a * ncq + idx] = (T)(-jxw * (Ji[a * 3 + 0] * S.vel[0] + Ji[a * 3 + 1] * S.vel[1] + Ji[a * 3 + 2] * S.vel[2]));
+        out[at(a)] = (T)(-jxw * (Ji[a * 3 + 0] * S.vel[0] + Ji[a * 3 + 1] * S.vel[1] + Ji[a * 3 + 2] * S.vel[2]));
     }
   }
 }
@@ -462,15 +479,24 @@ __global__ void setup_face_geometry(const SetupParams S, int d, int64_t n_faces,
       }
     }
     daw_out[idx] = daw;
-    if (S.op == dg::OP_SIPG) {
+    const int64_t oi = face_slot(S, d, f, q, n_faces);
+    if (S.op == dg::OP_SIPG && S.face_minor && !S.face_pair) {
+      // one vector per face point: J^{-T} n for n = +e_d.  Inside the
+      // domain the mapping is smooth, so both sides evaluate the same J at
+      // the face and their vectors differ only in the normal's sign (slot 1
+      // = -slot 0).  (Not across a periodic boundary of a deformed mesh,
+      // where the sine mapping's derivative changes sign: face_pair.)
+      for (int a = 0; a < 3; ++a) out[a * nfq + oi] = (T)(has[0] ? jn[0][a] : -jn[1][a]);
+      out[3 * nfq + oi] = (T)(kap * daw);
+    } else if (S.op == dg::OP_SIPG) {
       for (int slot = 0; slot < 2; ++slot)
-        for (int a = 0; a < 3; ++a) out[(slot * 3 + a) * nfq + idx] = (T)jn[slot][a];
-      out[6 * nfq + idx] = (T)(kap * daw);
+        for (int a = 0; a < 3; ++a) out[(slot * 3 + a) * nfq + oi] = (T)jn[slot][a];
+      out[6 * nfq + oi] = (T)(kap * daw);
     } else {
       // c.n da w with n the normal pointing to +d (outward normal of the lower side)
       double n[3];
       for (int a = 0; a < 3; ++a) n[a] = has[0] ? nrm[0][a] : -nrm[1][a];
-      out[idx] = (T)((S.vel[0] * n[0] + S.vel[1] * n[1] + S.vel[2] * n[2]) * daw);
+      out[oi] = (T)((S.vel[0] * n[0] + S.vel[1] * n[1] + S.vel[2] * n[2]) * daw);
     }
   }
 }
@@ -497,7 +523,7 @@ __global__ void setup_face_tau(const SetupParams S, int d, int64_t n_faces, cons
       const int64_t c = ijk[0] + (int64_t)S.n[0] * (ijk[1] + (int64_t)S.n[1] * ijk[2]);
       r = fmax(r, A / vol[c]);
     }
-    tau[f] = (T)(S.penalty * r);
+    tau[S.face_minor ? dg::face_minor_id(S.n, S.P, d, f) : f] = (T)(S.penalty * r);
   }
 }
 
@@ -758,6 +784,18 @@ __global__ void sum_to_scalar(const double* part, int64_t nparts, double* out) {
   if (threadIdx.x == 0) *out = v;
 }
 
+// Valid cells-per-block values of an operator's apply kernel, ascending:
+// the binary32 kernel's two compiled tile shapes, else the autotuner's
+// candidates up to the largest block.
+std::vector<int> tile_choices(const dg_handle* h) {
+  if (h->prec == DG_FP32) return {dg::f32_tile_small(h->k), dg::f32_geometry_block(h->k)};
+  static const int cands[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64};
+  std::vector<int> out;
+  for (int c : cands)
+    if (c <= dg::cells_per_block(h->k)) out.push_back(c);
+  return out;
+}
+
 int64_t apply_blocks(const dg_handle* h) {
   const int C = h->cpb;
   return (h->n_cells + C - 1) / C;
@@ -812,6 +850,8 @@ void fill_geometry(dg_handle* h, dg::Geometry<T>& g) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     const int64_t nf = (int64_t)g.P[d] * h->mesh.n[t1] * h->mesh.n[t2];
     g.nfq[d] = nf * k2;
+    g.nfc[d] = (int)nf;
+    g.face_pair = h->mesh.periodic && h->mesh.mapping != 0;
     g.face[d] = static_cast<const T*>(h->face_geo[d]);
     g.tau[d] = static_cast<const T*>(h->face_tau[d]);
   }
@@ -870,8 +910,18 @@ dg_status setup_geometry(dg_handle* h) {
     if (h->geom == DG_GEOM_FULL_JAC) ncell_arrays = 10;
     else ncell_arrays = h->op == DG_OP_SIPG ? 6 : 3;
   }
-  h->cell_bytes = (int64_t)ncell_arrays * ncq * sizeof(T);
+  // binary32: cell-blocked layout padded to whole blocks (zero padding)
+  S.ncomp = ncell_arrays;
+  S.cblk = h->prec == DG_FP32 ? dg::f32_geometry_block(k) : 0;
+  S.face_minor = h->prec == DG_FP32 ? 1 : 0;
+  S.face_pair = S.face_minor && h->mesh.periodic && h->mesh.mapping != 0;
+  const int64_t ncell_alloc = S.cblk ? (h->n_cells + S.cblk - 1) / S.cblk * S.cblk : h->n_cells;
+  h->cell_bytes = (int64_t)ncell_arrays * ncell_alloc * k3 * sizeof(T);
   st = dev_alloc(h, &h->cell_geo, (size_t)h->cell_bytes);
+  if (st == DG_OK && h->cell_bytes > 0 && ncell_alloc != h->n_cells) {
+    cudaError_t e = cudaMemsetAsync(h->cell_geo, 0, (size_t)h->cell_bytes, h->stream);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "cell geometry padding");
+  }
   if (st == DG_OK) {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((ncq + threads - 1) / threads, 152 * 64);
@@ -887,7 +937,7 @@ dg_status setup_geometry(dg_handle* h) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     const int64_t nf = (int64_t)S.P[d] * h->mesh.n[t1] * h->mesh.n[t2];
     const int64_t nfq = nf * k2;
-    const int nfa = h->op == DG_OP_SIPG ? 7 : 1;
+    const int nfa = h->op == DG_OP_SIPG ? (S.face_minor && !S.face_pair ? 4 : 7) : 1;
     double* daw = nullptr;
     if ((st = dev_alloc(h, &h->face_geo[d], sizeof(T) * nfa * nfq)) != DG_OK) break;
     if (h->op == DG_OP_SIPG && (st = dev_alloc(h, &h->face_tau[d], sizeof(T) * nf)) != DG_OK) break;
@@ -1164,7 +1214,7 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   h->op = opts->op;
   h->n_cells = nc;
   h->n_dofs = nc * k * k * k;
-  h->cpb = dg::cells_per_block(k);
+  h->cpb = h->prec == DG_FP32 ? dg::f32_tile_default(k) : dg::cells_per_block(k);
   h->stream = static_cast<cudaStream_t>(stream);
   build_tables(k, h->t64);
   h->tabd = cast_tables<double>(k, h->t64);
@@ -1208,8 +1258,11 @@ dg_status dg_info(const dg_handle* h, dg_info_t* info) {
   info->face_geometry_bytes = h->face_bytes;
   info->cells_per_block = h->cpb;
   info->threads_per_block = h->cpb * h->k * h->k;
-  info->shared_bytes_per_block = dg::smem_bytes_per_block(h->k, h->op, h->prec == DG_FP32 ? 4 : 8, h->cpb);
+  info->shared_bytes_per_block = h->prec == DG_FP32 ? dg::f32_smem_bytes(h->k, h->op, h->cpb)
+                                                    : dg::smem_bytes_per_block(h->k, h->op, 8, h->cpb);
   info->blocks = apply_blocks(h);
+  const std::vector<int> tc = tile_choices(h);
+  for (int i = 0; i < 24; ++i) info->tile_choices[i] = i < (int)tc.size() ? tc[i] : 0;
   return DG_OK;
 }
 
@@ -1393,6 +1446,15 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
 
 dg_status dg_set_cells_per_block(dg_handle* h, int cpb) {
   if (!h) return DG_ERR_ARG;
+  if (h->prec == DG_FP32) {
+    // the binary32 kernel is compiled for two tile shapes
+    if (cpb == 0) cpb = dg::f32_tile_default(h->k);
+    if (cpb != dg::f32_tile_small(h->k) && cpb != dg::f32_geometry_block(h->k))
+      return fail(h, DG_ERR_ARG, "binary32 cells per block must be " + std::to_string(dg::f32_tile_small(h->k)) +
+                                     " or " + std::to_string(dg::f32_geometry_block(h->k)));
+    h->cpb = cpb;
+    return DG_OK;
+  }
   if (cpb == 0) cpb = dg::cells_per_block(h->k);
   if (cpb < 1 || cpb > dg::cells_per_block(h->k))
     return fail(h, DG_ERR_ARG, "cells per block must be in 1.." + std::to_string(dg::cells_per_block(h->k)));
@@ -1410,13 +1472,11 @@ dg_status dg_autotune(dg_handle* h, int* best_cpb, double* best_ms) {
   cudaEvent_t e0, e1;
   DG_CUDA(h, cudaEventCreate(&e0));
   DG_CUDA(h, cudaEventCreate(&e1));
-  const int cands[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64};
   const int saved = h->cpb;
   int best = saved;
   float best_t = 1e30f;
   st = DG_OK;
-  for (int c : cands) {
-    if (c > dg::cells_per_block(h->k)) break;
+  for (int c : tile_choices(h)) {
     h->cpb = c;
     for (int w = 0; w < 2 && st == DG_OK; ++w) st = launch_apply(h, h->stage_src, h->stage_dst, nullptr);
     if (st != DG_OK) break;

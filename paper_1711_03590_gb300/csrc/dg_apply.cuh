@@ -927,10 +927,16 @@ cudaError_t launch_prec(const ApplyLaunch& L, int64_t n_cells) {
   return launch_one<K, T, GEO_MERGED, OP_ADV>(L, n_cells);
 }
 
+}  // namespace dg
+
+#include "dg_apply_f32.cuh"
+
+namespace dg {
+
 template <int K>
 cudaError_t launch_apply(const ApplyLaunch& L, int64_t n_cells) {
   if (L.prec == 0) return launch_prec<K, double>(L, n_cells);
-  if (L.prec == 1) return launch_prec<K, float>(L, n_cells);
+  if (L.prec == 1) return launch_apply_f32<K>(L, n_cells);
   return launch_prec<K, df64>(L, n_cells);
 }
 

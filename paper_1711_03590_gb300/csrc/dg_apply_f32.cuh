@@ -1,0 +1,751 @@
+// Binary32 DG apply kernel, laid out for shared-memory and instruction
+// economy (one launch per operator evaluation).
+//
+// Same method and face treatment as the FP64 kernel (element-centric: every
+// interior face is evaluated from both sides, each cell's result is set
+// exactly once, no atomics), reorganized because in binary32 the arithmetic
+// is cheap and the kernel is limited by shared-memory traffic, integer work
+// and latency:
+//
+//  * C cells per block (a compile-time tile shape), k^2 threads per cell;
+//    thread (a, b) of a cell owns the x-line (y=a, z=b), the y-line (x=a,
+//    z=b) and the z-line (x=a, y=b) in the phases that sweep in x, y and z,
+//    and face point (a, b) of the faces of every direction.
+//  * Shared memory is cell-minor: the value at point p of cell c sits at
+//    p C + c and thread t works on cell t mod C, so the 32 lanes of a warp
+//    address 32/C consecutive line positions of C cells; rows are padded to
+//    an odd length so that no line direction has bank conflicts.
+//  * The 1D sweeps keep their line in registers (k loads, k^2 FMAs, k
+//    stores); the z-line owner computes the z-derivative from registers.
+//  * The in-face sum factorization of the neighbours' traces (Eq.
+//    face_integral: S (x) S and the tangential derivatives of the face-normal
+//    data S_f u, D_f u) runs as line tasks spread over all threads of the
+//    block; the results land at the face point of the thread that forms the
+//    flux.
+//  * Face test functions are injected by the line owners in the phase where
+//    they integrate (apply D^T along their direction), so the only shared
+//    traffic for faces is the tangential gradient-test components pulled
+//    across directions.
+//  * Cell geometry is stored in a cell-blocked layout [block][array][point]
+//    [cell in block] so that its loads are whole 128-byte lines; boundary
+//    and tail handling are selects on clamped indices (no divergent
+//    branches).
+//
+// Phases (barrier-separated): gather + S_z, neighbour face data | S_y, first
+// in-face sweep | S_x, D_x, second in-face sweep with the neighbour's normal
+// flux | D_y, D_z | own face traces (extrapolation of the Gauss-point fields,
+// E_s) and numerical fluxes (Eq. poisson_sip / advection) | z: q-point
+// operation (Sec. 5 geometry variants), z-face injection, D_z^T | y: D_y^T |
+// x: D_x^T, S_x^T | y: S_y^T | z: S_z^T and the store (set) of dst.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "dg_internal.cuh"
+
+namespace dg {
+
+template <int K, int C>
+struct F32Shape {
+  static constexpr int K2 = K * K, K3 = K2 * K;
+  static constexpr int XS = (K % 2 == 0) ? K + 1 : K;  // odd row pitch
+  static constexpr int YS = XS * K;
+  static constexpr int NP = YS * K;  // padded points per cell
+  static constexpr int NT = C * K2;  // threads per block
+};
+
+// Resident blocks per SM the register allocation is sized for: about 900
+// threads per SM up to k = 6 (72-80 registers), fewer for the longer lines
+// of k >= 7 so that they do not spill; the shared memory of that many blocks
+// fits as well.
+__host__ __device__ constexpr int f32_min_blocks(int k, int C) {
+  return (k <= 6 ? 900 : 700) / (C * k * k) > 0 ? (k <= 6 ? 900 : 700) / (C * k * k) : 1;
+}
+
+template <int K, int C, int GEO, int OP>
+__global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
+    apply_f32_kernel(const __grid_constant__ ApplyParams<float> P) {
+  using Sh = F32Shape<K, C>;
+  constexpr int K2 = Sh::K2, K3 = Sh::K3, XS = Sh::XS, YS = Sh::YS, NP = Sh::NP, NT = Sh::NT;
+  constexpr int CBL = f32_geometry_block(K);
+  constexpr bool SIPG = OP == OP_SIPG;
+  constexpr bool CART = GEO == GEO_CART;
+  constexpr bool TANG = SIPG && !CART;        // tangential gradients on faces
+  constexpr int NBF = SIPG ? 2 : 1;           // neighbour face fields (value, normal derivative)
+  constexpr int NBB = SIPG ? (CART ? 2 : 3) : 1;  // after the first in-face sweep
+  constexpr int NA = GEO == GEO_FULL ? 10 : (SIPG ? 6 : 3);
+  static_assert(C == 4 || C == 8 || C == 16 || C == 32 || C == 64, "cells per block");
+  static_assert(CBL % C == 0, "geometry block width");
+
+  extern __shared__ __align__(16) float sm[];
+  float* U = sm;             // [NP][C]: u -> u at Gauss points -> integrated field
+  float* G0 = U + NP * C;    // gradients, then test fields
+  float* G1 = G0 + NP * C;
+  float* G2 = G1 + NP * C;
+  float* FA = G2 + NP * C;   // [6 faces][NBF][K2][C]: neighbour data at GL face points,
+                             // then (u+, w+) at the face Gauss points; last: dot reduction
+  float* FB = FA + 6 * NBF * K2 * C;  // [6][NBB][K2][C]: after the first in-face sweep;
+                                      // then the pulled face test components [2][2][2][K2][C]
+  int* NBC = reinterpret_cast<int*>(FB + 6 * NBB * K2 * C);  // [6][C] neighbour cell or -1
+  int* FID = NBC + 6 * C;                                    // [6][C] face id
+  constexpr int RS = K3;  // cell stride of the staged source
+  static_assert((C + 2) * RS <= 2 * NP * C, "staged source fits in G1/G2");
+
+  const Tables<float>& tb = P.tab;
+  const Geometry<float>& gm = P.geo;
+  const int tid = threadIdx.x;
+  const int lc = tid % C;
+  const int ln = tid / C;
+  const int a = ln % K, b = ln / K;
+  const int ncell = (int)gm.n_cells;
+  const int cell_raw = (int)blockIdx.x * C + lc;
+  const bool valid = cell_raw < ncell;
+  const int cell = valid ? cell_raw : ncell - 1;
+  int i0, i1, i2;
+  {
+    const unsigned q = (unsigned)cell / (unsigned)gm.n[0];
+    i0 = cell - (int)(q * (unsigned)gm.n[0]);
+    i1 = (int)(q % (unsigned)gm.n[1]);
+    i2 = (int)(q / (unsigned)gm.n[1]);
+  }
+
+  // the source of the block's cells and their two x-neighbours
+  // (cells cell0 - 1 .. cell0 + C, contiguous in memory) staged in shared
+  // memory with coalesced loads (cell-major, stride k^3); it occupies the
+  // G1/G2 region until phase 4
+  float* R = G1;
+  const int cfirst = (int)blockIdx.x * C - 1;
+  {
+    const int64_t base = (int64_t)cfirst * K3;
+    constexpr int NR = (C + 2) * K3;
+    const unsigned lo = cfirst < 0 ? K3 : 0u;  // cell -1 does not exist
+    const int rem = ncell - cfirst;            // cells from cfirst to the end of the mesh
+    const unsigned hi = (unsigned)(rem < C + 2 ? rem : C + 2) * K3;
+#pragma unroll
+    for (int r = 0; r < (NR + NT - 1) / NT; ++r) {
+      const unsigned e = tid + r * NT;
+      if (e >= lo && e < hi) R[e] = P.src[base + e];
+    }
+  }
+  // neighbour cells and face ids of the six faces (d, s), one thread each;
+  // faces are numbered like cells with the face position along d
+  for (int t = ln; t < 6; t += K2) {
+    const int d = t >> 1, s = t & 1;
+    const int id = d == 0 ? i0 : d == 1 ? i1 : i2;
+    const int nd = gm.n[d];
+    int jd = id + (s ? 1 : -1);
+    bool inside = jd >= 0 && jd < nd;
+    if (!inside && gm.periodic) {
+      jd = jd < 0 ? nd - 1 : 0;
+      inside = true;
+    }
+    int pos = id + s;
+    if (gm.periodic && pos == nd) pos = 0;
+    const int j0 = d == 0 ? jd : i0, j1 = d == 1 ? jd : i1, j2 = d == 2 ? jd : i2;
+    NBC[t * C + lc] = inside ? j0 + gm.n[0] * (j1 + gm.n[1] * j2) : -1;
+    const int f0 = d == 0 ? pos : i0, f1 = d == 1 ? pos : i1, f2 = d == 2 ? pos : i2;
+    const int e0 = d == 0 ? gm.P[0] : gm.n[0], e1 = d == 1 ? gm.P[1] : gm.n[1];
+    FID[t * C + lc] = f0 + e0 * (f1 + e1 * f2);
+  }
+  __syncthreads();
+
+  // 1. neighbours' face data at GL face point (a, b): the layer on the shared
+  // face and (SIPG) the normal derivative D_f of the line through it; x
+  // neighbours from the staged source where they are staged
+  float v[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) v[j] = R[(lc + 1) * RS + a + K * b + K2 * j];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const int d = t >> 1, s = t & 1;
+    const int nb = NBC[t * C + lc];
+    const int off = d == 0 ? K * (a + K * b) : d == 1 ? a + K2 * b : a + K * b;
+    const int str = d == 0 ? 1 : d == 1 ? K : K2;
+    float w[K];
+    if (d == 0) {
+      const int r = (nb >= 0 ? nb : cell) - cfirst;
+      if (r >= 0 && r < C + 2) {
+#pragma unroll
+        for (int l = 0; l < K; ++l) w[l] = R[r * RS + off + l];
+      } else {
+        const float* p = P.src + (size_t)nb * K3 + off;
+#pragma unroll
+        for (int l = 0; l < K; ++l) w[l] = p[l];
+      }
+    } else {
+      const float* p = P.src + (size_t)(nb >= 0 ? nb : cell) * K3 + off;
+#pragma unroll
+      for (int l = 0; l < K; ++l) w[l] = p[l * str];
+    }
+    FA[((t * NBF) * K2 + ln) * C + lc] = s ? w[0] : w[K - 1];
+    if (SIPG) {
+      float dn = 0.f;
+#pragma unroll
+      for (int l = 0; l < K; ++l) dn = fmaf(tb.DF[1 - s][l], w[l], dn);
+      FA[((t * NBF + 1) * K2 + ln) * C + lc] = dn;
+    }
+    // long lines: keep at most two of them in flight (register budget)
+    if (K >= 7 && s == 1) __syncwarp();
+  }
+  // S along z
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc = fmaf(tb.S[q * K + j], v[j], acc);
+    U[(a + XS * b + YS * q) * C + lc] = acc;
+  }
+  __syncthreads();
+
+  // 2. S along y; first in-face sweep (along t1) of the neighbour data
+  {
+    float w[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = U[(a + XS * j + YS * b) * C + lc];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[q * K + j], w[j], acc);
+      U[(a + XS * q + YS * b) * C + lc] = acc;
+    }
+  }
+  {
+    constexpr int NTASK = 6 * K * C, ROUNDS = (NTASK + NT - 1) / NT;
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+      const int task = tid + r * NT;
+      if (NTASK % NT == 0 || task < NTASK) {
+        const int tc = task % C, rest = task / C;
+        const int bb = rest % K, t = rest / K;
+        const float* in = FA + ((t * NBF) * K2 + K * bb) * C + tc;  // row (i, bb)
+        float* out = FB + ((t * NBB) * K2 + K * bb) * C + tc;
+        float xv[K], xn[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          xv[i] = in[i * C];
+          if (SIPG) xn[i] = in[(K2 + i) * C];
+        }
+#pragma unroll
+        for (int qa = 0; qa < K; ++qa) {
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+          for (int i = 0; i < K; ++i) {
+            s0 = fmaf(tb.S[qa * K + i], xv[i], s0);
+            if (TANG) s1 = fmaf(tb.DS[qa * K + i], xv[i], s1);
+            if (SIPG) s2 = fmaf(tb.S[qa * K + i], xn[i], s2);
+          }
+          out[qa * C] = s0;
+          if (TANG) out[(K2 + qa) * C] = s1;
+          if (SIPG) out[((NBB - 1) * K2 + qa) * C] = s2;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // 3. S along x -> u at the Gauss points; D along x; second in-face sweep
+  // (along t2) giving the neighbour's value u+ and normal flux w+ = (its
+  // derivative along this cell's outward normal) at face Gauss point (qa, qb)
+  {
+    float ux[K];
+    float w[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = U[(j + XS * a + YS * b) * C + lc];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[q * K + j], w[j], acc);
+      ux[q] = acc;
+      U[(q + XS * a + YS * b) * C + lc] = acc;
+    }
+    if (SIPG) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc = fmaf(tb.D[q * K + j], ux[j], acc);
+        G0[(q + XS * a + YS * b) * C + lc] = acc;
+      }
+    }
+  }
+  {
+    constexpr int NTASK = 6 * K * C, ROUNDS = (NTASK + NT - 1) / NT;
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+      const int task = tid + r * NT;
+      if (NTASK % NT == 0 || task < NTASK) {
+        const int tc = task % C, rest = task / C;
+        const int qa = rest % K, t = rest / K;
+        const int d = t >> 1, s = t & 1;
+        const float* in = FB + ((t * NBB) * K2 + qa) * C + tc;  // row (qa, j): stride K C
+        float* out = FA + ((t * NBF) * K2 + qa) * C + tc;
+        float sv[K], dsv[K], sn[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          sv[j] = in[j * K * C];
+          if (TANG) dsv[j] = in[(K2 + j * K) * C];
+          if (SIPG) sn[j] = in[((NBB - 1) * K2 + j * K) * C];
+        }
+        const float* fg = nullptr;
+        int64_t nfq = 0, nfc = 0;
+        if (TANG) {
+          nfq = gm.nfq[d];
+          nfc = gm.nfc[d];
+          fg = gm.face[d] + qa * nfc + FID[t * C + tc];
+        }
+        const float cj = CART && SIPG ? (s ? 1.f : -1.f) * gm.cart_jinv[d] : 0.f;
+#pragma unroll
+        for (int qb = 0; qb < K; ++qb) {
+          float u = 0.f, dt2 = 0.f, dt1 = 0.f, dn = 0.f;
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            u = fmaf(tb.S[qb * K + j], sv[j], u);
+            if (TANG) {
+              dt2 = fmaf(tb.DS[qb * K + j], sv[j], dt2);
+              dt1 = fmaf(tb.S[qb * K + j], dsv[j], dt1);
+            }
+            if (SIPG) dn = fmaf(tb.S[qb * K + j], sn[j], dn);
+          }
+          out[qb * K * C] = u;
+          if (SIPG) {
+            float wn;
+            if (CART) {
+              wn = cj * dn;
+            } else {
+              // reference-axis components: d carries the normal derivative,
+              // t1 < t2 the tangential ones; the neighbour is slot s
+              const float gx = d == 0 ? dn : dt1;
+              const float gy = d == 1 ? dn : (d == 0 ? dt1 : dt2);
+              const float gz = d == 2 ? dn : dt2;
+              // face vector j_f = J^{-T} e_d; the neighbour (slot s) has
+              // (s ? -j_f : j_f) (face_pair: both stored), and its
+              // derivative along this cell's outward normal is minus that
+              const float* f = fg + qb * (K * nfc) + (gm.face_pair ? s * 3 * nfq : 0);
+              const float jd = f[0] * gx + f[nfq] * gy + f[2 * nfq] * gz;
+              wn = (s && !gm.face_pair) ? jd : -jd;
+            }
+            out[(K2 + qb * K) * C] = wn;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // 4. D along y and z
+  if (SIPG) {
+    float uy[K], uz[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      uy[j] = U[(a + XS * j + YS * b) * C + lc];
+      uz[j] = U[(a + XS * b + YS * j) * C + lc];
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        s1 = fmaf(tb.D[q * K + j], uy[j], s1);
+        s2 = fmaf(tb.D[q * K + j], uz[j], s2);
+      }
+      G1[(a + XS * q + YS * b) * C + lc] = s1;
+      G2[(a + XS * b + YS * q) * C + lc] = s2;
+    }
+    __syncthreads();
+  }
+
+  // 5. own traces at face point (a, b) of the x and y faces (extrapolation
+  // E_s of the Gauss-point fields along the owned line) and the numerical
+  // flux; test coefficients: value tv, gradient tg * j_o.  The own-direction
+  // coefficients replace (u+, w+) in this thread's own slots of FA; the
+  // tangential ones consumed by other line owners go to FT.  (The z faces
+  // follow in phase 6, where the z-line owner holds the fields anyway.)
+  const float ea0 = tb.E[0][a], ea1 = tb.E[1][a], eb0 = tb.E[0][b], eb1 = tb.E[1][b];
+  const float wa = tb.W[a], wb = tb.W[b];
+  float* FT = FB;  // [face direction x, y][side][component slot][K2][C]
+  // trace and flux of face (d, s) at this thread's face point
+  auto own_flux = [&](auto dc, int s, const float(&lu)[K], const float(&lg)[3][K], float& tvv, float(&tgo)[3]) {
+    constexpr int d = decltype(dc)::value;
+    const int t = 2 * d + s;
+    const bool interior = NBC[t * C + lc] >= 0;
+    const int fid = FID[t * C + lc];
+    float uf = 0.f, gf[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float e = tb.E[s][j];
+      uf = fmaf(e, lu[j], uf);
+      if (SIPG) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c == d || TANG) gf[c] = fmaf(e, lg[c][j], gf[c]);
+      }
+    }
+    const float* slot = FA + ((t * NBF) * K2 + ln) * C + lc;  // this thread's (u+, w+) of face t
+    const float un = slot[0];
+    tgo[0] = tgo[1] = tgo[2] = 0.f;
+    if (SIPG) {
+      const float wn = slot[K2 * C];
+      float jo[3], fjxw, tau;
+      if (CART) {
+        const float jn = (s ? 1.f : -1.f) * gm.cart_jinv[d];
+        jo[0] = d == 0 ? jn : 0.f;
+        jo[1] = d == 1 ? jn : 0.f;
+        jo[2] = d == 2 ? jn : 0.f;
+        float kap = 1.f;
+        if (gm.kq) kap = d == 0 ? gm.kf[i0 + s] : gm.kq[i0 * K + a];
+        fjxw = kap * wa * wb * gm.cart_detj * gm.cart_jinv[d];
+        tau = gm.cart_tau[d];
+      } else {
+        const int64_t nfq = gm.nfq[d];
+        const float* fp = gm.face[d] + ln * (int64_t)gm.nfc[d] + fid;
+        // own slot 1 - s: the lower side (slot 0) has j_f, the upper -j_f
+        // (or both stored: face_pair)
+        const float* jp = fp + (gm.face_pair ? (1 - s) * 3 * nfq : 0);
+        const float sg = (s || gm.face_pair) ? 1.f : -1.f;
+        jo[0] = sg * jp[0];
+        jo[1] = sg * jp[nfq];
+        jo[2] = sg * jp[2 * nfq];
+        fjxw = fp[(gm.face_pair ? 6 : 3) * nfq];
+        tau = gm.tau[d][fid];
+      }
+      const float dno = CART ? jo[d] * gf[d] : jo[0] * gf[0] + jo[1] * gf[1] + jo[2] * gf[2];
+      const float jump = interior ? uf - un : 2.f * uf;
+      tvv = interior ? fjxw * (tau * jump - 0.5f * (dno + wn)) : fjxw * (tau * jump - dno);
+      const float tg = -0.5f * fjxw * jump;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tgo[c] = tg * jo[c];
+    } else {
+      float cn;
+      if (CART) {
+        cn = gm.vel[d] * wa * wb * gm.cart_detj * gm.cart_jinv[d];
+      } else {
+        cn = gm.face[d][(size_t)ln * gm.nfc[d] + fid];
+      }
+      const float cno = s ? cn : -cn;  // c.n da w with n the own outward normal
+      tvv = interior ? 0.5f * cno * (uf + un) + 0.5f * fabsf(cno) * (uf - un) : fabsf(cno) * uf;
+    }
+  };
+  auto xy_faces = [&](auto dc) {
+    constexpr int d = decltype(dc)::value;
+    float lu[K], lg[3][K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int pidx = (d == 0 ? (j + XS * a + YS * b) : (a + XS * j + YS * b)) * C + lc;
+      lu[j] = U[pidx];
+      if (SIPG) {
+        lg[0][j] = (d == 0 || TANG) ? G0[pidx] : 0.f;
+        lg[1][j] = (d == 1 || TANG) ? G1[pidx] : 0.f;
+        lg[2][j] = TANG ? G2[pidx] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      float tvv, tgo[3];
+      own_flux(dc, s, lu, lg, tvv, tgo);
+      float* slot = FA + (((2 * d + s) * NBF) * K2 + ln) * C + lc;
+      slot[0] = tvv;
+      if (SIPG) slot[K2 * C] = tgo[d];
+      if (TANG) {
+        // x faces give components 1 and 2, y faces 0 and 2
+        FT[(((d * 2 + s) * 2 + 0) * K2 + ln) * C + lc] = tgo[d == 0 ? 1 : 0];
+        FT[(((d * 2 + s) * 2 + 1) * K2 + ln) * C + lc] = tgo[2];
+      }
+    }
+  };
+  xy_faces(std::integral_constant<int, 0>{});
+  xy_faces(std::integral_constant<int, 1>{});
+  __syncthreads();
+
+  // 6. z-line owner: z-face traces and fluxes, q-point operation at
+  // (a, b, j), z-face injection, the z components of the x- and y-face
+  // gradient tests, then D_z^T
+  {
+    float lu[K], lg[3][K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int pidx = (a + XS * b + YS * j) * C + lc;
+      lu[j] = U[pidx];
+      if (SIPG) {
+        lg[0][j] = G0[pidx];
+        lg[1][j] = G1[pidx];
+        lg[2][j] = G2[pidx];
+      }
+    }
+    float tvz[2], tgz[3][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      float tvv, tgo[3];
+      own_flux(std::integral_constant<int, 2>{}, s, lu, lg, tvv, tgo);
+      tvz[s] = tvv;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tgz[c][s] = tgo[c];
+    }
+    float t2[K];
+    // cell-blocked geometry: array m, point q of cell c at
+    // ((c / CBL) NA + m) K3 + q) CBL + c mod CBL (padded to whole blocks,
+    // so the unclamped index of tail threads stays inside the allocation)
+    size_t gofs = 0;
+    if constexpr (!CART) gofs = ((size_t)(cell_raw / CBL) * NA * K3) * CBL + (cell_raw % CBL);
+    constexpr int MS = K3 * CBL;  // array stride
+    float kx = 1.f;
+    if (CART && SIPG && gm.kq) kx = gm.kq[i0 * K + a];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int q = a + K * b + K2 * j;
+      const int pidx = (a + XS * b + YS * j) * C + lc;
+      const float* cp = CART ? gm.cell : gm.cell + gofs + (size_t)q * CBL;
+      float t0, t1;
+      if (SIPG) {
+        const float g0 = lg[0][j], g1 = lg[1][j], g2 = lg[2][j];
+        if (CART) {
+          const float w = wa * wb * tb.W[j] * gm.cart_detj * kx;
+          t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+          t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+          t2[j] = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+        } else if (GEO == GEO_FULL) {
+          float J[9];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) J[m] = cp[m * MS];
+          const float jw = cp[9 * MS];
+          // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
+          const float x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
+          const float x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
+          const float x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+          t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
+          t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
+          t2[j] = J[6] * x0 + J[7] * x1 + J[8] * x2;
+        } else {
+          const float a00 = cp[0], a01 = cp[MS], a02 = cp[2 * MS], a11 = cp[3 * MS], a12 = cp[4 * MS],
+                      a22 = cp[5 * MS];
+          t0 = a00 * g0 + a01 * g1 + a02 * g2;
+          t1 = a01 * g0 + a11 * g1 + a12 * g2;
+          t2[j] = a02 * g0 + a12 * g1 + a22 * g2;
+        }
+        // z faces: gradient test along the line
+        const float e0 = tb.E[0][j], e1 = tb.E[1][j];
+        if (TANG) {
+          t0 += e0 * tgz[0][0] + e1 * tgz[0][1];
+          t1 += e0 * tgz[1][0] + e1 * tgz[1][1];
+        }
+        t2[j] += e0 * tgz[2][0] + e1 * tgz[2][1];
+        if (TANG) {
+          // x faces at (y=b, z=j), y faces at (x=a, z=j): their z components
+          t2[j] += ea0 * FT[(((0 * 2 + 0) * 2 + 1) * K2 + b + K * j) * C + lc] +
+                   ea1 * FT[(((0 * 2 + 1) * 2 + 1) * K2 + b + K * j) * C + lc] +
+                   eb0 * FT[(((1 * 2 + 0) * 2 + 1) * K2 + a + K * j) * C + lc] +
+                   eb1 * FT[(((1 * 2 + 1) * 2 + 1) * K2 + a + K * j) * C + lc];
+        }
+      } else {
+        const float uq = lu[j];
+        float b0, b1, b2;
+        if (CART) {
+          const float w = -wa * wb * tb.W[j] * gm.cart_detj;
+          b0 = w * gm.cart_jinv[0] * gm.vel[0];
+          b1 = w * gm.cart_jinv[1] * gm.vel[1];
+          b2 = w * gm.cart_jinv[2] * gm.vel[2];
+        } else if (GEO == GEO_FULL) {
+          float J[9];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) J[m] = cp[m * MS];
+          const float jw = -cp[9 * MS];
+          b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
+          b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
+          b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+        } else {
+          b0 = cp[0];
+          b1 = cp[MS];
+          b2 = cp[2 * MS];
+        }
+        t0 = b0 * uq;
+        t1 = b1 * uq;
+        t2[j] = b2 * uq;
+      }
+      G0[pidx] = t0;
+      G1[pidx] = t1;
+      // long lines: bound the geometry loads in flight (register budget)
+      if (K >= 7 && !CART && j % 2 == 1) __syncwarp();
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float acc = tb.E[0][i] * tvz[0] + tb.E[1][i] * tvz[1];
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t2[j], acc);
+      U[(a + XS * b + YS * i) * C + lc] = acc;
+    }
+  }
+  __syncthreads();
+
+  // 7. y-line owner (x=a, z=b): x-face and own y-face y components, D_y^T
+  {
+    const float* own = FA + ((2 * NBF) * K2 + ln) * C + lc;  // faces (1, s): tv, t_y part
+    const float tv0 = own[0], tv1 = own[NBF * K2 * C];
+    float tg0 = 0.f, tg1 = 0.f;
+    if (SIPG) {
+      tg0 = own[K2 * C];
+      tg1 = own[(NBF + 1) * K2 * C];
+    }
+    float t1[K], w[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int pidx = (a + XS * j + YS * b) * C + lc;
+      t1[j] = G1[pidx];
+      w[j] = U[pidx];
+      if (SIPG) t1[j] += tb.E[0][j] * tg0 + tb.E[1][j] * tg1;
+      if (TANG)
+        t1[j] += ea0 * FT[(((0 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc] +
+                 ea1 * FT[(((0 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc];
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float acc = w[i] + tb.E[0][i] * tv0 + tb.E[1][i] * tv1;
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t1[j], acc);
+      U[(a + XS * i + YS * b) * C + lc] = acc;
+    }
+  }
+  __syncthreads();
+
+  // 8. x-line owner (y=a, z=b): y-face and own x-face x components, D_x^T,
+  // then S_x^T (the integrated field is complete along x here)
+  {
+    const float* own = FA + ln * C + lc;  // faces (0, s): tv, t_x part
+    const float tv0 = own[0], tv1 = own[NBF * K2 * C];
+    float tg0 = 0.f, tg1 = 0.f;
+    if (SIPG) {
+      tg0 = own[K2 * C];
+      tg1 = own[(NBF + 1) * K2 * C];
+    }
+    float t0[K], w[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int pidx = (j + XS * a + YS * b) * C + lc;
+      t0[j] = G0[pidx];
+      w[j] = U[pidx];
+      if (SIPG) t0[j] += tb.E[0][j] * tg0 + tb.E[1][j] * tg1;
+      if (TANG)
+        t0[j] += ea0 * FT[(((1 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc] +
+                 ea1 * FT[(((1 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc];
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float acc = w[i] + tb.E[0][i] * tv0 + tb.E[1][i] * tv1;
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t0[j], acc);
+      w[i] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[j * K + i], w[j], acc);
+      U[(i + XS * a + YS * b) * C + lc] = acc;
+    }
+  }
+  __syncthreads();
+
+  // 9. S_y^T
+  {
+    float w[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = U[(a + XS * j + YS * b) * C + lc];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[j * K + i], w[j], acc);
+      U[(a + XS * i + YS * b) * C + lc] = acc;
+    }
+  }
+  __syncthreads();
+
+  // 10. S_z^T and the store (set) of the cell's dst z-line; optional src.dst
+  {
+    float w[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = U[(a + XS * b + YS * j) * C + lc];
+    float* o = P.dst + (size_t)cell * K3 + a + K * b;
+    const float* s = P.src + (size_t)cell * K3 + a + K * b;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float r = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) r = fmaf(tb.S[j * K + i], w[j], r);
+      if (valid) o[K2 * i] = r;
+      if (P.dot_partial) acc += (double)r * (double)s[K2 * i];
+    }
+    if (P.dot_partial) {
+      // fixed-order block reduction (FA is free since phase 5)
+      double* red = reinterpret_cast<double*>(FA);
+      red[tid] = valid ? acc : 0.0;
+      __syncthreads();
+      if (tid < 32) {
+        double t = 0.0;
+        for (int i = tid; i < NT; i += 32) t += red[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (tid == 0) P.dot_partial[blockIdx.x] = t;
+      }
+    }
+  }
+}
+
+// Compiled tile shapes (cells per block) of the binary32 kernel.
+template <int K>
+struct F32Tiles {
+  static constexpr int small = f32_tile_small(K);
+  static constexpr int large = f32_geometry_block(K);
+};
+
+template <int K, int C, int GEO, int OP>
+cudaError_t launch_f32_one(const ApplyLaunch& L, int64_t n_cells) {
+  ApplyParams<float> P;
+  P.tab = *static_cast<const Tables<float>*>(L.tables);
+  P.geo = *static_cast<const Geometry<float>*>(L.geometry);
+  P.src = static_cast<const float*>(L.src);
+  P.dst = static_cast<float*>(L.dst);
+  P.dot_partial = L.dot_partial;
+  P.C = C;
+  const int smem = f32_smem_bytes(K, OP, C);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(apply_f32_kernel<K, C, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    // shared-memory carveout for the intended resident blocks (percent of
+    // the 228 KB maximum); the rest of the unified cache stays L1
+    const int want = f32_min_blocks(K, C) * (smem + 1024);
+    const int pct = want >= 228 * 1024 ? 100 : (want * 100 + 228 * 1024 - 1) / (228 * 1024);
+    e = cudaFuncSetAttribute(apply_f32_kernel<K, C, GEO, OP>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int64_t grid = (n_cells + C - 1) / C;
+  if (grid <= 0) return cudaSuccess;
+  apply_f32_kernel<K, C, GEO, OP><<<(unsigned)grid, C * K * K, smem, L.stream>>>(P);
+  return cudaGetLastError();
+}
+
+template <int K, int C>
+cudaError_t launch_f32_tile(const ApplyLaunch& L, int64_t n_cells) {
+  if (L.op == OP_SIPG) {
+    if (L.geo == GEO_CART) return launch_f32_one<K, C, GEO_CART, OP_SIPG>(L, n_cells);
+    if (L.geo == GEO_FULL) return launch_f32_one<K, C, GEO_FULL, OP_SIPG>(L, n_cells);
+    return launch_f32_one<K, C, GEO_MERGED, OP_SIPG>(L, n_cells);
+  }
+  if (L.geo == GEO_CART) return launch_f32_one<K, C, GEO_CART, OP_ADV>(L, n_cells);
+  if (L.geo == GEO_FULL) return launch_f32_one<K, C, GEO_FULL, OP_ADV>(L, n_cells);
+  return launch_f32_one<K, C, GEO_MERGED, OP_ADV>(L, n_cells);
+}
+
+template <int K>
+cudaError_t launch_apply_f32(const ApplyLaunch& L, int64_t n_cells) {
+  if (L.cpb == F32Tiles<K>::large) return launch_f32_tile<K, F32Tiles<K>::large>(L, n_cells);
+  if (L.cpb == F32Tiles<K>::small) return launch_f32_tile<K, F32Tiles<K>::small>(L, n_cells);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dg

@@ -38,14 +38,18 @@ struct Geometry {
   // faces of direction d: positions P_d = periodic ? n_d : n_d + 1,
   // face id = pos + P_d (i_t1 + n_t1 i_t2), t1 < t2 the other directions
   int P[3];
-  // FULL / MERGED cell arrays (structure of arrays, stride ncq = n_cells k^3)
+  // FULL / MERGED cell arrays: structure of arrays, stride ncq = n_cells k^3
+  // (binary64 and double-float); binary32: cell-blocked, see f32_geometry_block
   const T* __restrict__ cell;  // FULL SIPG: 9 J^{-1} + 1 kappa JxW; FULL ADV: 9 + 1 JxW;
                                // MERGED SIPG: 6; MERGED ADV: 3
   int64_t ncq;
   // face arrays per direction (stride nfq[d] = nfaces_d k^2)
   const T* __restrict__ face[3];  // SIPG: 6 j_n (slot0 xyz, slot1 xyz) + 1 kappa da w; ADV: 1 c.n da w
+                                  // (binary32 SIPG unless face_pair: 3 j_n of slot 0 + 1 kappa da w)
   const T* __restrict__ tau[3];   // SIPG: penalty per face
   int64_t nfq[3];
+  int nfc[3];  // faces per direction (binary32 layout: [array][point][face])
+  int face_pair;  // binary32 SIPG face arrays: 1 = both sides' j_n (7 arrays), 0 = one (4)
   // Cartesian compression
   T cart_jinv[3];       // n_d
   T cart_detj;          // 1 / (n0 n1 n2)
@@ -76,6 +80,42 @@ struct ApplyLaunch {
 // the autotuner picks one per operator by timing.
 __host__ __device__ constexpr int cells_per_block(int k) {
   return k == 2 ? 64 : k == 3 ? 28 : k == 4 ? 16 : k == 5 ? 10 : k == 6 ? 7 : k == 7 ? 5 : k == 8 ? 4 : 3;
+}
+
+// Cell-block width of the binary32 kernel's cell geometry layout (the largest
+// of its compiled tile shapes, which all divide it).
+__host__ __device__ constexpr int f32_geometry_block(int k) {
+  return k == 2 ? 64 : k == 3 ? 32 : k <= 5 ? 16 : 8;
+}
+// Compiled tile shapes (cells per block) of the binary32 kernel, and the default.
+__host__ __device__ constexpr int f32_tile_small(int k) { return f32_geometry_block(k) / 2; }
+__host__ __device__ constexpr int f32_tile_default(int k) {
+  return k == 2 ? 64 : k == 3 ? 32 : k == 4 ? 16 : k <= 6 ? 8 : 4;
+}
+
+// Binary32 face numbering: faces of direction d numbered like cells, x
+// fastest, with the face position pos in [0, P_d) in place of the index
+// along d, so that the faces of consecutive cells are consecutive.  f is the
+// face id pos + P_d (i_t1 + n_t1 i_t2).
+__host__ __device__ inline int64_t face_minor_id(const int n[3], const int P[3], int d, int64_t f) {
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  const int pos = (int)(f % P[d]);
+  const int64_t rest = f / P[d];
+  const int it1 = (int)(rest % n[t1]), it2 = (int)(rest / n[t1]);
+  int c[3];
+  c[d] = pos;
+  c[t1] = it1;
+  c[t2] = it2;
+  const int e0 = d == 0 ? P[0] : n[0], e1 = d == 1 ? P[1] : n[1];
+  return c[0] + (int64_t)e0 * (c[1] + (int64_t)e1 * c[2]);
+}
+
+// Shared-memory bytes of the binary32 kernel for k points and C cells: four
+// padded point fields, the neighbour face data (6 faces x 2 fields x k^2),
+// the in-face sweep buffer (6 x 3 x k^2) and two face tables (6 ints each).
+__host__ __device__ constexpr int f32_smem_bytes(int k, int op, int C) {
+  return 4 * (4 * (k * (k % 2 == 0 ? k + 1 : k) * k) * C + 6 * (op == OP_SIPG ? 2 : 1) * k * k * C +
+              6 * (op == OP_SIPG ? 3 : 1) * k * k * C + 12 * C);
 }
 
 // Shared-memory scalars per cell: u, three gradient fields, the two

@@ -208,13 +208,16 @@ def test_tile_shape_does_not_change_results(p):
         op = dgp.Operator((5, 4, 3), p, geom="full", prec=prec, mapping=1, coeff=1)
         u = torch.tensor(dg_inputs.src_vector(op.n_dofs, 5), dtype=op.dtype, device="cuda")
         ref = op.apply(u).clone()
-        cmax = op.info()["cells_per_block"]
-        for c in sorted({1, 2, max(1, cmax // 2), cmax}):
+        choices = op.info()["tile_choices"]
+        assert choices == sorted(choices) and op.info()["cells_per_block"] in choices
+        cmax = choices[-1]
+        for c in sorted({choices[0], choices[min(1, len(choices) - 1)], choices[len(choices) // 2], cmax}):
             op.set_cells_per_block(c)
             assert op.info()["cells_per_block"] == c
+            assert op.info()["threads_per_block"] == c * (p + 1) ** 2
             assert torch.equal(op.apply(u), ref), (prec, c)
         c, ms = op.autotune()
-        assert 1 <= c <= cmax and ms > 0
+        assert c in choices and ms > 0
         assert torch.equal(op.apply(u), ref)
         with pytest.raises(dgp.DGError):
             op.set_cells_per_block(cmax + 1)

@@ -64,17 +64,19 @@ def test_mixed_precision_argument_checks():
     assert st == dgp.DG_ERR_NOT_CONVERGED and outer == 1
 
 
-@pytest.mark.parametrize("p,cpb", [(6, 5), (4, 5), (2, 1)])
-def test_fp32_dot_epilogue_with_odd_block_storage(p, cpb):
-    """The apply's src.dst epilogue reduces in shared memory behind an odd
-    number of binary32 values (C k^3 odd): the reduction buffer must be
-    8-byte aligned.  Checked through the mixed solve on a Cartesian mesh and
-    the allocation-free dot entry point."""
+@pytest.mark.parametrize("p", [1, 2, 4, 6])
+@pytest.mark.parametrize("tile", [0, -1])
+def test_fp32_dot_epilogue_every_tile_shape(p, tile):
+    """The binary32 apply's src.dst epilogue (a block reduction in FP64 in
+    shared memory) for both compiled tile shapes and a cell count that leaves
+    a partial last block.  Checked through the allocation-free dot entry
+    point and the mixed solve on a Cartesian mesh."""
     dgp.build()
-    o32 = dgp.Operator((4, 3, 5), p, geom="cartesian", prec="fp32")
-    o64 = dgp.Operator((4, 3, 5), p, geom="cartesian", prec="fp64")
+    o32 = dgp.Operator((3, 3, 7), p, geom="cartesian", prec="fp32")
+    o64 = dgp.Operator((3, 3, 7), p, geom="cartesian", prec="fp64")
+    cpb = o32.info()["tile_choices"][tile]
     o32.set_cells_per_block(cpb)
-    assert (o32.info()["cells_per_block"] * (p + 1) ** 3) % 2 == 1
+    assert 63 % cpb != 0
     src = torch.tensor(np.random.default_rng(p).uniform(-1, 1, o32.n_dofs), dtype=torch.float32, device="cuda")
     dst = torch.empty_like(src)
     dot = torch.zeros(1, dtype=torch.float64, device="cuda")

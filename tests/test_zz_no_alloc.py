@@ -44,11 +44,12 @@ def test_noalloc_apply_dot_matches_allocating_path(prec, tol):
 
 def test_noalloc_rejects_too_many_blocks():
     dgp.build()
-    # degree 8: 3 cells per block; 3 * 65536 + 3 cells need more than 65536 blocks
-    op = dgp.Operator((65539, 3, 1), 8, geom="cartesian", prec="fp32")
+    # one cell per block: 65537 cells need more than 65536 blocks
+    op = dgp.Operator((65537, 1, 1), 1, geom="cartesian", prec="fp64")
+    op.set_cells_per_block(1)
     assert op.info()["blocks"] > 65536
     dot = torch.zeros(1, dtype=torch.float64, device="cuda")
-    src = torch.zeros(op.n_dofs, dtype=torch.float32, device="cuda")
+    src = torch.zeros(op.n_dofs, dtype=torch.float64, device="cuda")
     dst = torch.zeros_like(src)
     with pytest.raises(dgp.DGError) as e:
         dgp.dg_apply_dot_noalloc(op.handle, src.data_ptr(), dst.data_ptr(), dot.data_ptr())
