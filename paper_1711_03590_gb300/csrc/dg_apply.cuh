@@ -1,4 +1,6 @@
-// Fused element-centric DG apply kernel (one launch per operator evaluation).
+// Fused element-centric DG apply kernel for the binary64 and double-float
+// operators (one launch per operator evaluation; the binary32 operator has
+// its own kernel in dg_apply_f32.cuh).
 //
 // Each CUDA block owns C consecutive cells (C k^2 threads; thread (a,b) of a
 // cell owns one line of k points in whichever direction a phase sweeps).
@@ -88,7 +90,7 @@ struct Smem {
 };
 
 // The outer (output) loops of the line helpers unroll UQ times: fully for
-// binary32/binary64 (matrix entries become constant-bank operands), not at
+// binary64 (matrix entries become constant-bank operands), not at
 // all for double-float, whose 12-instruction products would otherwise
 // overflow the instruction cache (its matrices are then read from shared
 // memory).
@@ -168,7 +170,6 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   T* sW = sE + 2 * K;                     // [K]
   T* sS = sW + K;                         // [K][K] (rows indexed by thread position)
   T* sD = sS + K2;                        // [K][K]
-  constexpr bool kLineFaces = std::is_same<T, float>::value;
   constexpr bool kCompact = std::is_same<T, df64>::value;
   constexpr int kUq = kCompact ? 1 : K;     // unroll of the sweep output loops
   constexpr int kUd = kCompact ? 1 : 3;     // unroll of the face-direction loop
@@ -238,11 +239,10 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
 
   if (tid < 2 * K) sE[tid] = tb.E[tid / K][tid % K];
   if (tid < K) sW[tid] = tb.W[tid];
-  if (!kLineFaces)
-    for (int i = tid; i < K2; i += blockDim.x) {
-      sS[i] = tb.S[i];
-      sD[i] = tb.D[i];
-    }
+  for (int i = tid; i < K2; i += blockDim.x) {
+    sS[i] = tb.S[i];
+    sD[i] = tb.D[i];
+  }
 
   // 1. gather (coalesced over the block's contiguous range)
   {
@@ -327,159 +327,76 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
     }
     __syncthreads();
     // 3b. in-face interpolation of the neighbour's traces to the face Gauss
-    // points.  FP32 (LSU-limited): line sweeps, one thread per line, matrices
-    // with compile-time indices.  FP64 (FP64-pipe-limited, charged per warp
-    // instruction): one thread per face point so that every lane works.
-    if constexpr (kLineFaces) {
-      // along t1 at fixed t2 index j: the value with S and with DS = d/dt1,
-      // the normal derivative with S (Cartesian meshes need no tangential
-      // derivative)
+    // points, one thread per face point so that every lane works (the FP64
+    // pipe is charged per warp instruction).
+    // along t1 (output point (qa = la, j = lb)), then along t2 (point (i = la, qb = lb))
     if (active) {
-      constexpr int NB1 = (OP == OP_SIPG) ? (GEO == GEO_CART ? 2 : 3) : 1;
-      for (int task = ln; task < 2 * NB1 * K; task += K2) {
-        const int s = task / (NB1 * K), f = (task / K) % NB1, j = task % K;
-        if ((s ? nbc[1] : nbc[0]) < 0) continue;
-        const T* in = nba + (s * NBA + (f == 1 ? 1 : 0)) * K2;
-        T* out = nbb + (s * NBB + f) * K2;
-        if (OP == OP_SIPG && f == 2)
-          line_apply_to<K, K>(tb.DS, in, K * j, 1, out, K * j, 1);
-        else
-          line_apply_to<K, K>(tb.S, in, K * j, 1, out, K * j, 1);
-      }
-    }
-    __syncthreads();
-    // ... then along t2 at fixed t1 index i, one thread per line and side for
-    // all fields; it forms the neighbour's derivative along this cell's
-    // outward normal, -j_n(nb) . grad_xi u_nb, at each face point
-    if (active && ln < 2 * K) {
-      const int s = ln / K, i = ln % K;
-      if ((s ? nbc[1] : nbc[0]) >= 0) {
-        const T* in = nbb + s * NBB * K2;
-        T* out = nba + s * NBA * K2;
-        T x0[K], val[K];
 #pragma unroll
-        for (int jj = 0; jj < K; ++jj) x0[jj] = in[i + K * jj];
+      for (int s = 0; s < 2; ++s) {
+        if (nbc[s] < 0) continue;
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-          T acc = T(0);
+        for (int f = 0; f < NBA; ++f) {
+          const T* in = nba + (s * NBA + f) * K2;
+          Acc<T> acc;
+          acc.init();
 #pragma unroll
-          for (int jj = 0; jj < K; ++jj) acc = fma(tb.S[q * K + jj], x0[jj], acc);
-          val[q] = acc;
-          out[i + K * q] = acc;
-        }
-        if (OP == OP_SIPG) {
-          T x1[K], dn[K];
-#pragma unroll
-          for (int jj = 0; jj < K; ++jj) x1[jj] = in[K2 + i + K * jj];
-#pragma unroll
-          for (int q = 0; q < K; ++q) {
-            T acc = T(0);
-#pragma unroll
-            for (int jj = 0; jj < K; ++jj) acc = fma(tb.S[q * K + jj], x1[jj], acc);
-            dn[q] = acc;
-          }
-          if (GEO == GEO_CART) {
-            const T jn = (s ? T(1) : T(-1)) * gm.cart_jinv[d];
-#pragma unroll
-            for (int q = 0; q < K; ++q) out[K2 + i + K * q] = jn * dn[q];
-          } else {
-            T x2[K];
-#pragma unroll
-            for (int jj = 0; jj < K; ++jj) x2[jj] = in[2 * K2 + i + K * jj];
-            const int64_t nfq = gm.nfq[d];
-            const T* fp = gm.face[d] + (s ? fid[1] : fid[0]) * K2 + i;
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-              T dt1 = T(0), dt2 = T(0);
-#pragma unroll
-              for (int jj = 0; jj < K; ++jj) {
-                dt1 = fma(tb.S[q * K + jj], x2[jj], dt1);
-                dt2 = fma(tb.D[q * K + jj], val[jj], dt2);
-              }
-              T gn[3];
-              gn[d] = dn[q];
-              gn[t1] = dt1;
-              gn[t2] = dt2;
-              // the neighbour is slot s of this face (slot 0 = lower side)
-              const T* f = fp + K * q;
-              out[K2 + i + K * q] = -(f[(s * 3 + 0) * nfq] * gn[0] + f[(s * 3 + 1) * nfq] * gn[1] +
-                                      f[(s * 3 + 2) * nfq] * gn[2]);
-            }
-          }
+          for (int i = 0; i < K; ++i) acc.add(sS[la * K + i], in[i + K * lb]);
+          nbb[(s * NBB + f) * K2 + ln] = acc.get();
         }
       }
     }
     __syncthreads();
-    } else {
-      // along t1 (output point (qa = la, j = lb)), then along t2 (point (i = la, qb = lb))
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (nbc[s] < 0) continue;
+#pragma unroll
+        for (int f = 0; f < NBA; ++f) {
+          const T* in = nbb + (s * NBB + f) * K2;
+          Acc<T> acc;
+          acc.init();
+#pragma unroll
+          for (int j = 0; j < K; ++j) acc.add(sS[lb * K + j], in[la + K * j]);
+          nba[(s * NBA + f) * K2 + ln] = acc.get();
+        }
+      }
+    }
+    __syncthreads();
+    // neighbour derivative along this cell's outward normal at point (la, lb)
+    T dnn[2] = {T(0), T(0)};
+    if (OP == OP_SIPG && active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (nbc[s] < 0) continue;
+        const T* nbt = nba + s * NBA * K2;
+        if (GEO == GEO_CART) {
+          dnn[s] = (s ? T(1) : T(-1)) * cjd * nbt[K2 + ln];
+        } else {
+          Acc<T> a1, a2;
+          a1.init();
+          a2.init();
+#pragma unroll
+          for (int i = 0; i < K; ++i) {
+            a1.add(sD[la * K + i], nbt[i + K * lb]);
+            a2.add(sD[lb * K + i], nbt[la + K * i]);
+          }
+          // reference-axis components: d carries the normal derivative,
+          // t1 < t2 the two tangential ones
+          const T gdn = nbt[K2 + ln], ga1 = a1.get(), ga2 = a2.get();
+          const T gx = d == 0 ? gdn : ga1;
+          const T gy = d == 1 ? gdn : (d == 0 ? ga1 : ga2);
+          const T gz = d == 2 ? gdn : ga2;
+          const T* fp = fgeo + fid[s] * K2 + ln;
+          dnn[s] = -(fp[(s * 3 + 0) * nfqd] * gx + fp[(s * 3 + 1) * nfqd] * gy + fp[(s * 3 + 2) * nfqd] * gz);
+        }
+      }
+    }
+    if (OP == OP_SIPG) {
+      __syncthreads();  // every read of the d_n field is done before it is overwritten
       if (active) {
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          if (nbc[s] < 0) continue;
-#pragma unroll
-          for (int f = 0; f < NBA; ++f) {
-            const T* in = nba + (s * NBA + f) * K2;
-            Acc<T> acc;
-            acc.init();
-#pragma unroll
-            for (int i = 0; i < K; ++i) acc.add(sS[la * K + i], in[i + K * lb]);
-            nbb[(s * NBB + f) * K2 + ln] = acc.get();
-          }
-        }
-      }
-      __syncthreads();
-      if (active) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          if (nbc[s] < 0) continue;
-#pragma unroll
-          for (int f = 0; f < NBA; ++f) {
-            const T* in = nbb + (s * NBB + f) * K2;
-            Acc<T> acc;
-            acc.init();
-#pragma unroll
-            for (int j = 0; j < K; ++j) acc.add(sS[lb * K + j], in[la + K * j]);
-            nba[(s * NBA + f) * K2 + ln] = acc.get();
-          }
-        }
-      }
-      __syncthreads();
-      // neighbour derivative along this cell's outward normal at point (la, lb)
-      T dnn[2] = {T(0), T(0)};
-      if (OP == OP_SIPG && active) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          if (nbc[s] < 0) continue;
-          const T* nbt = nba + s * NBA * K2;
-          if (GEO == GEO_CART) {
-            dnn[s] = (s ? T(1) : T(-1)) * cjd * nbt[K2 + ln];
-          } else {
-            Acc<T> a1, a2;
-            a1.init();
-            a2.init();
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-              a1.add(sD[la * K + i], nbt[i + K * lb]);
-              a2.add(sD[lb * K + i], nbt[la + K * i]);
-            }
-            // reference-axis components: d carries the normal derivative,
-            // t1 < t2 the two tangential ones
-            const T gdn = nbt[K2 + ln], ga1 = a1.get(), ga2 = a2.get();
-            const T gx = d == 0 ? gdn : ga1;
-            const T gy = d == 1 ? gdn : (d == 0 ? ga1 : ga2);
-            const T gz = d == 2 ? gdn : ga2;
-            const T* fp = fgeo + fid[s] * K2 + ln;
-            dnn[s] = -(fp[(s * 3 + 0) * nfqd] * gx + fp[(s * 3 + 1) * nfqd] * gy + fp[(s * 3 + 2) * nfqd] * gz);
-          }
-        }
-      }
-      if (OP == OP_SIPG) {
-        __syncthreads();  // every read of the d_n field is done before it is overwritten
-        if (active) {
-#pragma unroll
-          for (int s = 0; s < 2; ++s)
-            if (nbc[s] >= 0) nba[(s * NBA + 1) * K2 + ln] = dnn[s];
-        }
+        for (int s = 0; s < 2; ++s)
+          if (nbc[s] >= 0) nba[(s * NBA + 1) * K2 + ln] = dnn[s];
       }
     }
     __syncthreads();
@@ -571,298 +488,125 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
     __syncthreads();
   }
 
-  if constexpr (kLineFaces) {
-    // 4. (z-line owner) quadrature-point operation and the z faces' test
-    // coefficients, injected along the z line by the thread that formed them
-    if (active) {
-      const T* fz = FT + ((lc * 3 + 2) * 2) * FTF * K2 + ln;
-      T fa[FTF], fb[FTF];
-#pragma unroll
-      for (int f = 0; f < FTF; ++f) {
-        fa[f] = fz[f * K2];
-        fb[f] = fz[(FTF + f) * K2];
-      }
-#pragma unroll
-      for (int z = 0; z < K; ++z) {
-        const int pt = la + K * (lb + K * z);
-        const T e0 = tb.E[0][z], e1 = tb.E[1][z];
-        T t0, t1, t2;
-        const int64_t qi = cell * K3 + pt;
+  // 4. quadrature-point operation and injection of the face test coefficients
+  if (active) {
+    const T e0a = sE[la], e1a = sE[K + la], e0b = sE[lb], e1b = sE[K + lb];
+    const T* ftc = FT + lc * 6 * FTF * K2;
+#pragma unroll(kCompact ? 1 : K)
+    for (int z = 0; z < K; ++z) {
+      const int pt = la + K * (lb + K * z);
+      T fv, fg0 = T(0), fg1 = T(0), fg2 = T(0);
+      {
+        // x faces: along = la, proj = lb + K z; y faces: along = lb, proj = la + K z;
+        // z faces: along = z, proj = la + K lb
+        const T* fx0 = ftc + (0 * 2 + 0) * FTF * K2 + lb + K * z;
+        const T* fx1 = ftc + (0 * 2 + 1) * FTF * K2 + lb + K * z;
+        const T* fy0 = ftc + (1 * 2 + 0) * FTF * K2 + la + K * z;
+        const T* fy1 = ftc + (1 * 2 + 1) * FTF * K2 + la + K * z;
+        const T* fz0 = ftc + (2 * 2 + 0) * FTF * K2 + la + K * lb;
+        const T* fz1 = ftc + (2 * 2 + 1) * FTF * K2 + la + K * lb;
+        const T ez0 = kCompact ? sE[z] : tb.E[0][z], ez1 = kCompact ? sE[K + z] : tb.E[1][z];
+        auto inj = [&](int f) {
+          Acc<T> a;
+          a.init();
+          a.add(e0a, fx0[f * K2]);
+          a.add(e1a, fx1[f * K2]);
+          a.add(e0b, fy0[f * K2]);
+          a.add(e1b, fy1[f * K2]);
+          a.add(ez0, fz0[f * K2]);
+          a.add(ez1, fz1[f * K2]);
+          return a.get();
+        };
+        fv = inj(0);
         if (OP == OP_SIPG) {
-          const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
-          if (GEO == GEO_CART) {
-            T w = sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
-            if (gm.kq) w *= gm.kq[ijk[0] * K + la];
-            t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
-            t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
-            t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
-          } else if (GEO == GEO_FULL) {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            T J[9];
-  #pragma unroll
-            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-            const T jw = cp[9 * n];
-            // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
-            const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
-            const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
-            const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
-            t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
-            t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
-            t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
-          } else {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
-            t0 = a00 * g0 + a01 * g1 + a02 * g2;
-            t1 = a01 * g0 + a11 * g1 + a12 * g2;
-            t2 = a02 * g0 + a12 * g1 + a22 * g2;
-          }
-        } else {
-          const T uq = Uc[pt];
-          T b0, b1, b2;
-          if (GEO == GEO_CART) {
-            const T w = -sW[la] * sW[lb] * tb.W[z] * gm.cart_detj;
-            b0 = w * gm.cart_jinv[0] * gm.vel[0];
-            b1 = w * gm.cart_jinv[1] * gm.vel[1];
-            b2 = w * gm.cart_jinv[2] * gm.vel[2];
-          } else if (GEO == GEO_FULL) {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            T J[9];
-  #pragma unroll
-            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-            const T jw = -cp[9 * n];
-            b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
-            b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
-            b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
-          } else {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            b0 = cp[0];
-            b1 = cp[n];
-            b2 = cp[2 * n];
-          }
-          t0 = b0 * uq;
-          t1 = b1 * uq;
-          t2 = b2 * uq;
-        }
-        if (OP == OP_SIPG) {
-          t0 += e0 * fa[1] + e1 * fb[1];
-          t1 += e0 * fa[2] + e1 * fb[2];
-          t2 += e0 * fa[3] + e1 * fb[3];
-        }
-        G0[pt] = t0;
-        G1[pt] = t1;
-        G2[pt] = t2;
-        Uc[pt] = e0 * fa[0] + e1 * fb[0];
-      }
-    }
-    __syncthreads();
-    // (y-line owner) the y faces' contributions to the x and z gradient fields
-    if (OP == OP_SIPG) {
-      if (active) {
-        const T* fy = FT + ((lc * 3 + 1) * 2) * FTF * K2 + ln;
-        const T a0 = fy[K2], a2 = fy[3 * K2], b0 = fy[(FTF + 1) * K2], b2 = fy[(FTF + 3) * K2];
-#pragma unroll
-        for (int y = 0; y < K; ++y) {
-          const int pt = la + K * (y + K * lb);
-          const T e0 = tb.E[0][y], e1 = tb.E[1][y];
-          G0[pt] += e0 * a0 + e1 * b0;
-          G2[pt] += e0 * a2 + e1 * b2;
+          fg0 = inj(1);
+          fg1 = inj(2);
+          fg2 = inj(3);
         }
       }
-      __syncthreads();
-    }
-    // 5. integration.  x-line owner: V += D^T (T_x + x-face part) + x-face value
-    // part; the x faces' contributions to T_y, T_z are added along the line
-    if (active) {
-      const T* fx = FT + ((lc * 3 + 0) * 2) * FTF * K2 + ln;
-      T fa[FTF], fb[FTF];
-#pragma unroll
-      for (int f = 0; f < FTF; ++f) {
-        fa[f] = fx[f * K2];
-        fb[f] = fx[(FTF + f) * K2];
-      }
-      const int base = K * (la + K * lb);
-      T t[K], v[K];
-#pragma unroll
-      for (int x = 0; x < K; ++x) {
-        const T e0 = tb.E[0][x], e1 = tb.E[1][x];
-        t[x] = G0[base + x];
-        v[x] = Uc[base + x] + e0 * fa[0] + e1 * fb[0];
-        if (OP == OP_SIPG) {
-          t[x] += e0 * fa[1] + e1 * fb[1];
-          G1[base + x] += e0 * fa[2] + e1 * fb[2];
-          G2[base + x] += e0 * fa[3] + e1 * fb[3];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        T acc = v[j];
-#pragma unroll
-        for (int q = 0; q < K; ++q) acc = fma(tb.D[q * K + j], t[q], acc);
-        Uc[base + j] = acc;
-      }
-    }
-    __syncthreads();
-    // y-line owner: V += D^T (T_y + y-face part) + y-face value part
-    if (active) {
-      const T* fy = FT + ((lc * 3 + 1) * 2) * FTF * K2 + ln;
-      const T va = fy[0], vb = fy[FTF * K2];
-      T ga = T(0), gb = T(0);
+      T t0, t1, t2;
+      const int64_t qi = cell * K3 + pt;
       if (OP == OP_SIPG) {
-        ga = fy[2 * K2];
-        gb = fy[(FTF + 2) * K2];
-      }
-      const int base = la + K2 * lb;
-      T t[K], v[K];
+        const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
+        if (GEO == GEO_CART) {
+          T w = sW[la] * sW[lb] * (kCompact ? sW[z] : tb.W[z]) * gm.cart_detj;
+          if (gm.kq) w *= gm.kq[ijk[0] * K + la];
+          t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+          t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+          t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+        } else if (GEO == GEO_FULL) {
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          T J[9];
 #pragma unroll
-      for (int y = 0; y < K; ++y) {
-        const T e0 = tb.E[0][y], e1 = tb.E[1][y];
-        t[y] = G1[base + K * y] + e0 * ga + e1 * gb;
-        v[y] = Uc[base + K * y] + e0 * va + e1 * vb;
-      }
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        T acc = v[j];
-#pragma unroll
-        for (int q = 0; q < K; ++q) acc = fma(tb.D[q * K + j], t[q], acc);
-        Uc[base + K * j] = acc;
-      }
-    }
-    __syncthreads();
-    // z-line owner: V += D^T T_z, then S^T along z, y, x
-    if (active) {
-      line_add_transposed<K, K>(tb.D, G2, Uc, la + K * lb, K2);
-      line_apply<K, true, K>(tb.S, Uc, la + K * lb, K2);
-    }
-    __syncthreads();
-    if (active) line_apply<K, true, K>(tb.S, Uc, la + K2 * lb, K);
-    __syncthreads();
-    if (active) line_apply<K, true, K>(tb.S, Uc, K * (la + K * lb), 1);
-    __syncthreads();
-  } else {
-    // 4. quadrature-point operation and injection of the face test coefficients
-    if (active) {
-      const T e0a = sE[la], e1a = sE[K + la], e0b = sE[lb], e1b = sE[K + lb];
-      const T* ftc = FT + lc * 6 * FTF * K2;
-  #pragma unroll(kCompact ? 1 : K)
-      for (int z = 0; z < K; ++z) {
-        const int pt = la + K * (lb + K * z);
-        T fv, fg0 = T(0), fg1 = T(0), fg2 = T(0);
-        {
-          // x faces: along = la, proj = lb + K z; y faces: along = lb, proj = la + K z;
-          // z faces: along = z, proj = la + K lb
-          const T* fx0 = ftc + (0 * 2 + 0) * FTF * K2 + lb + K * z;
-          const T* fx1 = ftc + (0 * 2 + 1) * FTF * K2 + lb + K * z;
-          const T* fy0 = ftc + (1 * 2 + 0) * FTF * K2 + la + K * z;
-          const T* fy1 = ftc + (1 * 2 + 1) * FTF * K2 + la + K * z;
-          const T* fz0 = ftc + (2 * 2 + 0) * FTF * K2 + la + K * lb;
-          const T* fz1 = ftc + (2 * 2 + 1) * FTF * K2 + la + K * lb;
-          const T ez0 = kCompact ? sE[z] : tb.E[0][z], ez1 = kCompact ? sE[K + z] : tb.E[1][z];
-          auto inj = [&](int f) {
-            Acc<T> a;
-            a.init();
-            a.add(e0a, fx0[f * K2]);
-            a.add(e1a, fx1[f * K2]);
-            a.add(e0b, fy0[f * K2]);
-            a.add(e1b, fy1[f * K2]);
-            a.add(ez0, fz0[f * K2]);
-            a.add(ez1, fz1[f * K2]);
-            return a.get();
-          };
-          fv = inj(0);
-          if (OP == OP_SIPG) {
-            fg0 = inj(1);
-            fg1 = inj(2);
-            fg2 = inj(3);
-          }
-        }
-        T t0, t1, t2;
-        const int64_t qi = cell * K3 + pt;
-        if (OP == OP_SIPG) {
-          const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
-          if (GEO == GEO_CART) {
-            T w = sW[la] * sW[lb] * (kCompact ? sW[z] : tb.W[z]) * gm.cart_detj;
-            if (gm.kq) w *= gm.kq[ijk[0] * K + la];
-            t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
-            t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
-            t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
-          } else if (GEO == GEO_FULL) {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            T J[9];
-  #pragma unroll
-            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-            const T jw = cp[9 * n];
-            // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
-            const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
-            const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
-            const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
-            t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
-            t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
-            t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
-          } else {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
-            t0 = a00 * g0 + a01 * g1 + a02 * g2;
-            t1 = a01 * g0 + a11 * g1 + a12 * g2;
-            t2 = a02 * g0 + a12 * g1 + a22 * g2;
-          }
+          for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+          const T jw = cp[9 * n];
+          // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
+          const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
+          const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
+          const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+          t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
+          t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
+          t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
         } else {
-          const T uq = Uc[pt];
-          T b0, b1, b2;
-          if (GEO == GEO_CART) {
-            const T w = -sW[la] * sW[lb] * (kCompact ? sW[z] : tb.W[z]) * gm.cart_detj;
-            b0 = w * gm.cart_jinv[0] * gm.vel[0];
-            b1 = w * gm.cart_jinv[1] * gm.vel[1];
-            b2 = w * gm.cart_jinv[2] * gm.vel[2];
-          } else if (GEO == GEO_FULL) {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            T J[9];
-  #pragma unroll
-            for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-            const T jw = -cp[9 * n];
-            b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
-            b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
-            b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
-          } else {
-            const T* cp = gm.cell + qi;
-            const int64_t n = gm.ncq;
-            b0 = cp[0];
-            b1 = cp[n];
-            b2 = cp[2 * n];
-          }
-          t0 = b0 * uq;
-          t1 = b1 * uq;
-          t2 = b2 * uq;
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
+          t0 = a00 * g0 + a01 * g1 + a02 * g2;
+          t1 = a01 * g0 + a11 * g1 + a12 * g2;
+          t2 = a02 * g0 + a12 * g1 + a22 * g2;
         }
-        G0[pt] = t0 + fg0;
-        G1[pt] = t1 + fg1;
-        G2[pt] = t2 + fg2;
-        Uc[pt] = fv;
+      } else {
+        const T uq = Uc[pt];
+        T b0, b1, b2;
+        if (GEO == GEO_CART) {
+          const T w = -sW[la] * sW[lb] * (kCompact ? sW[z] : tb.W[z]) * gm.cart_detj;
+          b0 = w * gm.cart_jinv[0] * gm.vel[0];
+          b1 = w * gm.cart_jinv[1] * gm.vel[1];
+          b2 = w * gm.cart_jinv[2] * gm.vel[2];
+        } else if (GEO == GEO_FULL) {
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          T J[9];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+          const T jw = -cp[9 * n];
+          b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
+          b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
+          b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+        } else {
+          const T* cp = gm.cell + qi;
+          const int64_t n = gm.ncq;
+          b0 = cp[0];
+          b1 = cp[n];
+          b2 = cp[2 * n];
+        }
+        t0 = b0 * uq;
+        t1 = b1 * uq;
+        t2 = b2 * uq;
       }
+      G0[pt] = t0 + fg0;
+      G1[pt] = t1 + fg1;
+      G2[pt] = t2 + fg2;
+      Uc[pt] = fv;
     }
-    __syncthreads();
-
-    // 5. integration: V += D^T T_x, D^T T_y, D^T T_z, then S^T along z, y, x
-    if (active) line_add_transposed<K, kUq>(mD, G0, Uc, K * (la + K * lb), 1);
-    __syncthreads();
-    if (active) line_add_transposed<K, kUq>(mD, G1, Uc, la + K2 * lb, K);
-    __syncthreads();
-    if (active) {
-      line_add_transposed<K, kUq>(mD, G2, Uc, la + K * lb, K2);
-      line_apply<K, true, kUq>(mS, Uc, la + K * lb, K2);
-    }
-    __syncthreads();
-    if (active) line_apply<K, true, kUq>(mS, Uc, la + K2 * lb, K);
-    __syncthreads();
-    if (active) line_apply<K, true, kUq>(mS, Uc, K * (la + K * lb), 1);
-    __syncthreads();
   }
+  __syncthreads();
+
+  // 5. integration: V += D^T T_x, D^T T_y, D^T T_z, then S^T along z, y, x
+  if (active) line_add_transposed<K, kUq>(mD, G0, Uc, K * (la + K * lb), 1);
+  __syncthreads();
+  if (active) line_add_transposed<K, kUq>(mD, G1, Uc, la + K2 * lb, K);
+  __syncthreads();
+  if (active) {
+    line_add_transposed<K, kUq>(mD, G2, Uc, la + K * lb, K2);
+    line_apply<K, true, kUq>(mS, Uc, la + K * lb, K2);
+  }
+  __syncthreads();
+  if (active) line_apply<K, true, kUq>(mS, Uc, la + K2 * lb, K);
+  __syncthreads();
+  if (active) line_apply<K, true, kUq>(mS, Uc, K * (la + K * lb), 1);
+  __syncthreads();
 
   // write (set) the block's contiguous range; optional src . dst partial
   {
@@ -876,8 +620,8 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
       if (dot) acc += A::to_double(v) * (double)s[i];
     }
     if (dot) {
-      // the gradient region is free now; its start rounded up to 8 bytes
-      // (C k^3 binary32 values can be an odd count) holds blockDim doubles
+      // the gradient region is free now; its start (rounded up to 8 bytes)
+      // holds blockDim doubles
       double* red = reinterpret_cast<double*>(
           smem_raw + ((size_t)C * K3 * sizeof(T) + 7) / 8 * 8);
       red[tid] = acc;
