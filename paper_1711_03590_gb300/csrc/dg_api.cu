@@ -318,17 +318,22 @@ struct SetupParams {
   double penalty;  // penalty_scale (p+1)^2
   int cblk;        // cell arrays: 0 = structure of arrays, else cell-blocked with this width
   int ncomp;       // number of cell arrays
-  int face_minor;  // face arrays: 0 = [array][face][point], 1 = [array][point][face] with faces
-                   // numbered like cells (x fastest; the face position replaces the index along d)
+  int face_minor;  // face arrays: 0 = [array][face][point]; 1 = blocks of kFaceBlock faces,
+                   // [face block][array][point][face in block], faces numbered like cells
+                   // (x fastest; the face position replaces the index along d)
+  int nfa;         // number of face arrays
   int face_pair;   // binary32 SIPG: both sides' J^{-T} n (else one vector, see setup_face_geometry)
 };
 
-// Position of face f (numbered pos + P_d (i_t1 + n_t1 i_t2)) and point q in
-// a face array of direction d, for the layout selected by S.face_minor.
-__device__ int64_t face_slot(const SetupParams& S, int d, int64_t f, int q, int64_t n_faces) {
+// Position of array m, face f (numbered pos + P_d (i_t1 + n_t1 i_t2)) and
+// point q in the face arrays of direction d, for the layout selected by
+// S.face_minor (nfq = faces x points, the array stride of the plain layout).
+__device__ int64_t face_slot(const SetupParams& S, int d, int m, int64_t f, int q, int64_t nfq) {
   const int k2 = S.k * S.k;
-  if (!S.face_minor) return f * k2 + q;
-  return (int64_t)q * n_faces + dg::face_minor_id(S.n, S.P, d, f);
+  if (!S.face_minor) return m * nfq + f * k2 + q;
+  const int64_t fm = dg::face_minor_id(S.n, S.P, d, f);
+  constexpr int B = dg::kFaceBlock;
+  return ((fm / B) * S.nfa * k2 + (int64_t)m * k2 + q) * B + fm % B;
 }
 
 // x = X + a s(X)(1,1,1), s = sin(pi X) sin(pi Y) sin(pi Z); J = dx/dxi includes 1/n_d
@@ -479,24 +484,24 @@ __global__ void setup_face_geometry(const SetupParams S, int d, int64_t n_faces,
       }
     }
     daw_out[idx] = daw;
-    const int64_t oi = face_slot(S, d, f, q, n_faces);
+    auto at = [&](int m) { return face_slot(S, d, m, f, q, nfq); };
     if (S.op == dg::OP_SIPG && S.face_minor && !S.face_pair) {
       // one vector per face point: J^{-T} n for n = +e_d.  Inside the
       // domain the mapping is smooth, so both sides evaluate the same J at
       // the face and their vectors differ only in the normal's sign (slot 1
       // = -slot 0).  (Not across a periodic boundary of a deformed mesh,
       // where the sine mapping's derivative changes sign: face_pair.)
-      for (int a = 0; a < 3; ++a) out[a * nfq + oi] = (T)(has[0] ? jn[0][a] : -jn[1][a]);
-      out[3 * nfq + oi] = (T)(kap * daw);
+      for (int a = 0; a < 3; ++a) out[at(a)] = (T)(has[0] ? jn[0][a] : -jn[1][a]);
+      out[at(3)] = (T)(kap * daw);
     } else if (S.op == dg::OP_SIPG) {
       for (int slot = 0; slot < 2; ++slot)
-        for (int a = 0; a < 3; ++a) out[(slot * 3 + a) * nfq + oi] = (T)jn[slot][a];
-      out[6 * nfq + oi] = (T)(kap * daw);
+        for (int a = 0; a < 3; ++a) out[at(slot * 3 + a)] = (T)jn[slot][a];
+      out[at(6)] = (T)(kap * daw);
     } else {
       // c.n da w with n the normal pointing to +d (outward normal of the lower side)
       double n[3];
       for (int a = 0; a < 3; ++a) n[a] = has[0] ? nrm[0][a] : -nrm[1][a];
-      out[oi] = (T)((S.vel[0] * n[0] + S.vel[1] * n[1] + S.vel[2] * n[2]) * daw);
+      out[at(0)] = (T)((S.vel[0] * n[0] + S.vel[1] * n[1] + S.vel[2] * n[2]) * daw);
     }
   }
 }
@@ -938,11 +943,22 @@ dg_status setup_geometry(dg_handle* h) {
     const int64_t nf = (int64_t)S.P[d] * h->mesh.n[t1] * h->mesh.n[t2];
     const int64_t nfq = nf * k2;
     const int nfa = h->op == DG_OP_SIPG ? (S.face_minor && !S.face_pair ? 4 : 7) : 1;
+    S.nfa = nfa;
+    // the blocked binary32 layout is padded to whole face blocks (zeros)
+    const int64_t nf_alloc = S.face_minor ? (nf + dg::kFaceBlock - 1) / dg::kFaceBlock * dg::kFaceBlock : nf;
+    const int64_t fbytes = (int64_t)sizeof(T) * nfa * nf_alloc * k2;
     double* daw = nullptr;
-    if ((st = dev_alloc(h, &h->face_geo[d], sizeof(T) * nfa * nfq)) != DG_OK) break;
+    if ((st = dev_alloc(h, &h->face_geo[d], fbytes)) != DG_OK) break;
+    if (nf_alloc != nf) {
+      cudaError_t e = cudaMemsetAsync(h->face_geo[d], 0, fbytes, h->stream);
+      if (e != cudaSuccess) {
+        st = cuda_fail(h, e, "face geometry padding");
+        break;
+      }
+    }
     if (h->op == DG_OP_SIPG && (st = dev_alloc(h, &h->face_tau[d], sizeof(T) * nf)) != DG_OK) break;
     if ((st = dev_alloc(h, (void**)&daw, sizeof(double) * nfq)) != DG_OK) break;
-    h->face_bytes += (int64_t)sizeof(T) * nfa * nfq + (h->op == DG_OP_SIPG ? (int64_t)sizeof(T) * nf : 0);
+    h->face_bytes += fbytes + (h->op == DG_OP_SIPG ? (int64_t)sizeof(T) * nf : 0);
     const int threads = 256;
     setup_face_geometry<T><<<(unsigned)std::min<int64_t>((nfq + threads - 1) / threads, 152 * 64), threads, 0,
                              h->stream>>>(S, d, nf, static_cast<T*>(h->face_geo[d]), nfq, daw, bad);

@@ -59,6 +59,10 @@ struct F32Shape {
 // threads per SM up to k = 6 (72-80 registers), fewer for the longer lines
 // of k >= 7 so that they do not spill; the shared memory of that many blocks
 // fits as well.
+__device__ __forceinline__ void f32_prefetch_bulk_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __host__ __device__ constexpr int f32_min_blocks(int k, int C) {
   return (k <= 6 ? 900 : 700) / (C * k * k) > 0 ? (k <= 6 ? 900 : 700) / (C * k * k) : 1;
 }
@@ -94,6 +98,13 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 
   const Tables<float>& tb = P.tab;
   const Geometry<float>& gm = P.geo;
+  // face arrays: blocks of FBW faces, [face block][array][point][face in
+  // block]; element (m, fp) of face f at face_at(d, f)[(m K2 + fp) FBW]
+  constexpr int FBW = kFaceBlock;
+  const int NFA = SIPG ? (gm.face_pair ? 7 : 4) : 1;
+  auto face_at = [&](int d, int f) -> const float* {
+    return gm.face[d] + (size_t)(f / FBW) * (NFA * K2 * FBW) + f % FBW;
+  };
   const int tid = threadIdx.x;
   const int lc = tid % C;
   const int ln = tid / C;
@@ -149,6 +160,28 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     FID[t * C + lc] = f0 + e0 * (f1 + e1 * f2);
   }
   __syncthreads();
+
+  // start the HBM fetch of this block's cell geometry (read in phase 6)
+  // and face geometry (phases 3, 5, 6) into L2: bulk prefetches of the
+  // geometry block and of the face blocks of the first and last cell of
+  // every face direction and side
+  if constexpr (!CART) {
+    constexpr unsigned BYTES = NA * K3 * CBL * 4, NPF = 8;
+    constexpr unsigned CH = (BYTES / NPF + 15) / 16 * 16;
+    if (tid < (int)NPF) {
+      const char* g = reinterpret_cast<const char*>(gm.cell + ((size_t)(blockIdx.x * C / CBL) * NA * K3) * CBL);
+      const unsigned off = tid * CH;
+      if (off < BYTES) {
+        const unsigned sz = BYTES - off < CH ? BYTES - off : CH;
+        f32_prefetch_bulk_l2(g + off, sz);
+      }
+    } else if (tid < (int)NPF + 12) {
+      const int i = tid - NPF, t = i >> 1, d = t >> 1;
+      const int fb = FID[t * C + ((i & 1) ? C - 1 : 0)] / FBW;
+      if (!(i & 1) || fb != FID[t * C] / FBW)
+        f32_prefetch_bulk_l2(gm.face[d] + (size_t)fb * (NFA * K2 * FBW), NFA * K2 * FBW * 4);
+    }
+  }
 
   // 1. neighbours' face data at GL face point (a, b): the layer on the shared
   // face and (SIPG) the normal derivative D_f of the line through it; x
@@ -290,12 +323,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
           if (SIPG) sn[j] = in[((NBB - 1) * K2 + j * K) * C];
         }
         const float* fg = nullptr;
-        int64_t nfq = 0, nfc = 0;
-        if (TANG) {
-          nfq = gm.nfq[d];
-          nfc = gm.nfc[d];
-          fg = gm.face[d] + qa * nfc + FID[t * C + tc];
-        }
+        if (TANG) fg = face_at(d, FID[t * C + tc]) + qa * FBW;
         const float cj = CART && SIPG ? (s ? 1.f : -1.f) * gm.cart_jinv[d] : 0.f;
 #pragma unroll
         for (int qb = 0; qb < K; ++qb) {
@@ -323,8 +351,8 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
               // face vector j_f = J^{-T} e_d; the neighbour (slot s) has
               // (s ? -j_f : j_f) (face_pair: both stored), and its
               // derivative along this cell's outward normal is minus that
-              const float* f = fg + qb * (K * nfc) + (gm.face_pair ? s * 3 * nfq : 0);
-              const float jd = f[0] * gx + f[nfq] * gy + f[2 * nfq] * gz;
+              const float* f = fg + qb * K * FBW + (gm.face_pair ? s * 3 * K2 * FBW : 0);
+              const float jd = f[0] * gx + f[K2 * FBW] * gy + f[2 * K2 * FBW] * gz;
               wn = (s && !gm.face_pair) ? jd : -jd;
             }
             out[(K2 + qb * K) * C] = wn;
@@ -399,16 +427,15 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
         fjxw = kap * wa * wb * gm.cart_detj * gm.cart_jinv[d];
         tau = gm.cart_tau[d];
       } else {
-        const int64_t nfq = gm.nfq[d];
-        const float* fp = gm.face[d] + ln * (int64_t)gm.nfc[d] + fid;
+        const float* fp = face_at(d, fid) + ln * FBW;
         // own slot 1 - s: the lower side (slot 0) has j_f, the upper -j_f
         // (or both stored: face_pair)
-        const float* jp = fp + (gm.face_pair ? (1 - s) * 3 * nfq : 0);
+        const float* jp = fp + (gm.face_pair ? (1 - s) * 3 * K2 * FBW : 0);
         const float sg = (s || gm.face_pair) ? 1.f : -1.f;
         jo[0] = sg * jp[0];
-        jo[1] = sg * jp[nfq];
-        jo[2] = sg * jp[2 * nfq];
-        fjxw = fp[(gm.face_pair ? 6 : 3) * nfq];
+        jo[1] = sg * jp[K2 * FBW];
+        jo[2] = sg * jp[2 * K2 * FBW];
+        fjxw = fp[(gm.face_pair ? 6 : 3) * K2 * FBW];
         tau = gm.tau[d][fid];
       }
       const float dno = CART ? jo[d] * gf[d] : jo[0] * gf[0] + jo[1] * gf[1] + jo[2] * gf[2];
@@ -422,7 +449,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       if (CART) {
         cn = gm.vel[d] * wa * wb * gm.cart_detj * gm.cart_jinv[d];
       } else {
-        cn = gm.face[d][(size_t)ln * gm.nfc[d] + fid];
+        cn = face_at(d, fid)[ln * FBW];
       }
       const float cno = s ? cn : -cn;  // c.n da w with n the own outward normal
       tvv = interior ? 0.5f * cno * (uf + un) + 0.5f * fabsf(cno) * (uf - un) : fabsf(cno) * uf;

@@ -48,7 +48,7 @@ struct Geometry {
                                   // (binary32 SIPG unless face_pair: 3 j_n of slot 0 + 1 kappa da w)
   const T* __restrict__ tau[3];   // SIPG: penalty per face
   int64_t nfq[3];
-  int nfc[3];  // faces per direction (binary32 layout: [array][point][face])
+  int nfc[3];  // faces per direction
   int face_pair;  // binary32 SIPG face arrays: 1 = both sides' j_n (7 arrays), 0 = one (4)
   // Cartesian compression
   T cart_jinv[3];       // n_d
@@ -92,6 +92,11 @@ __host__ __device__ constexpr int f32_tile_small(int k) { return f32_geometry_bl
 __host__ __device__ constexpr int f32_tile_default(int k) {
   return k == 2 ? 64 : k == 3 ? 32 : k == 4 ? 16 : k <= 6 ? 8 : 4;
 }
+
+// Faces per block of the binary32 face layout [face block][array][point]
+// [face in block]: one block row is a 32-byte sector, and the faces of up to
+// 8 consecutive cells are one contiguous chunk per direction and side.
+constexpr int kFaceBlock = 8;
 
 // Binary32 face numbering: faces of direction d numbered like cells, x
 // fastest, with the face position pos in [0, P_d) in place of the index
