@@ -121,6 +121,31 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     i2 = (int)(q / (unsigned)gm.n[1]);
   }
 
+  // lines of the y and z neighbours through this thread's face points,
+  // loaded before the first barrier so that their latency overlaps the
+  // staging below (short lines only: register budget); boundary sides read
+  // the own cell (their data is not used)
+  constexpr bool EARLY = K <= 6;
+  float wyz[EARLY ? 4 : 1][EARLY ? K : 1];
+  if constexpr (EARLY) {
+    const int n0 = gm.n[0], n01 = gm.n[0] * gm.n[1];
+    const int per = gm.periodic;
+    const int ny[2] = {i1 > 0 ? cell - n0 : per ? cell + (gm.n[1] - 1) * n0 : cell,
+                       i1 < gm.n[1] - 1 ? cell + n0 : per ? cell - (gm.n[1] - 1) * n0 : cell};
+    const int nz[2] = {i2 > 0 ? cell - n01 : per ? cell + (gm.n[2] - 1) * n01 : cell,
+                       i2 < gm.n[2] - 1 ? cell + n01 : per ? cell - (gm.n[2] - 1) * n01 : cell};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const float* py = P.src + (size_t)ny[s] * K3 + a + K2 * b;
+      const float* pz = P.src + (size_t)nz[s] * K3 + a + K * b;
+#pragma unroll
+      for (int l = 0; l < K; ++l) {
+        wyz[s][l] = py[l * K];
+        wyz[2 + s][l] = pz[l * K2];
+      }
+    }
+  }
+
   // the source of the block's cells and their two x-neighbours
   // (cells cell0 - 1 .. cell0 + C, contiguous in memory) staged in shared
   // memory with coalesced loads (cell-major, stride k^3); it occupies the
@@ -206,6 +231,9 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
         for (int l = 0; l < K; ++l) w[l] = p[l];
       }
+    } else if constexpr (EARLY) {
+#pragma unroll
+      for (int l = 0; l < K; ++l) w[l] = wyz[t - 2][l];
     } else {
       const float* p = P.src + (size_t)(nb >= 0 ? nb : cell) * K3 + off;
 #pragma unroll
@@ -554,16 +582,17 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
         // z faces: gradient test along the line
         const float e0 = tb.E[0][j], e1 = tb.E[1][j];
         if (TANG) {
-          t0 += e0 * tgz[0][0] + e1 * tgz[0][1];
-          t1 += e0 * tgz[1][0] + e1 * tgz[1][1];
+          t0 = fmaf(e0, tgz[0][0], fmaf(e1, tgz[0][1], t0));
+          t1 = fmaf(e0, tgz[1][0], fmaf(e1, tgz[1][1], t1));
         }
-        t2[j] += e0 * tgz[2][0] + e1 * tgz[2][1];
+        t2[j] = fmaf(e0, tgz[2][0], fmaf(e1, tgz[2][1], t2[j]));
         if (TANG) {
           // x faces at (y=b, z=j), y faces at (x=a, z=j): their z components
-          t2[j] += ea0 * FT[(((0 * 2 + 0) * 2 + 1) * K2 + b + K * j) * C + lc] +
-                   ea1 * FT[(((0 * 2 + 1) * 2 + 1) * K2 + b + K * j) * C + lc] +
-                   eb0 * FT[(((1 * 2 + 0) * 2 + 1) * K2 + a + K * j) * C + lc] +
-                   eb1 * FT[(((1 * 2 + 1) * 2 + 1) * K2 + a + K * j) * C + lc];
+          float acc = t2[j];
+          acc = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 1) * K2 + b + K * j) * C + lc], acc);
+          acc = fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 1) * K2 + b + K * j) * C + lc], acc);
+          acc = fmaf(eb0, FT[(((1 * 2 + 0) * 2 + 1) * K2 + a + K * j) * C + lc], acc);
+          t2[j] = fmaf(eb1, FT[(((1 * 2 + 1) * 2 + 1) * K2 + a + K * j) * C + lc], acc);
         }
       } else {
         const float uq = lu[j];
@@ -597,7 +626,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      float acc = tb.E[0][i] * tvz[0] + tb.E[1][i] * tvz[1];
+      float acc = fmaf(tb.E[0][i], tvz[0], tb.E[1][i] * tvz[1]);
 #pragma unroll
       for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t2[j], acc);
       U[(a + XS * b + YS * i) * C + lc] = acc;
@@ -620,14 +649,14 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       const int pidx = (a + XS * j + YS * b) * C + lc;
       t1[j] = G1[pidx];
       w[j] = U[pidx];
-      if (SIPG) t1[j] += tb.E[0][j] * tg0 + tb.E[1][j] * tg1;
+      if (SIPG) t1[j] = fmaf(tb.E[0][j], tg0, fmaf(tb.E[1][j], tg1, t1[j]));
       if (TANG)
-        t1[j] += ea0 * FT[(((0 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc] +
-                 ea1 * FT[(((0 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc];
+        t1[j] = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc],
+                     fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc], t1[j]));
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      float acc = w[i] + tb.E[0][i] * tv0 + tb.E[1][i] * tv1;
+      float acc = fmaf(tb.E[0][i], tv0, fmaf(tb.E[1][i], tv1, w[i]));
 #pragma unroll
       for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t1[j], acc);
       U[(a + XS * i + YS * b) * C + lc] = acc;
@@ -651,14 +680,14 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       const int pidx = (j + XS * a + YS * b) * C + lc;
       t0[j] = G0[pidx];
       w[j] = U[pidx];
-      if (SIPG) t0[j] += tb.E[0][j] * tg0 + tb.E[1][j] * tg1;
+      if (SIPG) t0[j] = fmaf(tb.E[0][j], tg0, fmaf(tb.E[1][j], tg1, t0[j]));
       if (TANG)
-        t0[j] += ea0 * FT[(((1 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc] +
-                 ea1 * FT[(((1 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc];
+        t0[j] = fmaf(ea0, FT[(((1 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc],
+                     fmaf(ea1, FT[(((1 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc], t0[j]));
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      float acc = w[i] + tb.E[0][i] * tv0 + tb.E[1][i] * tv1;
+      float acc = fmaf(tb.E[0][i], tv0, fmaf(tb.E[1][i], tv1, w[i]));
 #pragma unroll
       for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t0[j], acc);
       w[i] = acc;
@@ -695,16 +724,19 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     for (int j = 0; j < K; ++j) w[j] = U[(a + XS * b + YS * j) * C + lc];
     float* o = P.dst + (size_t)cell * K3 + a + K * b;
     const float* s = P.src + (size_t)cell * K3 + a + K * b;
-    double acc = 0.0;
+    float r[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      float r = 0.f;
+      float acc = 0.f;
 #pragma unroll
-      for (int j = 0; j < K; ++j) r = fmaf(tb.S[j * K + i], w[j], r);
-      if (valid) o[K2 * i] = r;
-      if (P.dot_partial) acc += (double)r * (double)s[K2 * i];
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[j * K + i], w[j], acc);
+      r[i] = acc;
+      if (valid) o[K2 * i] = acc;
     }
     if (P.dot_partial) {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc += (double)r[i] * (double)s[K2 * i];
       // fixed-order block reduction (FA is free since phase 5)
       double* red = reinterpret_cast<double*>(FA);
       red[tid] = valid ? acc : 0.0;
