@@ -87,11 +87,16 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   float* G0 = U + NP * C;    // gradients, then test fields
   float* G1 = G0 + NP * C;
   float* G2 = G1 + NP * C;
-  float* FA = G2 + NP * C;   // [6 faces][NBF][K2][C]: neighbour data at GL face points,
+  // face buffers: face point (a, b) at a + KP b (odd row pitch KP), fields
+  // KK apart, faces FSA / FSB apart (padded so that the line tasks of the
+  // in-face sweeps are free of bank conflicts)
+  constexpr int KP = f32_face_pitch(K), KK = K * KP;
+  constexpr int FSA = NBF * KK + f32_face_pad(K, C, NBF), FSB = NBB * KK + f32_face_pad(K, C, NBB);
+  float* FA = G2 + NP * C;   // [6 faces][NBF][K KP][C]: neighbour data at GL face points,
                              // then (u+, w+) at the face Gauss points; last: dot reduction
-  float* FB = FA + 6 * NBF * K2 * C;  // [6][NBB][K2][C]: after the first in-face sweep;
-                                      // then the pulled face test components [2][2][2][K2][C]
-  int* NBC = reinterpret_cast<int*>(FB + 6 * NBB * K2 * C);  // [6][C] neighbour cell or -1
+  float* FB = FA + 6 * FSA * C;  // [6][NBB][K KP][C]: after the first in-face sweep;
+                                 // then the pulled face test components [2][2][2][K KP][C]
+  int* NBC = reinterpret_cast<int*>(FB + 6 * FSB * C);  // [6][C] neighbour cell or -1
   int* FID = NBC + 6 * C;                                    // [6][C] face id
   constexpr int RS = K3;  // cell stride of the staged source
   static_assert((C + 2) * RS <= 2 * NP * C, "staged source fits in G1/G2");
@@ -109,6 +114,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   const int lc = tid % C;
   const int ln = tid / C;
   const int a = ln % K, b = ln / K;
+  const int fpt = a + f32_face_pitch(K) * b;  // face point (a, b) in the face buffers
   const int ncell = (int)gm.n_cells;
   const int cell_raw = (int)blockIdx.x * C + lc;
   const bool valid = cell_raw < ncell;
@@ -239,12 +245,12 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
       for (int l = 0; l < K; ++l) w[l] = p[l * str];
     }
-    FA[((t * NBF) * K2 + ln) * C + lc] = s ? w[0] : w[K - 1];
+    FA[(t * FSA + fpt) * C + lc] = s ? w[0] : w[K - 1];
     if (SIPG) {
       float dn = 0.f;
 #pragma unroll
       for (int l = 0; l < K; ++l) dn = fmaf(tb.DF[1 - s][l], w[l], dn);
-      FA[((t * NBF + 1) * K2 + ln) * C + lc] = dn;
+      FA[(t * FSA + KK + fpt) * C + lc] = dn;
     }
     // long lines: keep at most two of them in flight (register budget)
     if (K >= 7 && s == 1) __syncwarp();
@@ -280,13 +286,13 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       if (NTASK % NT == 0 || task < NTASK) {
         const int tc = task % C, rest = task / C;
         const int bb = rest % K, t = rest / K;
-        const float* in = FA + ((t * NBF) * K2 + K * bb) * C + tc;  // row (i, bb)
-        float* out = FB + ((t * NBB) * K2 + K * bb) * C + tc;
+        const float* in = FA + (t * FSA + KP * bb) * C + tc;  // row (i, bb)
+        float* out = FB + (t * FSB + KP * bb) * C + tc;
         float xv[K], xn[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           xv[i] = in[i * C];
-          if (SIPG) xn[i] = in[(K2 + i) * C];
+          if (SIPG) xn[i] = in[(KK + i) * C];
         }
 #pragma unroll
         for (int qa = 0; qa < K; ++qa) {
@@ -298,8 +304,8 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
             if (SIPG) s2 = fmaf(tb.S[qa * K + i], xn[i], s2);
           }
           out[qa * C] = s0;
-          if (TANG) out[(K2 + qa) * C] = s1;
-          if (SIPG) out[((NBB - 1) * K2 + qa) * C] = s2;
+          if (TANG) out[(KK + qa) * C] = s1;
+          if (SIPG) out[((NBB - 1) * KK + qa) * C] = s2;
         }
       }
     }
@@ -341,14 +347,14 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
         const int tc = task % C, rest = task / C;
         const int qa = rest % K, t = rest / K;
         const int d = t >> 1, s = t & 1;
-        const float* in = FB + ((t * NBB) * K2 + qa) * C + tc;  // row (qa, j): stride K C
-        float* out = FA + ((t * NBF) * K2 + qa) * C + tc;
+        const float* in = FB + (t * FSB + qa) * C + tc;  // row (qa, j): stride KP C
+        float* out = FA + (t * FSA + qa) * C + tc;
         float sv[K], dsv[K], sn[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          sv[j] = in[j * K * C];
-          if (TANG) dsv[j] = in[(K2 + j * K) * C];
-          if (SIPG) sn[j] = in[((NBB - 1) * K2 + j * K) * C];
+          sv[j] = in[j * KP * C];
+          if (TANG) dsv[j] = in[(KK + j * KP) * C];
+          if (SIPG) sn[j] = in[((NBB - 1) * KK + j * KP) * C];
         }
         const float* fg = nullptr;
         if (TANG) fg = face_at(d, FID[t * C + tc]) + qa * FBW;
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
             }
             if (SIPG) dn = fmaf(tb.S[qb * K + j], sn[j], dn);
           }
-          out[qb * K * C] = u;
+          out[qb * KP * C] = u;
           if (SIPG) {
             float wn;
             if (CART) {
@@ -383,7 +389,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
               const float jd = f[0] * gx + f[K2 * FBW] * gy + f[2 * K2 * FBW] * gz;
               wn = (s && !gm.face_pair) ? jd : -jd;
             }
-            out[(K2 + qb * K) * C] = wn;
+            out[(KK + qb * KP) * C] = wn;
           }
         }
       }
@@ -439,11 +445,11 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
           if (c == d || TANG) gf[c] = fmaf(e, lg[c][j], gf[c]);
       }
     }
-    const float* slot = FA + ((t * NBF) * K2 + ln) * C + lc;  // this thread's (u+, w+) of face t
+    const float* slot = FA + (t * FSA + fpt) * C + lc;  // this thread's (u+, w+) of face t
     const float un = slot[0];
     tgo[0] = tgo[1] = tgo[2] = 0.f;
     if (SIPG) {
-      const float wn = slot[K2 * C];
+      const float wn = slot[KK * C];
       float jo[3], fjxw, tau;
       if (CART) {
         const float jn = (s ? 1.f : -1.f) * gm.cart_jinv[d];
@@ -500,13 +506,13 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     for (int s = 0; s < 2; ++s) {
       float tvv, tgo[3];
       own_flux(dc, s, lu, lg, tvv, tgo);
-      float* slot = FA + (((2 * d + s) * NBF) * K2 + ln) * C + lc;
+      float* slot = FA + ((2 * d + s) * FSA + fpt) * C + lc;
       slot[0] = tvv;
-      if (SIPG) slot[K2 * C] = tgo[d];
+      if (SIPG) slot[KK * C] = tgo[d];
       if (TANG) {
         // x faces give components 1 and 2, y faces 0 and 2
-        FT[(((d * 2 + s) * 2 + 0) * K2 + ln) * C + lc] = tgo[d == 0 ? 1 : 0];
-        FT[(((d * 2 + s) * 2 + 1) * K2 + ln) * C + lc] = tgo[2];
+        FT[(((d * 2 + s) * 2 + 0) * KK + fpt) * C + lc] = tgo[d == 0 ? 1 : 0];
+        FT[(((d * 2 + s) * 2 + 1) * KK + fpt) * C + lc] = tgo[2];
       }
     }
   };
@@ -589,10 +595,10 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
         if (TANG) {
           // x faces at (y=b, z=j), y faces at (x=a, z=j): their z components
           float acc = t2[j];
-          acc = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 1) * K2 + b + K * j) * C + lc], acc);
-          acc = fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 1) * K2 + b + K * j) * C + lc], acc);
-          acc = fmaf(eb0, FT[(((1 * 2 + 0) * 2 + 1) * K2 + a + K * j) * C + lc], acc);
-          t2[j] = fmaf(eb1, FT[(((1 * 2 + 1) * 2 + 1) * K2 + a + K * j) * C + lc], acc);
+          acc = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 1) * KK + b + KP * j) * C + lc], acc);
+          acc = fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 1) * KK + b + KP * j) * C + lc], acc);
+          acc = fmaf(eb0, FT[(((1 * 2 + 0) * 2 + 1) * KK + a + KP * j) * C + lc], acc);
+          t2[j] = fmaf(eb1, FT[(((1 * 2 + 1) * 2 + 1) * KK + a + KP * j) * C + lc], acc);
         }
       } else {
         const float uq = lu[j];
@@ -636,12 +642,12 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 
   // 7. y-line owner (x=a, z=b): x-face and own y-face y components, D_y^T
   {
-    const float* own = FA + ((2 * NBF) * K2 + ln) * C + lc;  // faces (1, s): tv, t_y part
-    const float tv0 = own[0], tv1 = own[NBF * K2 * C];
+    const float* own = FA + (2 * FSA + fpt) * C + lc;  // faces (1, s): tv, t_y part
+    const float tv0 = own[0], tv1 = own[FSA * C];
     float tg0 = 0.f, tg1 = 0.f;
     if (SIPG) {
-      tg0 = own[K2 * C];
-      tg1 = own[(NBF + 1) * K2 * C];
+      tg0 = own[KK * C];
+      tg1 = own[(FSA + KK) * C];
     }
     float t1[K], w[K];
 #pragma unroll
@@ -651,8 +657,8 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       w[j] = U[pidx];
       if (SIPG) t1[j] = fmaf(tb.E[0][j], tg0, fmaf(tb.E[1][j], tg1, t1[j]));
       if (TANG)
-        t1[j] = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc],
-                     fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc], t1[j]));
+        t1[j] = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 0) * KK + j + KP * b) * C + lc],
+                     fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 0) * KK + j + KP * b) * C + lc], t1[j]));
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
@@ -667,12 +673,12 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   // 8. x-line owner (y=a, z=b): y-face and own x-face x components, D_x^T,
   // then S_x^T (the integrated field is complete along x here)
   {
-    const float* own = FA + ln * C + lc;  // faces (0, s): tv, t_x part
-    const float tv0 = own[0], tv1 = own[NBF * K2 * C];
+    const float* own = FA + fpt * C + lc;  // faces (0, s): tv, t_x part
+    const float tv0 = own[0], tv1 = own[FSA * C];
     float tg0 = 0.f, tg1 = 0.f;
     if (SIPG) {
-      tg0 = own[K2 * C];
-      tg1 = own[(NBF + 1) * K2 * C];
+      tg0 = own[KK * C];
+      tg1 = own[(FSA + KK) * C];
     }
     float t0[K], w[K];
 #pragma unroll
@@ -682,8 +688,8 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       w[j] = U[pidx];
       if (SIPG) t0[j] = fmaf(tb.E[0][j], tg0, fmaf(tb.E[1][j], tg1, t0[j]));
       if (TANG)
-        t0[j] = fmaf(ea0, FT[(((1 * 2 + 0) * 2 + 0) * K2 + j + K * b) * C + lc],
-                     fmaf(ea1, FT[(((1 * 2 + 1) * 2 + 0) * K2 + j + K * b) * C + lc], t0[j]));
+        t0[j] = fmaf(ea0, FT[(((1 * 2 + 0) * 2 + 0) * KK + j + KP * b) * C + lc],
+                     fmaf(ea1, FT[(((1 * 2 + 1) * 2 + 0) * KK + j + KP * b) * C + lc], t0[j]));
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {

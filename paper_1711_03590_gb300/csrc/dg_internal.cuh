@@ -115,12 +115,25 @@ __host__ __device__ inline int64_t face_minor_id(const int n[3], const int P[3],
   return c[0] + (int64_t)e0 * (c[1] + (int64_t)e1 * c[2]);
 }
 
+// Face buffers of the binary32 kernel: odd row pitch, and per-face padding
+// (in scalars, for nf fields per face) chosen so that the line tasks of the
+// in-face sweeps, C cells per block, touch every shared-memory bank once.
+__host__ __device__ constexpr int f32_face_pitch(int k) { return k % 2 ? k : k + 1; }
+__host__ __device__ constexpr int f32_face_pad(int k, int C, int nf) {
+  return nf == 2 ? (k == 3 && C == 16 ? 1 : k == 5 ? (C == 8 ? 3 : 1) : k == 6 ? 2 : k == 7 ? (C == 4 ? 5 : 1)
+                    : k == 9 ? (C == 4 ? 7 : 3) : 0)
+         : nf == 3 ? (k == 5 && C == 8 ? 2 : k == 7 && C == 4 ? 4 : k == 9 ? (C == 4 ? 6 : 2) : 0)
+                   : 0;
+}
+
 // Shared-memory bytes of the binary32 kernel for k points and C cells: four
-// padded point fields, the neighbour face data (6 faces x 2 fields x k^2),
-// the in-face sweep buffer (6 x 3 x k^2) and two face tables (6 ints each).
+// padded point fields, the neighbour face data (6 faces x 2 fields), the
+// in-face sweep buffer (6 faces x 3 fields) and two face tables (6 ints each).
 __host__ __device__ constexpr int f32_smem_bytes(int k, int op, int C) {
-  return 4 * (4 * (k * (k % 2 == 0 ? k + 1 : k) * k) * C + 6 * (op == OP_SIPG ? 2 : 1) * k * k * C +
-              6 * (op == OP_SIPG ? 3 : 1) * k * k * C + 12 * C);
+  return 4 * (4 * (k * (k % 2 == 0 ? k + 1 : k) * k) * C +
+              6 * ((op == OP_SIPG ? 2 : 1) * k * f32_face_pitch(k) + f32_face_pad(k, C, op == OP_SIPG ? 2 : 1)) * C +
+              6 * ((op == OP_SIPG ? 3 : 1) * k * f32_face_pitch(k) + f32_face_pad(k, C, op == OP_SIPG ? 3 : 1)) * C +
+              12 * C);
 }
 
 // Shared-memory scalars per cell: u, three gradient fields, the two
