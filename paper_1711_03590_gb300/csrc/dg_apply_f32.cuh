@@ -516,14 +516,16 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       }
     }
   };
-  xy_faces(std::integral_constant<int, 0>{});
-  xy_faces(std::integral_constant<int, 1>{});
-  __syncthreads();
-
-  // 6. z-line owner: z-face traces and fluxes, q-point operation at
-  // (a, b, j), z-face injection, the z components of the x- and y-face
-  // gradient tests, then D_z^T
-  {
+  // z-line owner: z-face traces and fluxes, q-point operation at (a, b, j)
+  // (Sec. 5 geometry), z-face injection; results: the reference
+  // gradient-test fields along the line (tz0..tz2) and the z faces' value
+  // tests tvz.
+  // It reads only fields that are complete after phase 4 and its own face
+  // slots, so for short lines it runs before the barrier below, and its
+  // geometry loads overlap the x and y face work; the stores of tz0, tz1 into
+  // G0, G1 (read by the x and y traces) follow the barrier.
+  float tz0[K], tz1[K], tz2[K], tvz[2];
+  auto z_line = [&]() {
     float lu[K], lg[3][K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -535,7 +537,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
         lg[2][j] = G2[pidx];
       }
     }
-    float tvz[2], tgz[3][2];
+    float tgz[3][2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       float tvv, tgo[3];
@@ -544,7 +546,6 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
       for (int c = 0; c < 3; ++c) tgz[c][s] = tgo[c];
     }
-    float t2[K];
     // cell-blocked geometry: array m, point q of cell c at
     // ((c / CBL) NA + m) K3 + q) CBL + c mod CBL (padded to whole blocks,
     // so the unclamped index of tail threads stays inside the allocation)
@@ -556,16 +557,14 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const int q = a + K * b + K2 * j;
-      const int pidx = (a + XS * b + YS * j) * C + lc;
       const float* cp = CART ? gm.cell : gm.cell + gofs + (size_t)q * CBL;
-      float t0, t1;
       if (SIPG) {
         const float g0 = lg[0][j], g1 = lg[1][j], g2 = lg[2][j];
         if (CART) {
           const float w = wa * wb * tb.W[j] * gm.cart_detj * kx;
-          t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
-          t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
-          t2[j] = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+          tz0[j] = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+          tz1[j] = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+          tz2[j] = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
         } else if (GEO == GEO_FULL) {
           float J[9];
 #pragma unroll
@@ -575,31 +574,23 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
           const float x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
           const float x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
           const float x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
-          t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
-          t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
-          t2[j] = J[6] * x0 + J[7] * x1 + J[8] * x2;
+          tz0[j] = J[0] * x0 + J[1] * x1 + J[2] * x2;
+          tz1[j] = J[3] * x0 + J[4] * x1 + J[5] * x2;
+          tz2[j] = J[6] * x0 + J[7] * x1 + J[8] * x2;
         } else {
           const float a00 = cp[0], a01 = cp[MS], a02 = cp[2 * MS], a11 = cp[3 * MS], a12 = cp[4 * MS],
                       a22 = cp[5 * MS];
-          t0 = a00 * g0 + a01 * g1 + a02 * g2;
-          t1 = a01 * g0 + a11 * g1 + a12 * g2;
-          t2[j] = a02 * g0 + a12 * g1 + a22 * g2;
+          tz0[j] = a00 * g0 + a01 * g1 + a02 * g2;
+          tz1[j] = a01 * g0 + a11 * g1 + a12 * g2;
+          tz2[j] = a02 * g0 + a12 * g1 + a22 * g2;
         }
         // z faces: gradient test along the line
         const float e0 = tb.E[0][j], e1 = tb.E[1][j];
         if (TANG) {
-          t0 = fmaf(e0, tgz[0][0], fmaf(e1, tgz[0][1], t0));
-          t1 = fmaf(e0, tgz[1][0], fmaf(e1, tgz[1][1], t1));
+          tz0[j] = fmaf(e0, tgz[0][0], fmaf(e1, tgz[0][1], tz0[j]));
+          tz1[j] = fmaf(e0, tgz[1][0], fmaf(e1, tgz[1][1], tz1[j]));
         }
-        t2[j] = fmaf(e0, tgz[2][0], fmaf(e1, tgz[2][1], t2[j]));
-        if (TANG) {
-          // x faces at (y=b, z=j), y faces at (x=a, z=j): their z components
-          float acc = t2[j];
-          acc = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 1) * KK + b + KP * j) * C + lc], acc);
-          acc = fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 1) * KK + b + KP * j) * C + lc], acc);
-          acc = fmaf(eb0, FT[(((1 * 2 + 0) * 2 + 1) * KK + a + KP * j) * C + lc], acc);
-          t2[j] = fmaf(eb1, FT[(((1 * 2 + 1) * 2 + 1) * KK + a + KP * j) * C + lc], acc);
-        }
+        tz2[j] = fmaf(e0, tgz[2][0], fmaf(e1, tgz[2][1], tz2[j]));
       } else {
         const float uq = lu[j];
         float b0, b1, b2;
@@ -621,20 +612,42 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
           b1 = cp[MS];
           b2 = cp[2 * MS];
         }
-        t0 = b0 * uq;
-        t1 = b1 * uq;
-        t2[j] = b2 * uq;
+        tz0[j] = b0 * uq;
+        tz1[j] = b1 * uq;
+        tz2[j] = b2 * uq;
       }
-      G0[pidx] = t0;
-      G1[pidx] = t1;
       // long lines: bound the geometry loads in flight (register budget)
       if (K >= 7 && !CART && j % 2 == 1) __syncwarp();
+    }
+  };
+  if constexpr (EARLY) z_line();
+  xy_faces(std::integral_constant<int, 0>{});
+  xy_faces(std::integral_constant<int, 1>{});
+  __syncthreads();
+
+  // 6. z-line owner: the pulled z components of the x- and y-face gradient
+  // tests, then D_z^T
+  {
+    if constexpr (!EARLY) z_line();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int pidx = (a + XS * b + YS * j) * C + lc;
+      G0[pidx] = tz0[j];
+      G1[pidx] = tz1[j];
+      if (TANG) {
+        // x faces at (y=b, z=j), y faces at (x=a, z=j)
+        float acc = tz2[j];
+        acc = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 1) * KK + b + KP * j) * C + lc], acc);
+        acc = fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 1) * KK + b + KP * j) * C + lc], acc);
+        acc = fmaf(eb0, FT[(((1 * 2 + 0) * 2 + 1) * KK + a + KP * j) * C + lc], acc);
+        tz2[j] = fmaf(eb1, FT[(((1 * 2 + 1) * 2 + 1) * KK + a + KP * j) * C + lc], acc);
+      }
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       float acc = fmaf(tb.E[0][i], tvz[0], tb.E[1][i] * tvz[1]);
 #pragma unroll
-      for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t2[j], acc);
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], tz2[j], acc);
       U[(a + XS * b + YS * i) * C + lc] = acc;
     }
   }
