@@ -85,7 +85,7 @@ __host__ __device__ constexpr int cells_per_block(int k) {
 // Cell-block width of the binary32 kernel's cell geometry layout (the largest
 // of its compiled tile shapes, which all divide it).
 __host__ __device__ constexpr int f32_geometry_block(int k) {
-  return k == 2 ? 64 : k == 3 ? 32 : k <= 5 ? 16 : 8;
+  return k == 2 ? 32 : k == 3 ? 16 : 8;
 }
 // Compiled tile shapes (cells per block) of the binary32 kernel, and the
 // default: the faster of the two on the 32^3 deformed G3 SIPG apply (GB300).
@@ -121,8 +121,8 @@ __host__ __device__ inline int64_t face_minor_id(const int n[3], const int P[3],
 // in-face sweeps, C cells per block, touch every shared-memory bank once.
 __host__ __device__ constexpr int f32_face_pitch(int k) { return k % 2 ? k : k + 1; }
 __host__ __device__ constexpr int f32_face_pad(int k, int C, int nf) {
-  return nf == 2 ? (k == 3 && C == 16 ? 1 : k == 5 ? (C == 8 ? 3 : 1) : k == 6 ? 2 : k == 7 ? (C == 4 ? 5 : 1)
-                    : k == 9 ? (C == 4 ? 7 : 3) : 0)
+  return nf == 2 ? (k == 3 ? (C == 32 ? 0 : 1) : k == 4 && C == 4 ? 4 : k == 5 ? (C == 16 ? 1 : 3) : k == 6 ? 2
+                    : k == 7 ? (C == 4 ? 5 : 1) : k == 9 ? (C == 4 ? 7 : 3) : 0)
          : nf == 3 ? (k == 5 && C == 8 ? 2 : k == 7 && C == 4 ? 4 : k == 9 ? (C == 4 ? 6 : 2) : 0)
                    : 0;
 }
