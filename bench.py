@@ -386,6 +386,39 @@ def config3_metrics(torch, dgp, rtol=1e-10, cases=(("cartesian_64^3_p3", 64, 3, 
     return out
 
 
+def degree_sweep_metrics(torch, dgp, steps=30):
+    """Apply throughput for p = 1..8 in FP64 and FP32 on the 32^3 mesh and on
+    the paper's larger-than-cache size schedule (128^3 for p = 1-2, 64^3 for
+    p = 3-5, 32^3 for p = 6-8), Cartesian, G3 (deformed, full Jacobians) and
+    G4 (deformed, merged coefficients); DoFs/s from the mean per-launch CUDA
+    event time after warm-up, and the HBM fraction of the algorithmic bytes."""
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    rows = []
+    for p in range(1, 9):
+        for sched, n in (("32^3", 32), ("paper", dg_inputs.paper_size_schedule(p))):
+            if sched == "paper" and n == 32:
+                continue
+            for geom, mapping in (("cartesian", 0), ("full", 1), ("merged", 1)):
+                for prec in ("fp64", "fp32"):
+                    o = dgp.Operator(n, p, geom=geom, prec=prec, mapping=mapping, amplitude=0.1, coeff=1)
+                    src = torch.tensor(dg_inputs.src_vector(o.n_dofs, 3), dtype=o.dtype, device="cuda")
+                    dst = torch.empty_like(src)
+                    for _ in range(3):
+                        o.apply(src, dst)
+                    _, ms = time_applies(torch, o, src, dst, steps)
+                    s = 4 if prec == "fp32" else 8
+                    bpd = bytes_per_dof(p + 1, s, "sipg", geom)
+                    rows.append({"p": p, "mesh": "%d^3" % n, "schedule": sched, "geometry": geom, "prec": prec,
+                                 "dofs": o.n_dofs, "us": round(ms * 1e3, 2),
+                                 "gdofs_per_s": round(o.n_dofs / (ms / 1e3) / 1e9, 3),
+                                 "hbm_frac": round(bpd * o.n_dofs / (ms / 1e3) / 1e9 / hbm, 4)})
+                    o.close()
+                    del src, dst
+                    torch.cuda.empty_cache()
+    return {"operator": "SIPG, kappa = 1 + 0.5 sin(2 pi x), Dirichlet", "hbm_peak_gbs": hbm, "rows": rows}
+
+
 def cpu_baseline(workload, form, target_s=12.0):
     """The FP64 oracle (cell-by-cell brute-force quadrature, OpenMP on the
     host cores) on a seeded sample of cells of the same workload; DoFs/s =
@@ -460,6 +493,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--solve-config3", action="store_true",
                     help="only run the full-size mixed-precision solves and print their JSON")
+    ap.add_argument("--degree-sweep", action="store_true",
+                    help="only run the apply degree sweep (32^3 and the paper's size schedule) and print its JSON")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -480,6 +515,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
+    if args.degree_sweep:
+        if rank == 0:
+            print(json.dumps({"degree_sweep": degree_sweep_metrics(torch, dgp)}), flush=True)
+        return
     if args.solve_config3:
         if rank == 0:
             print(json.dumps({"solve_config3": config3_metrics(torch, dgp)}), flush=True)
