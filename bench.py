@@ -46,20 +46,37 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def kernel_flops_per_cell(k, op, geom):
-    """Floating-point operations of one cell in the fused apply kernel as
-    implemented (FMA = 2): tensor-product sweeps on the cell, the
-    neighbour's face-normal and in-face interpolation, the own-side face
+def even_odd_ops(k, anti):
+    """Operations of one 1D kernel on a line of k values in even-odd form
+    (Sec. 4.1): k - (k mod 2) sums/differences, h = k // 2 output pairs
+    from (k+1)//2 even and h odd products plus their sum and difference, and
+    the middle output for odd k."""
+    h, h2 = k // 2, (k + 1) // 2
+    return 2 * h + h * (h2 + h + 2) + ((h if anti else h2) if k % 2 else 0)
+
+
+def kernel_flops_per_cell(k, op, geom, even_odd=False):
+    """Floating-point work of one cell in the apply kernels as implemented,
+    counted as 2 per arithmetic instruction (an FMA, or an add or multiply
+    that takes an FMA slot of the pipe): tensor-product sweeps on the cell,
+    the neighbour's face-normal and in-face interpolation, the own-side face
     traces and flux at every face point, the quadrature-point operation and
-    the injection of the face coefficients."""
+    the injection of the face coefficients.  even_odd: the cell sweeps in
+    even-odd form (the binary64 kernel for k >= 5)."""
     k2, k3, k4 = k * k, k ** 3, k ** 4
     if op == "sipg":
-        sweeps = 24 * k4                   # 12 sweeps (3 S, 3 D^co, 3 D^T, 3 S^T), k^4 FMA each
+        if even_odd:   # 3 S + 3 S^T (centrosymmetric), 3 D + 3 D^T (anti), D^T accumulated
+            sweeps = 2 * k2 * (6 * even_odd_ops(k, False) + 6 * even_odd_ops(k, True) + 3 * k)
+        else:
+            sweeps = 24 * k4                   # 12 sweeps (3 S, 3 D^co, 3 D^T, 3 S^T), k^4 FMA each
         nb = 6 * 2 * (k3 + 4 * k3)        # 6 faces: D_f (k^3 FMA) + 2 fields x 2 in-face sweeps
         flux = 6 * k2 * (2 * 6 * k + 20)  # own value + 3 gradients, 2 neighbour tangential, flux
         qop = {"full": 39, "merged": 15, "cartesian": 8}[geom] + 48  # q-op + 24 FMA injection
         return sweeps + nb + flux + qop * k3
-    sweeps = 18 * k4                       # 3 S, 3 D^T, 3 S^T
+    if even_odd:
+        sweeps = 2 * k2 * (6 * even_odd_ops(k, False) + 3 * even_odd_ops(k, True) + 3 * k)
+    else:
+        sweeps = 18 * k4                       # 3 S, 3 D^T, 3 S^T
     nb = 6 * 2 * (2 * k3)                  # value layer, 2 in-face sweeps
     flux = 6 * k2 * (2 * k + 8)
     qop = {"full": 24, "merged": 3, "cartesian": 3}[geom] + 3 + 12
@@ -556,11 +573,14 @@ def main():
     ms_per_step = t_max / args.steps
 
     # roofline of the apply kernel (the only kernel of a step)
-    flops = kernel_flops_per_cell(k, "sipg", w["geom"]) * n_cells
+    flops = kernel_flops_per_cell(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5)) * n_cells
     achieved_tf = flops / (launch_ms / 1e3) / 1e12
     bpd = bytes_per_dof(k, ssz, "sipg", w["geom"])
     achieved_gbs = bpd * n / (launch_ms / 1e3) / 1e9
-    kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, {"fp64": "double", "fp32": "float", "fp64emu": "df64"}[args.prec])
+    if args.prec == "fp32":
+        kname = "apply_f32_kernel<%d,%d,FULL,SIPG>" % (k, op.info()["cells_per_block"])
+    else:
+        kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, {"fp64": "double", "fp64emu": "df64"}[args.prec])
     hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": kname, "bytes_per_dof": bpd,
            "peak_source": peaks.get("source")}

@@ -218,6 +218,21 @@ dg::Tables<T> cast_tables(int k, const Tables64& t) {
       o.DF[s][i] = (T)t.DF[s][i];
     }
   for (int i = 0; i < k; ++i) o.W[i] = (T)t.gw[i];
+  // even-odd halves, from the FP64 tables
+  const int h = k / 2, h2 = (k + 1) / 2;
+  for (int m = 0; m < 4; ++m) {
+    auto M = [&](int q, int i) {
+      return m == dg::EO_S ? t.S[q * k + i] : m == dg::EO_ST ? t.S[i * k + q] : m == dg::EO_D ? t.D[q * k + i]
+                                                                                               : t.D[i * k + q];
+    };
+    for (int q = 0; q < h2; ++q) {
+      for (int i = 0; i < h; ++i) {
+        o.EO[m][0][q * dg::kHalf + i] = (T)(0.5 * (M(q, i) + M(q, k - 1 - i)));
+        o.EO[m][1][q * dg::kHalf + i] = (T)(0.5 * (M(q, i) - M(q, k - 1 - i)));
+      }
+      if (k % 2) o.EO[m][0][q * dg::kHalf + h] = (T)M(q, h);
+    }
+  }
   return o;
 }
 

@@ -145,6 +145,80 @@ __device__ __forceinline__ void line_add_transposed(const T* __restrict__ M, con
   }
 }
 
+// Even-odd form of a 1D kernel (Sec. 4.1): out = M in for a
+// centrosymmetric (ANTI = false: S, S^T) or anti-centrosymmetric (ANTI =
+// true: D, D^T) k x k matrix from its even and odd halves ME, MO (see
+// Tables::EO): about k^2/2 + 2k operations instead of k^2.
+template <int K, bool ANTI, typename T>
+__device__ __forceinline__ void eo_line(const T* __restrict__ ME, const T* __restrict__ MO, const T (&in)[K],
+                                        T (&out)[K]) {
+  constexpr int h = K / 2, H2 = (K + 1) / 2;
+  T e[H2], o[h];
+#pragma unroll
+  for (int i = 0; i < h; ++i) {
+    e[i] = in[i] + in[K - 1 - i];
+    o[i] = in[i] - in[K - 1 - i];
+  }
+  if (K % 2) e[h] = in[h];
+#pragma unroll
+  for (int q = 0; q < h; ++q) {
+    T ev = ME[q * kHalf] * e[0];
+#pragma unroll
+    for (int i = 1; i < H2; ++i) ev = fma(ME[q * kHalf + i], e[i], ev);
+    T od = MO[q * kHalf] * o[0];
+#pragma unroll
+    for (int i = 1; i < h; ++i) od = fma(MO[q * kHalf + i], o[i], od);
+    out[q] = ev + od;
+    out[K - 1 - q] = ANTI ? od - ev : ev - od;
+  }
+  if (K % 2) {
+    T mid;
+    if (!ANTI) {
+      mid = ME[h * kHalf] * e[0];
+#pragma unroll
+      for (int i = 1; i < H2; ++i) mid = fma(ME[h * kHalf + i], e[i], mid);
+    } else {
+      mid = MO[h * kHalf] * o[0];
+#pragma unroll
+      for (int i = 1; i < h; ++i) mid = fma(MO[h * kHalf + i], o[i], mid);
+    }
+    out[h] = mid;
+  }
+}
+
+// The sweeps of the binary64 kernel in even-odd form (k >= 5, where it saves
+// operations): S or S^T in place on a line, D from a line to a line, and
+// v += D^T t along a line.
+template <int K, int WHICH, typename T>
+__device__ __forceinline__ void eo_apply(const Tables<T>& tb, T* v, int base, int stride) {
+  T in[K], out[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) in[i] = v[base + i * stride];
+  eo_line<K, false>(tb.EO[WHICH][0], tb.EO[WHICH][1], in, out);
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[base + i * stride] = out[i];
+}
+template <int K, typename T>
+__device__ __forceinline__ void eo_derivative_to(const Tables<T>& tb, const T* in, int ib, int is, T* out_, int ob,
+                                                 int os) {
+  T x[K], out[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) x[i] = in[ib + i * is];
+  eo_line<K, true>(tb.EO[EO_D][0], tb.EO[EO_D][1], x, out);
+#pragma unroll
+  for (int i = 0; i < K; ++i) out_[ob + i * os] = out[i];
+}
+template <int K, typename T>
+__device__ __forceinline__ void eo_add_derivative_transposed(const Tables<T>& tb, const T* t, T* v, int base,
+                                                             int stride) {
+  T x[K], out[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) x[i] = t[base + i * stride];
+  eo_line<K, true>(tb.EO[EO_DT][0], tb.EO[EO_DT][1], x, out);
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[base + i * stride] += out[i];
+}
+
 // start of the line along direction d through tangential indices (a, b)
 template <int K>
 __device__ __forceinline__ int line_base(int d, int a, int b) {
@@ -254,17 +328,27 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   // 2. basis change to the Gauss points, x then y then z; collocation derivatives
   const T* mS = kCompact ? sS : tb.S;
   const T* mD = kCompact ? sD : tb.D;
-  if (active) line_apply<K, false, kUq>(mS, Uc, K * (la + K * lb), 1);
+  // binary64 sweeps in even-odd form where that saves operations (k >= 5)
+  constexpr bool kEO = !kCompact && K >= 5;
+  auto sweep_S = [&](int base, int stride) {
+    if constexpr (kEO) eo_apply<K, EO_S>(tb, Uc, base, stride);
+    else line_apply<K, false, kUq>(mS, Uc, base, stride);
+  };
+  auto sweep_D = [&](int base, int stride, T* out) {
+    if constexpr (kEO) eo_derivative_to<K>(tb, Uc, base, stride, out, base, stride);
+    else line_apply_to<K, kUq>(mD, Uc, base, stride, out, base, stride);
+  };
+  if (active) sweep_S(K * (la + K * lb), 1);
   __syncthreads();
-  if (active) line_apply<K, false, kUq>(mS, Uc, la + K2 * lb, K);
+  if (active) sweep_S(la + K2 * lb, K);
   __syncthreads();
-  if (active) line_apply<K, false, kUq>(mS, Uc, la + K * lb, K2);
+  if (active) sweep_S(la + K * lb, K2);
   __syncthreads();
   if (OP == OP_SIPG) {
     if (active) {
-      line_apply_to<K, kUq>(mD, Uc, K * (la + K * lb), 1, G0, K * (la + K * lb), 1);
-      line_apply_to<K, kUq>(mD, Uc, la + K2 * lb, K, G1, la + K2 * lb, K);
-      line_apply_to<K, kUq>(mD, Uc, la + K * lb, K2, G2, la + K * lb, K2);
+      sweep_D(K * (la + K * lb), 1, G0);
+      sweep_D(la + K2 * lb, K, G1);
+      sweep_D(la + K * lb, K2, G2);
     }
     __syncthreads();
   }
@@ -594,18 +678,26 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   __syncthreads();
 
   // 5. integration: V += D^T T_x, D^T T_y, D^T T_z, then S^T along z, y, x
-  if (active) line_add_transposed<K, kUq>(mD, G0, Uc, K * (la + K * lb), 1);
+  auto sweep_DT = [&](const T* t, int base, int stride) {
+    if constexpr (kEO) eo_add_derivative_transposed<K>(tb, t, Uc, base, stride);
+    else line_add_transposed<K, kUq>(mD, t, Uc, base, stride);
+  };
+  auto sweep_ST = [&](int base, int stride) {
+    if constexpr (kEO) eo_apply<K, EO_ST>(tb, Uc, base, stride);
+    else line_apply<K, true, kUq>(mS, Uc, base, stride);
+  };
+  if (active) sweep_DT(G0, K * (la + K * lb), 1);
   __syncthreads();
-  if (active) line_add_transposed<K, kUq>(mD, G1, Uc, la + K2 * lb, K);
+  if (active) sweep_DT(G1, la + K2 * lb, K);
   __syncthreads();
   if (active) {
-    line_add_transposed<K, kUq>(mD, G2, Uc, la + K * lb, K2);
-    line_apply<K, true, kUq>(mS, Uc, la + K * lb, K2);
+    sweep_DT(G2, la + K * lb, K2);
+    sweep_ST(la + K * lb, K2);
   }
   __syncthreads();
-  if (active) line_apply<K, true, kUq>(mS, Uc, la + K2 * lb, K);
+  if (active) sweep_ST(la + K2 * lb, K);
   __syncthreads();
-  if (active) line_apply<K, true, kUq>(mS, Uc, K * (la + K * lb), 1);
+  if (active) sweep_ST(K * (la + K * lb), 1);
   __syncthreads();
 
   // write (set) the block's contiguous range; optional src . dst partial

@@ -14,6 +14,7 @@
 namespace dg {
 
 constexpr int kMaxK = 9;  // degree 8
+constexpr int kHalf = (kMaxK + 1) / 2;
 
 enum Geo { GEO_CART = 0, GEO_FULL = 2, GEO_MERGED = 3 };
 enum Op { OP_SIPG = 0, OP_ADV = 1 };
@@ -27,7 +28,17 @@ struct Tables {
   T E[2][kMaxK];        // E[s][j]   = l^G_j(s), Gauss-collocation value at xi = s
   T DF[2][kMaxK];       // DF[s][i]  = (l^GL_i)'(s), GL derivative at xi = s
   T W[kMaxK];           // Gauss weights on [0,1]
+  // Even-odd halves of S, S^T, D, D^T (index EO_S, EO_ST, EO_D, EO_DT) for
+  // the 1D kernels of Sec. 4.1: S is centrosymmetric (M[q][i] =
+  // M[k-1-q][k-1-i]) and D anti-centrosymmetric (M[q][i] = -M[k-1-q][k-1-i]),
+  // so with h = k/2, rows q < (k+1)/2 and e_i = u_i + u_{k-1-i},
+  // o_i = u_i - u_{k-1-i} (i < h; e_h = u_h for odd k):
+  //   ME[q][i] = (M[q][i] + M[q][k-1-i]) / 2 (i < h), ME[q][h] = M[q][h],
+  //   MO[q][i] = (M[q][i] - M[q][k-1-i]) / 2 (i < h),
+  // stored with row stride kHalf.
+  T EO[4][2][kHalf * kHalf];
 };
+enum { EO_S = 0, EO_ST = 1, EO_D = 2, EO_DT = 3 };
 
 // Device geometry and mesh description used by the apply kernel.
 template <typename T>
