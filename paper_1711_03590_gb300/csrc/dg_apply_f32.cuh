@@ -429,22 +429,14 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   const float wa = tb.W[a], wb = tb.W[b];
   float* FT = FB;  // [face direction x, y][side][component slot][K2][C]
   // trace and flux of face (d, s) at this thread's face point
-  auto own_flux = [&](auto dc, int s, const float(&lu)[K], const float(&lg)[3][K], float& tvv, float(&tgo)[3]) {
+  // numerical flux of face (d, s) at this thread's face point from the own
+  // traces uf (value) and gf (reference gradient; the components other than
+  // d are needed on non-Cartesian meshes only)
+  auto face_flux = [&](auto dc, int s, float uf, const float(&gf)[3], float& tvv, float(&tgo)[3]) {
     constexpr int d = decltype(dc)::value;
     const int t = 2 * d + s;
     const bool interior = NBC[t * C + lc] >= 0;
     const int fid = FID[t * C + lc];
-    float uf = 0.f, gf[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const float e = tb.E[s][j];
-      uf = fmaf(e, lu[j], uf);
-      if (SIPG) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (c == d || TANG) gf[c] = fmaf(e, lg[c][j], gf[c]);
-      }
-    }
     const float* slot = FA + (t * FSA + fpt) * C + lc;  // this thread's (u+, w+) of face t
     const float un = slot[0];
     tgo[0] = tgo[1] = tgo[2] = 0.f;
@@ -489,6 +481,22 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       tvv = interior ? 0.5f * cno * (uf + un) + 0.5f * fabsf(cno) * (uf - un) : fabsf(cno) * uf;
     }
   };
+  // the same from the fields along the owned d-line (extrapolation E_s)
+  auto own_flux = [&](auto dc, int s, const float(&lu)[K], const float(&lg)[3][K], float& tvv, float(&tgo)[3]) {
+    constexpr int d = decltype(dc)::value;
+    float uf = 0.f, gf[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float e = tb.E[s][j];
+      uf = fmaf(e, lu[j], uf);
+      if (SIPG) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c == d || TANG) gf[c] = fmaf(e, lg[c][j], gf[c]);
+      }
+    }
+    face_flux(dc, s, uf, gf, tvv, tgo);
+  };
   auto xy_faces = [&](auto dc) {
     constexpr int d = decltype(dc)::value;
     float lu[K], lg[3][K];
@@ -525,6 +533,77 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   // geometry loads overlap the x and y face work; the stores of tz0, tz1 into
   // G0, G1 (read by the x and y traces) follow the barrier.
   float tz0[K], tz1[K], tz2[K], tvz[2];
+  // cell-blocked geometry: array m, point q of cell c at
+  // ((c / CBL) NA + m) K3 + q) CBL + c mod CBL (padded to whole blocks, so
+  // the unclamped index of tail threads stays inside the allocation)
+  size_t gofs = 0;
+  if constexpr (!CART) gofs = ((size_t)(cell_raw / CBL) * NA * K3) * CBL + (cell_raw % CBL);
+  constexpr int MS = K3 * CBL;  // array stride
+  float kx = 1.f;
+  if (CART && SIPG && gm.kq) kx = gm.kq[i0 * K + a];
+  // q-point operation at (a, b, j) and the z faces' gradient-test injection
+  // (tgz: the z faces' coefficients, [component][side])
+  auto qpoint = [&](int j, float g0, float g1, float g2, float uq, const float(&tgz)[3][2], float& t0, float& t1,
+                    float& t2) {
+    const int q = a + K * b + K2 * j;
+    const float* cp = CART ? gm.cell : gm.cell + gofs + (size_t)q * CBL;
+    if (SIPG) {
+      if (CART) {
+        const float w = wa * wb * tb.W[j] * gm.cart_detj * kx;
+        t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+        t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+        t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+      } else if (GEO == GEO_FULL) {
+        float J[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) J[m] = cp[m * MS];
+        const float jw = cp[9 * MS];
+        // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
+        const float x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
+        const float x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
+        const float x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+        t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
+        t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
+        t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+      } else {
+        const float a00 = cp[0], a01 = cp[MS], a02 = cp[2 * MS], a11 = cp[3 * MS], a12 = cp[4 * MS],
+                    a22 = cp[5 * MS];
+        t0 = a00 * g0 + a01 * g1 + a02 * g2;
+        t1 = a01 * g0 + a11 * g1 + a12 * g2;
+        t2 = a02 * g0 + a12 * g1 + a22 * g2;
+      }
+      // z faces: gradient test along the line
+      const float e0 = tb.E[0][j], e1 = tb.E[1][j];
+      if (TANG) {
+        t0 = fmaf(e0, tgz[0][0], fmaf(e1, tgz[0][1], t0));
+        t1 = fmaf(e0, tgz[1][0], fmaf(e1, tgz[1][1], t1));
+      }
+      t2 = fmaf(e0, tgz[2][0], fmaf(e1, tgz[2][1], t2));
+    } else {
+      float b0, b1, b2;
+      if (CART) {
+        const float w = -wa * wb * tb.W[j] * gm.cart_detj;
+        b0 = w * gm.cart_jinv[0] * gm.vel[0];
+        b1 = w * gm.cart_jinv[1] * gm.vel[1];
+        b2 = w * gm.cart_jinv[2] * gm.vel[2];
+      } else if (GEO == GEO_FULL) {
+        float J[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) J[m] = cp[m * MS];
+        const float jw = -cp[9 * MS];
+        b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
+        b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
+        b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+      } else {
+        b0 = cp[0];
+        b1 = cp[MS];
+        b2 = cp[2 * MS];
+      }
+      t0 = b0 * uq;
+      t1 = b1 * uq;
+      t2 = b2 * uq;
+    }
+  };
   auto z_line = [&]() {
     float lu[K], lg[3][K];
 #pragma unroll
@@ -546,78 +625,10 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
       for (int c = 0; c < 3; ++c) tgz[c][s] = tgo[c];
     }
-    // cell-blocked geometry: array m, point q of cell c at
-    // ((c / CBL) NA + m) K3 + q) CBL + c mod CBL (padded to whole blocks,
-    // so the unclamped index of tail threads stays inside the allocation)
-    size_t gofs = 0;
-    if constexpr (!CART) gofs = ((size_t)(cell_raw / CBL) * NA * K3) * CBL + (cell_raw % CBL);
-    constexpr int MS = K3 * CBL;  // array stride
-    float kx = 1.f;
-    if (CART && SIPG && gm.kq) kx = gm.kq[i0 * K + a];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      const int q = a + K * b + K2 * j;
-      const float* cp = CART ? gm.cell : gm.cell + gofs + (size_t)q * CBL;
-      if (SIPG) {
-        const float g0 = lg[0][j], g1 = lg[1][j], g2 = lg[2][j];
-        if (CART) {
-          const float w = wa * wb * tb.W[j] * gm.cart_detj * kx;
-          tz0[j] = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
-          tz1[j] = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
-          tz2[j] = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
-        } else if (GEO == GEO_FULL) {
-          float J[9];
-#pragma unroll
-          for (int m = 0; m < 9; ++m) J[m] = cp[m * MS];
-          const float jw = cp[9 * MS];
-          // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
-          const float x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
-          const float x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
-          const float x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
-          tz0[j] = J[0] * x0 + J[1] * x1 + J[2] * x2;
-          tz1[j] = J[3] * x0 + J[4] * x1 + J[5] * x2;
-          tz2[j] = J[6] * x0 + J[7] * x1 + J[8] * x2;
-        } else {
-          const float a00 = cp[0], a01 = cp[MS], a02 = cp[2 * MS], a11 = cp[3 * MS], a12 = cp[4 * MS],
-                      a22 = cp[5 * MS];
-          tz0[j] = a00 * g0 + a01 * g1 + a02 * g2;
-          tz1[j] = a01 * g0 + a11 * g1 + a12 * g2;
-          tz2[j] = a02 * g0 + a12 * g1 + a22 * g2;
-        }
-        // z faces: gradient test along the line
-        const float e0 = tb.E[0][j], e1 = tb.E[1][j];
-        if (TANG) {
-          tz0[j] = fmaf(e0, tgz[0][0], fmaf(e1, tgz[0][1], tz0[j]));
-          tz1[j] = fmaf(e0, tgz[1][0], fmaf(e1, tgz[1][1], tz1[j]));
-        }
-        tz2[j] = fmaf(e0, tgz[2][0], fmaf(e1, tgz[2][1], tz2[j]));
-      } else {
-        const float uq = lu[j];
-        float b0, b1, b2;
-        if (CART) {
-          const float w = -wa * wb * tb.W[j] * gm.cart_detj;
-          b0 = w * gm.cart_jinv[0] * gm.vel[0];
-          b1 = w * gm.cart_jinv[1] * gm.vel[1];
-          b2 = w * gm.cart_jinv[2] * gm.vel[2];
-        } else if (GEO == GEO_FULL) {
-          float J[9];
-#pragma unroll
-          for (int m = 0; m < 9; ++m) J[m] = cp[m * MS];
-          const float jw = -cp[9 * MS];
-          b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
-          b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
-          b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
-        } else {
-          b0 = cp[0];
-          b1 = cp[MS];
-          b2 = cp[2 * MS];
-        }
-        tz0[j] = b0 * uq;
-        tz1[j] = b1 * uq;
-        tz2[j] = b2 * uq;
-      }
-      // long lines: bound the geometry loads in flight (register budget)
-      if (K >= 7 && !CART && j % 2 == 1) __syncwarp();
+      qpoint(j, SIPG ? lg[0][j] : 0.f, SIPG ? lg[1][j] : 0.f, SIPG ? lg[2][j] : 0.f, lu[j], tgz, tz0[j], tz1[j],
+             tz2[j]);
     }
   };
   if constexpr (EARLY) z_line();
@@ -626,9 +637,9 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   __syncthreads();
 
   // 6. z-line owner: the pulled z components of the x- and y-face gradient
-  // tests, then D_z^T
-  {
-    if constexpr (!EARLY) z_line();
+  // tests, then D_z^T.  Long lines (k >= 7) do the z-line work here, point
+  // by point through shared memory (register budget).
+  if constexpr (EARLY) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const int pidx = (a + XS * b + YS * j) * C + lc;
@@ -648,6 +659,65 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       float acc = fmaf(tb.E[0][i], tvz[0], tb.E[1][i] * tvz[1]);
 #pragma unroll
       for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], tz2[j], acc);
+      U[(a + XS * b + YS * i) * C + lc] = acc;
+    }
+  } else {
+    // z traces: extrapolate the fields along the line
+    float uf[2] = {0.f, 0.f}, gf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+      const int pidx = (a + XS * b + YS * j) * C + lc;
+      const float u = U[pidx];
+      float g[3] = {0.f, 0.f, 0.f};
+      if (SIPG) {
+        g[2] = G2[pidx];
+        if (TANG) {
+          g[0] = G0[pidx];
+          g[1] = G1[pidx];
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const float e = tb.E[s][j];
+        uf[s] = fmaf(e, u, uf[s]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gf[s][c] = fmaf(e, g[c], gf[s][c]);
+      }
+    }
+    float tgz[3][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      float tvv, tgo[3];
+      face_flux(std::integral_constant<int, 2>{}, s, uf[s], gf[s], tvv, tgo);
+      tvz[s] = tvv;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tgz[c][s] = tgo[c];
+    }
+    // q-point operation, injection and pulled components, point by point;
+    // the gradient-test fields go to G0..G2
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+      const int pidx = (a + XS * b + YS * j) * C + lc;
+      float t0, t1, t2;
+      qpoint(j, SIPG ? G0[pidx] : 0.f, SIPG ? G1[pidx] : 0.f, SIPG ? G2[pidx] : 0.f, U[pidx], tgz, t0, t1, t2);
+      if (TANG) {
+        t2 = fmaf(ea0, FT[(((0 * 2 + 0) * 2 + 1) * KK + b + KP * j) * C + lc], t2);
+        t2 = fmaf(ea1, FT[(((0 * 2 + 1) * 2 + 1) * KK + b + KP * j) * C + lc], t2);
+        t2 = fmaf(eb0, FT[(((1 * 2 + 0) * 2 + 1) * KK + a + KP * j) * C + lc], t2);
+        t2 = fmaf(eb1, FT[(((1 * 2 + 1) * 2 + 1) * KK + a + KP * j) * C + lc], t2);
+      }
+      G0[pidx] = t0;
+      G1[pidx] = t1;
+      G2[pidx] = t2;
+    }
+    float t2l[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) t2l[j] = G2[(a + XS * b + YS * j) * C + lc];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float acc = fmaf(tb.E[0][i], tvz[0], tb.E[1][i] * tvz[1]);
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t2l[j], acc);
       U[(a + XS * b + YS * i) * C + lc] = acc;
     }
   }
