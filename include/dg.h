@@ -169,8 +169,12 @@ dg_status dg_apply(dg_handle *h, const void *src, void *dst);
 
 /* The same operator with HOST buffers: copies src to the device, applies,
  * copies the result back, and waits for the stream.  Pinned host memory
- * makes the copies asynchronous DMA.  Device staging buffers are allocated
- * on the first call and kept by the handle. */
+ * makes the copies asynchronous DMA; on non-periodic meshes whose z-planes
+ * hold a multiple of 64 cells the work is pipelined over up to 8 slabs of
+ * z-planes (copies in, applies and copies out overlap; the result is the
+ * same bits as dg_apply).  Device staging buffers, two copy streams, a
+ * second compute stream and their events are created on the first call and
+ * kept by the handle. */
 dg_status dg_apply_host(dg_handle *h, const void *src_host, void *dst_host);
 
 /* rhs_i = (phi_i, f) for the manufactured solution u = sin(pi x) sin(pi y)

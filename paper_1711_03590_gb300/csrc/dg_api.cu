@@ -241,6 +241,9 @@ dg::Tables<T> cast_tables(int k, const Tables64& t) {
 // ---------------------------------------------------------------------------
 // Handle
 // ---------------------------------------------------------------------------
+// slabs of the pipelined host-buffer apply
+constexpr int kHostSlabs = 8;
+
 struct dg_handle {
   dg_mesh mesh;
   dg_opts opts;
@@ -271,8 +274,11 @@ struct dg_handle {
   cudaEvent_t cg_event;
   double* xw;             // extra work vectors (inner solution and right-hand side of
   double* bw;             // the mixed-precision solve), allocated on first use
-  // host-buffer apply staging
+  // host-buffer apply staging, and the copy streams and events of its slab
+  // pipeline (created on first use)
   void *stage_src, *stage_dst;
+  cudaStream_t h2d_stream, d2h_stream, cmp_stream;
+  cudaEvent_t pipe_ev[2 * kHostSlabs + 2];
   std::string err;
 };
 
@@ -821,7 +827,8 @@ int64_t apply_blocks(const dg_handle* h) {
   return (h->n_cells + C - 1) / C;
 }
 
-dg_status launch_apply(dg_handle* h, const void* src, void* dst, double* dot_partial) {
+dg_status launch_apply_range(dg_handle* h, const void* src, void* dst, double* dot_partial, int64_t cell_begin,
+                             int64_t cell_end, cudaStream_t stream) {
   dg::ApplyLaunch L;
   L.k = h->k;
   L.prec = h->prec;
@@ -836,8 +843,10 @@ dg_status launch_apply(dg_handle* h, const void* src, void* dst, double* dot_par
                : h->prec == DG_FP32 ? (const void*)&h->geof
                                     : (const void*)&h->geodf;
   L.dot_partial = dot_partial;
-  L.stream = h->stream;
+  L.stream = stream;
   L.cpb = h->cpb;
+  L.cell_begin = cell_begin;
+  L.cell_end = cell_end;
   cudaError_t e;
   switch (h->k) {
     case 2: e = dg::launch_apply_k2(L, h->n_cells); break;
@@ -852,6 +861,10 @@ dg_status launch_apply(dg_handle* h, const void* src, void* dst, double* dot_par
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "apply kernel launch");
   return DG_OK;
+}
+
+dg_status launch_apply(dg_handle* h, const void* src, void* dst, double* dot_partial) {
+  return launch_apply_range(h, src, dst, dot_partial, 0, h->n_cells, h->stream);
 }
 
 template <typename T>
@@ -1031,6 +1044,11 @@ void free_handle(dg_handle* h) {
   dev_free(h, h->xw);
   dev_free(h, h->bw);
   if (h->cg_stream) cudaStreamDestroy(h->cg_stream);
+  if (h->h2d_stream) cudaStreamDestroy(h->h2d_stream);
+  if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
+  if (h->cmp_stream) cudaStreamDestroy(h->cmp_stream);
+  for (auto e : h->pipe_ev)
+    if (e) cudaEventDestroy(e);
   if (h->cg_event) cudaEventDestroy(h->cg_event);
   delete h;
 }
@@ -1315,16 +1333,65 @@ dg_status dg_apply(dg_handle* h, const void* src, void* dst) {
   return launch_apply(h, src, dst, nullptr);
 }
 
+// dst = A src with host buffers, pipelined over slabs of whole z-planes of
+// cells (contiguous cell ranges): all host-to-device copies are queued on one
+// copy stream; slab s is applied (on the handle's stream and a second
+// compute stream, alternately) as soon as slab s+1 (its upper z-neighbours)
+// has arrived; its result is copied back on a second copy stream while later
+// slabs are computed.  Results are the same as one
+// dg_apply (every cell's arithmetic is independent of the launch range).
+// Periodic meshes in z (the first slab needs the last) and meshes whose
+// z-planes do not align with the kernels' cell blocks use a single slab.
 dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
   if (!h) return DG_ERR_ARG;
   if (!src_host || !dst_host) return fail(h, DG_ERR_ARG, "src or dst is NULL");
-  const size_t bytes = (size_t)h->n_dofs * (h->prec == DG_FP32 ? 4 : 8);
+  const size_t scal = h->prec == DG_FP32 ? 4 : 8;
+  const size_t bytes = (size_t)h->n_dofs * scal;
   dg_status st;
   if (!h->stage_src && (st = dev_alloc(h, &h->stage_src, bytes)) != DG_OK) return st;
   if (!h->stage_dst && (st = dev_alloc(h, &h->stage_dst, bytes)) != DG_OK) return st;
-  DG_CUDA(h, cudaMemcpyAsync(h->stage_src, src_host, bytes, cudaMemcpyHostToDevice, h->stream));
-  if ((st = launch_apply(h, h->stage_src, h->stage_dst, nullptr)) != DG_OK) return st;
-  DG_CUDA(h, cudaMemcpyAsync(dst_host, h->stage_dst, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (!h->h2d_stream) {
+    DG_CUDA(h, cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking));
+    DG_CUDA(h, cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
+    DG_CUDA(h, cudaStreamCreateWithFlags(&h->cmp_stream, cudaStreamNonBlocking));
+    for (auto& e : h->pipe_ev) DG_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const int64_t plane = (int64_t)h->mesh.n[0] * h->mesh.n[1];
+  const int nz = h->mesh.n[2];
+  int slabs = (!h->mesh.periodic && plane % 64 == 0 && nz >= 4) ? std::min(kHostSlabs, nz / 2) : 1;
+  const int64_t k3 = (int64_t)h->k * h->k * h->k;
+  auto cell_of_slab = [&](int s) { return plane * ((int64_t)nz * s / slabs); };
+  cudaEvent_t* ev_in = h->pipe_ev;              // slab s on the device
+  cudaEvent_t* ev_out = h->pipe_ev + kHostSlabs;  // slab s computed
+  cudaEvent_t ev_start = h->pipe_ev[2 * kHostSlabs], ev_cmp = h->pipe_ev[2 * kHostSlabs + 1];
+  // the copies follow earlier work on the handle's stream (staging reuse)
+  DG_CUDA(h, cudaEventRecord(ev_start, h->stream));
+  DG_CUDA(h, cudaStreamWaitEvent(h->h2d_stream, ev_start, 0));
+  DG_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, ev_start, 0));
+  DG_CUDA(h, cudaStreamWaitEvent(h->cmp_stream, ev_start, 0));
+  for (int s = 0; s < slabs; ++s) {
+    const int64_t c0 = cell_of_slab(s), c1 = cell_of_slab(s + 1);
+    const size_t off = (size_t)(c0 * k3) * scal, len = (size_t)((c1 - c0) * k3) * scal;
+    DG_CUDA(h, cudaMemcpyAsync(static_cast<char*>(h->stage_src) + off, static_cast<const char*>(src_host) + off, len,
+                               cudaMemcpyHostToDevice, h->h2d_stream));
+    DG_CUDA(h, cudaEventRecord(ev_in[s], h->h2d_stream));
+  }
+  for (int s = 0; s < slabs; ++s) {
+    const int64_t c0 = cell_of_slab(s), c1 = cell_of_slab(s + 1);
+    // slabs alternate between two compute streams so that one slab's last
+    // blocks overlap the next slab's first ones
+    cudaStream_t cs = (s % 2) ? h->cmp_stream : h->stream;
+    DG_CUDA(h, cudaStreamWaitEvent(cs, ev_in[std::min(s + 1, slabs - 1)], 0));
+    if ((st = launch_apply_range(h, h->stage_src, h->stage_dst, nullptr, c0, c1, cs)) != DG_OK) return st;
+    DG_CUDA(h, cudaEventRecord(ev_out[s], cs));
+    DG_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, ev_out[s], 0));
+    const size_t off = (size_t)(c0 * k3) * scal, len = (size_t)((c1 - c0) * k3) * scal;
+    DG_CUDA(h, cudaMemcpyAsync(static_cast<char*>(dst_host) + off, static_cast<const char*>(h->stage_dst) + off, len,
+                               cudaMemcpyDeviceToHost, h->d2h_stream));
+  }
+  DG_CUDA(h, cudaEventRecord(ev_cmp, h->cmp_stream));
+  DG_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cmp, 0));
+  DG_CUDA(h, cudaStreamSynchronize(h->d2h_stream));
   DG_CUDA(h, cudaStreamSynchronize(h->stream));
   return DG_OK;
 }

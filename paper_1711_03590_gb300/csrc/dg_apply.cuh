@@ -73,6 +73,7 @@ struct ApplyParams {
   typename Arith<T>::V* dst;
   double* dot_partial;
   int C;  // cells per block
+  int64_t cell_begin, cell_end;  // cells of this launch
 };
 
 template <int K>
@@ -255,10 +256,10 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   const int lc = tid / K2;
   const int ln = tid - lc * K2;
   const int la = ln % K, lb = ln / K;
-  const int64_t cell0 = (int64_t)blockIdx.x * C;
+  const int64_t cell0 = P.cell_begin + (int64_t)blockIdx.x * C;
   const int64_t cell = cell0 + lc;
-  const bool active = cell < gm.n_cells;
-  const int nloc = (int)min((int64_t)C, gm.n_cells - cell0);
+  const bool active = cell < P.cell_end;
+  const int nloc = (int)min((int64_t)C, P.cell_end - cell0);
   T* Uc = U + lc * K3;
   T* G0 = G + lc * K3;
   T* G1 = G + (C + lc) * K3;
@@ -737,6 +738,8 @@ cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
   P.dot_partial = L.dot_partial;
   const int C = (L.cpb >= 1 && L.cpb <= cells_per_block(K)) ? L.cpb : cells_per_block(K);
   P.C = C;
+  P.cell_begin = L.cell_begin;
+  P.cell_end = L.cell_end;
   const int smem = smem_bytes_per_block(K, OP, (int)sizeof(T), C);
   static bool configured = false;
   if (!configured) {
@@ -745,7 +748,8 @@ cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int64_t grid = (n_cells + C - 1) / C;
+  (void)n_cells;
+  const int64_t grid = (L.cell_end - L.cell_begin + C - 1) / C;
   if (grid <= 0) return cudaSuccess;
   apply_kernel<K, T, GEO, OP><<<(unsigned)grid, C * K * K, smem, L.stream>>>(P);
   return cudaGetLastError();

@@ -116,9 +116,11 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   const int a = ln % K, b = ln / K;
   const int fpt = a + f32_face_pitch(K) * b;  // face point (a, b) in the face buffers
   const int ncell = (int)gm.n_cells;
-  const int cell_raw = (int)blockIdx.x * C + lc;
-  const bool valid = cell_raw < ncell;
-  const int cell = valid ? cell_raw : ncell - 1;
+  const int cell0 = (int)P.cell_begin + (int)blockIdx.x * C;  // this block's first cell
+  const int cell_end = (int)P.cell_end;                         // end of this launch's cells
+  const int cell_raw = cell0 + lc;
+  const bool valid = cell_raw < cell_end;
+  const int cell = valid ? cell_raw : cell_end - 1;
   int i0, i1, i2;
   {
     const unsigned q = (unsigned)cell / (unsigned)gm.n[0];
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
   // memory with coalesced loads (cell-major, stride k^3); it occupies the
   // G1/G2 region until phase 4
   float* R = G1;
-  const int cfirst = (int)blockIdx.x * C - 1;
+  const int cfirst = cell0 - 1;
   {
     const int64_t base = (int64_t)cfirst * K3;
     constexpr int NR = (C + 2) * K3;
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     constexpr unsigned BYTES = NA * K3 * CBL * 4, NPF = 8;
     constexpr unsigned CH = (BYTES / NPF + 15) / 16 * 16;
     if (tid < (int)NPF) {
-      const char* g = reinterpret_cast<const char*>(gm.cell + ((size_t)(blockIdx.x * C / CBL) * NA * K3) * CBL);
+      const char* g = reinterpret_cast<const char*>(gm.cell + ((size_t)(cell0 / CBL) * NA * K3) * CBL);
       const unsigned off = tid * CH;
       if (off < BYTES) {
         const unsigned sz = BYTES - off < CH ? BYTES - off : CH;
@@ -857,6 +859,8 @@ cudaError_t launch_f32_one(const ApplyLaunch& L, int64_t n_cells) {
   P.dst = static_cast<float*>(L.dst);
   P.dot_partial = L.dot_partial;
   P.C = C;
+  P.cell_begin = L.cell_begin;
+  P.cell_end = L.cell_end;
   const int smem = f32_smem_bytes(K, OP, C);
   static bool configured = false;
   if (!configured) {
@@ -871,7 +875,8 @@ cudaError_t launch_f32_one(const ApplyLaunch& L, int64_t n_cells) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int64_t grid = (n_cells + C - 1) / C;
+  (void)n_cells;
+  const int64_t grid = (L.cell_end - L.cell_begin + C - 1) / C;
   if (grid <= 0) return cudaSuccess;
   apply_f32_kernel<K, C, GEO, OP><<<(unsigned)grid, C * K * K, smem, L.stream>>>(P);
   return cudaGetLastError();

@@ -83,6 +83,8 @@ struct ApplyLaunch {
   double* dot_partial;   // optional: per-block partial of src . dst (FP64)
   cudaStream_t stream;
   int cpb;               // cells per block (1 .. cells_per_block(k))
+  int64_t cell_begin;    // the launch covers cells cell_begin .. cell_end - 1 (neighbours anywhere);
+  int64_t cell_end;      // binary32: cell_begin a multiple of f32_geometry_block(k)
 };
 
 // Largest number of cells per block of the apply kernel for k points per
