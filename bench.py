@@ -333,10 +333,11 @@ def serve_requests(dgp, count, seed, dof_lo=1e4, dof_hi=2e7, rtol=1e-8):
     return reqs
 
 
-def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rates=(0.5, 0.9)):
+def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rates=(0.5, 0.9), progress=None):
     """Continuous-batching solve server under Poisson arrivals: first all
     requests at once (capacity in solves/s), then Poisson arrivals at given
-    fractions of that capacity; p50/p99 latency (submit to done) per rate."""
+    fractions of that capacity; p50/p99 latency (submit to done) per rate.
+    progress: optional callable given the partial result after each run."""
     budget = int(budget_gb * (1 << 30))
     reqs = serve_requests(dgp, count, seed, dof_hi=dof_hi)
     out = {"requests": count, "slots": slots, "budget_gb": budget_gb,
@@ -348,7 +349,10 @@ def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rat
     span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
     cap = count / span
     out["saturated"] = {"solves_per_s": cap, "seconds": span,
-                        "all_converged": all(r["status"] == 0 and r["rel_res"] <= 1e-8 for r in res)}
+                        "all_converged": all(r["status"] == 0 and r["rel_res"] <= 1e-8 for r in res),
+                        "p50_latency_ms": 1e3 * float(np.percentile([r["t_done"] - r["t_submit"] for r in res], 50))}
+    if progress:
+        progress(out)
     rng = np.random.default_rng(seed + 1)
     for frac in rates:
         lam = frac * cap
@@ -361,6 +365,8 @@ def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rat
             "arrival_rate_per_s": lam, "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
             "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)), "solves_per_s": count / span,
             "all_converged": all(r["status"] == 0 and r["rel_res"] <= 1e-8 for r in res)}
+        if progress:
+            progress(out)
     return out
 
 
@@ -512,6 +518,8 @@ def main():
                     help="only run the full-size mixed-precision solves and print their JSON")
     ap.add_argument("--degree-sweep", action="store_true",
                     help="only run the apply degree sweep (32^3 and the paper's size schedule) and print its JSON")
+    ap.add_argument("--serve-config5", action="store_true",
+                    help="only run the full serving stream (2000 requests, 1e4..2e7 dofs, swept arrival rates)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -532,6 +540,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
+    if args.serve_config5:
+        # the full stream: 2000 requests, 1e4..2e7 dofs (mean about 2.7e6),
+        # saturated and at 90% of that capacity; each run prints when done
+        if rank == 0:
+            serve_metrics(dgp, count=2000, seed=11, dof_hi=2e7, rates=(0.9,),
+                          progress=lambda r: print(json.dumps({"serve_config5": r}), flush=True))
+        return
     if args.degree_sweep:
         if rank == 0:
             print(json.dumps({"degree_sweep": degree_sweep_metrics(torch, dgp)}), flush=True)
