@@ -14,7 +14,11 @@
 //  * Shared memory is cell-minor: the value at point p of cell c sits at
 //    p C + c and thread t works on cell t mod C, so the 32 lanes of a warp
 //    address 32/C consecutive line positions of C cells; rows are padded to
-//    an odd length so that no line direction has bank conflicts.
+//    an odd length so that no line direction has bank conflicts, and the face
+//    buffers are padded per face for the in-face line tasks.
+//  * The block's source cells and their x-neighbours are staged with
+//    coalesced loads; the y/z neighbours' lines through the thread's face
+//    points are loaded before the first barrier.
 //  * The 1D sweeps keep their line in registers (k loads, k^2 FMAs, k
 //    stores); the z-line owner computes the z-derivative from registers.
 //  * The in-face sum factorization of the neighbours' traces (Eq.
@@ -27,16 +31,20 @@
 //    traffic for faces is the tangential gradient-test components pulled
 //    across directions.
 //  * Cell geometry is stored in a cell-blocked layout [block][array][point]
-//    [cell in block] so that its loads are whole 128-byte lines; boundary
-//    and tail handling are selects on clamped indices (no divergent
-//    branches).
+//    [cell in block] and face geometry in blocks of 8 faces, so that their
+//    loads are whole sectors; bulk L2 prefetches of both start after the
+//    first barrier.  Boundary and tail handling are selects on clamped
+//    indices (no divergent branches).
 //
-// Phases (barrier-separated): gather + S_z, neighbour face data | S_y, first
-// in-face sweep | S_x, D_x, second in-face sweep with the neighbour's normal
-// flux | D_y, D_z | own face traces (extrapolation of the Gauss-point fields,
-// E_s) and numerical fluxes (Eq. poisson_sip / advection) | z: q-point
-// operation (Sec. 5 geometry variants), z-face injection, D_z^T | y: D_y^T |
-// x: D_x^T, S_x^T | y: S_y^T | z: S_z^T and the store (set) of dst.
+// Phases (barrier-separated): staging, face tables | neighbour face data,
+// S_z | S_y, first in-face sweep | S_x, D_x, second in-face sweep with the
+// neighbour's normal flux | D_y, D_z | own x/y face traces (extrapolation of
+// the Gauss-point fields, E_s) and numerical fluxes (Eq. poisson_sip /
+// advection), and for k <= 6 the z-line's traces, fluxes and q-point
+// operation (Sec. 5 geometry variants) | z: (k >= 7: the same, point by
+// point) z-face injection, pulled components, D_z^T | y: D_y^T | x: D_x^T,
+// S_x^T | y: S_y^T | z: S_z^T and the store (set) of dst.  A launch covers a
+// range of cells (the whole mesh, or a slab of the pipelined host apply).
 #pragma once
 
 #include <cstdint>
