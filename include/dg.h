@@ -119,6 +119,7 @@ typedef struct {
   int shared_bytes_per_block;
   int64_t blocks;               /* blocks of one apply launch */
   int tile_choices[24];         /* valid cells_per_block values, ascending, 0-terminated */
+  int face_mode;                /* DG_FACE_ELEMENT or DG_FACE_LOOP (dg_set_face_mode) */
 } dg_info_t;
 
 /* Build an operator: 1D tables, geometry arrays and work buffers on the
@@ -152,6 +153,20 @@ dg_status dg_set_stream(dg_handle *h, void *stream);
  * Results do not depend on it (each cell's arithmetic is the same); an
  * invalid value returns DG_ERR_ARG.  Synchronous. */
 dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
+
+/* Face evaluation of the DG_FP64 apply.  DG_FACE_ELEMENT (default): one
+ * fused kernel, every cell evaluates its six faces (each interior face twice,
+ * the neighbour's traces re-interpolated from its dofs).  DG_FACE_LOOP: three
+ * launches -- cells write their own face traces and q-point fields, one
+ * kernel per face direction evaluates each face once for both sides (the
+ * paper's face loop, Algorithm 1 steps (iii)-(iv), here without atomics),
+ * cells inject and integrate -- trading memory traffic for FP64 arithmetic.
+ * Same results up to rounding.  DG_FACE_LOOP allocates its work arrays
+ * (about 28 + 24 doubles per dof at p = 4) here; it covers whole meshes only,
+ * so dg_apply_host does not pipeline it.  Other precisions: DG_ERR_UNSUPPORTED.
+ * Synchronous. */
+typedef enum { DG_FACE_ELEMENT = 0, DG_FACE_LOOP = 1 } dg_face_mode;
+dg_status dg_set_face_mode(dg_handle *h, int mode);
 
 /* Autotuner: times the apply for every value in tile_choices on
  * the handle's stream (CUDA events, warm-up first) and keeps the fastest.

@@ -36,6 +36,8 @@ DG_GEOM_CARTESIAN = 0
 DG_GEOM_AFFINE = 1
 DG_GEOM_FULL_JAC = 2
 DG_GEOM_MERGED = 3
+DG_FACE_ELEMENT = 0
+DG_FACE_LOOP = 1
 DG_FP64 = 0
 DG_FP32 = 1
 DG_FP64_EMU = 2
@@ -49,7 +51,7 @@ EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg
             "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
             "dg_set_cells_per_block", "dg_autotune", "dg_batch_create", "dg_batch_launch", "dg_batch_destroy",
             "dg_batch_last_error", "dg_request_device_bytes", "dg_server_create", "dg_server_submit",
-            "dg_server_wait", "dg_server_destroy", "dg_server_last_error", "dg_l2_error"]
+            "dg_server_wait", "dg_server_destroy", "dg_server_last_error", "dg_l2_error", "dg_set_face_mode"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -78,7 +80,7 @@ class dg_info_t(ctypes.Structure):
                 ("cell_geometry_bytes", ctypes.c_int64), ("face_geometry_bytes", ctypes.c_int64),
                 ("cells_per_block", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("shared_bytes_per_block", ctypes.c_int), ("blocks", ctypes.c_int64),
-                ("tile_choices", ctypes.c_int * 24)]
+                ("tile_choices", ctypes.c_int * 24), ("face_mode", ctypes.c_int)]
 
 
 class dg_request(ctypes.Structure):
@@ -121,6 +123,7 @@ def load_library(path=None):
                               ctypes.POINTER(ctypes.c_double)]
     L.dg_apply_dot_noalloc.argtypes = [_vp, _vp, _vp, _vp]
     L.dg_set_cells_per_block.argtypes = [_vp, ctypes.c_int]
+    L.dg_set_face_mode.argtypes = [_vp, ctypes.c_int]
     L.dg_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
     L.dg_batch_launch.argtypes = [_vp]
@@ -247,6 +250,10 @@ def dg_cg_solve_mixed(h64, h32, rhs_ptr, x_ptr, rtol, max_outer=50, inner_rtol=1
 
 def dg_set_cells_per_block(handle, cells_per_block):
     _check(load_library().dg_set_cells_per_block(_vp(handle), int(cells_per_block)), handle)
+
+
+def dg_set_face_mode(handle, mode):
+    _check(load_library().dg_set_face_mode(_vp(handle), int(mode)), handle)
 
 
 def dg_autotune(handle):
@@ -433,6 +440,10 @@ class Operator:
 
     def set_cells_per_block(self, cpb):
         dg_set_cells_per_block(self.handle, cpb)
+
+    def set_face_mode(self, mode):
+        """"element" (fused kernel, default) or "loop" (each face once; FP64)."""
+        dg_set_face_mode(self.handle, {"element": DG_FACE_ELEMENT, "loop": DG_FACE_LOOP}.get(mode, mode))
 
     def autotune(self):
         return dg_autotune(self.handle)

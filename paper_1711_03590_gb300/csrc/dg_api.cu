@@ -277,6 +277,9 @@ struct dg_handle {
   // host-buffer apply staging, and the copy streams and events of its slab
   // pipeline (created on first use)
   void *stage_src, *stage_dst;
+  // face-loop variant of the binary64 apply (dg_set_face_mode)
+  int face_mode;
+  dg::SplitArrays split;
   cudaStream_t h2d_stream, d2h_stream, cmp_stream;
   cudaEvent_t pipe_ev[2 * kHostSlabs + 2];
   std::string err;
@@ -847,6 +850,10 @@ dg_status launch_apply_range(dg_handle* h, const void* src, void* dst, double* d
   L.cpb = h->cpb;
   L.cell_begin = cell_begin;
   L.cell_end = cell_end;
+  L.face_mode = h->face_mode;
+  L.split = &h->split;
+  if (h->face_mode == 1 && (cell_begin != 0 || cell_end != h->n_cells))
+    return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply covers the whole mesh");
   cudaError_t e;
   switch (h->k) {
     case 2: e = dg::launch_apply_k2(L, h->n_cells); break;
@@ -1043,6 +1050,11 @@ void free_handle(dg_handle* h) {
   dev_free(h, h->stage_dst);
   dev_free(h, h->xw);
   dev_free(h, h->bw);
+  for (int d = 0; d < 3; ++d) {
+    dev_free(h, h->split.tr[d]);
+    dev_free(h, h->split.ft[d]);
+  }
+  dev_free(h, h->split.tq);
   if (h->cg_stream) cudaStreamDestroy(h->cg_stream);
   if (h->h2d_stream) cudaStreamDestroy(h->h2d_stream);
   if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
@@ -1312,6 +1324,7 @@ dg_status dg_info(const dg_handle* h, dg_info_t* info) {
   info->blocks = apply_blocks(h);
   const std::vector<int> tc = tile_choices(h);
   for (int i = 0; i < 24; ++i) info->tile_choices[i] = i < (int)tc.size() ? tc[i] : 0;
+  info->face_mode = h->face_mode;
   return DG_OK;
 }
 
@@ -1358,7 +1371,8 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
   }
   const int64_t plane = (int64_t)h->mesh.n[0] * h->mesh.n[1];
   const int nz = h->mesh.n[2];
-  int slabs = (!h->mesh.periodic && plane % 64 == 0 && nz >= 4) ? std::min(kHostSlabs, nz / 2) : 1;
+  int slabs =
+      (!h->mesh.periodic && h->face_mode == 0 && plane % 64 == 0 && nz >= 4) ? std::min(kHostSlabs, nz / 2) : 1;
   const int64_t k3 = (int64_t)h->k * h->k * h->k;
   auto cell_of_slab = [&](int s) { return plane * ((int64_t)nz * s / slabs); };
   cudaEvent_t* ev_in = h->pipe_ev;              // slab s on the device
@@ -1540,6 +1554,31 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
   if (inner_iters) *inner_iters = inner_total;
   if (final_rel_res) *final_rel_res = rel;
   return st;
+}
+
+dg_status dg_set_face_mode(dg_handle* h, int mode) {
+  if (!h) return DG_ERR_ARG;
+  if (mode != DG_FACE_ELEMENT && mode != DG_FACE_LOOP) return fail(h, DG_ERR_ARG, "unknown face mode");
+  if (mode == DG_FACE_LOOP && h->prec != DG_FP64)
+    return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply is implemented for DG_FP64");
+  if (mode == DG_FACE_LOOP && !h->split.tq) {
+    // traces and test coefficients per face and slot, gradient-test fields per point
+    const int k2 = h->k * h->k;
+    const int nf = h->op == DG_OP_SIPG ? 4 : 1;
+    dg_status st;
+    for (int d = 0; d < 3; ++d) {
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const int64_t faces = (int64_t)(h->mesh.periodic ? h->mesh.n[d] : h->mesh.n[d] + 1) * h->mesh.n[t1] *
+                            h->mesh.n[t2];
+      const size_t bytes = sizeof(double) * faces * 2 * nf * k2;
+      if ((st = dev_alloc(h, (void**)&h->split.tr[d], bytes)) != DG_OK) return st;
+      if ((st = dev_alloc(h, (void**)&h->split.ft[d], bytes)) != DG_OK) return st;
+    }
+    if ((st = dev_alloc(h, (void**)&h->split.tq, sizeof(double) * 3 * h->n_dofs)) != DG_OK) return st;
+    DG_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  h->face_mode = mode;
+  return DG_OK;
 }
 
 dg_status dg_set_cells_per_block(dg_handle* h, int cpb) {

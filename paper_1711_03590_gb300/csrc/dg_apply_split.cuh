@@ -1,0 +1,503 @@
+// Face-loop variant of the binary64 apply: every face is evaluated once.
+//
+// The fused kernel (dg_apply.cuh) is element-centric: each cell evaluates
+// its six faces, so every interior face is computed twice, and the
+// neighbour's traces are re-interpolated from its Gauss-Lobatto dofs (S_f,
+// D_f and the in-face sweeps of Eq. face_integral).  On GB300 the binary64
+// apply is bound by the FP64 pipe (1/64 of the binary32 rate) while HBM is
+// nearly idle, so this variant trades memory traffic for arithmetic, in the
+// spirit of the paper's face loop with a two-sided write (Algorithm 1 steps
+// (iii)-(iv) over faces), without atomics:
+//
+//   1. cell kernel: gather, S (x) S (x) S and D^co sweeps; the cell's own
+//      traces on its six faces (u and the reference gradient, by the
+//      Gauss-collocation extrapolation E_s) are written per face and slot;
+//      the q-point operation (Sec. 5 geometry) writes the gradient-test
+//      fields at the Gauss points;
+//   2. face kernel (one launch per direction): per face point, both slots'
+//      traces and the face geometry give the numerical flux once (Eq.
+//      poisson_sip / advection) and the test coefficients of both sides
+//      (value and reference gradient, Algorithm 1 step (iii)(c)) are written
+//      per face and slot;
+//   3. cell kernel: the gradient-test fields and the six faces' test
+//      coefficients of this cell's slot are injected (transpose of E_s) and
+//      integrated (D^co^T, S^T (x) S^T (x) S^T); dst is set.
+//
+// Work arrays (per operator, allocated when the mode is selected): traces
+// and test coefficients [face][slot][field][k^2] per direction, and three
+// gradient-test fields [field][cell][k^3].  The results equal the fused
+// kernel's up to rounding (same method, other operation order).
+#pragma once
+
+#include <cstdint>
+
+namespace dg {
+
+template <int OP>
+struct SplitFields {
+  static constexpr int NTR = OP == OP_SIPG ? 4 : 1;  // u (+ reference gradient)
+  static constexpr int NFT = OP == OP_SIPG ? 4 : 1;  // value test (+ gradient test)
+};
+
+// Face id (pos + P_d (i_t1 + n_t1 i_t2)) of side s (0: lower face, 1: upper
+// face) of cell ijk in direction d.
+__device__ __forceinline__ int split_face_id(const int ijk[3], int d, int s, const int n[3], const int P[3],
+                                             int periodic) {
+  const int id = d == 0 ? ijk[0] : d == 1 ? ijk[1] : ijk[2];
+  const int it1 = d == 0 ? ijk[1] : ijk[0], it2 = d == 2 ? ijk[1] : ijk[2];
+  const int nd = d == 0 ? n[0] : d == 1 ? n[1] : n[2];
+  const int nt1 = d == 0 ? n[1] : n[0];
+  const int Pd = d == 0 ? P[0] : d == 1 ? P[1] : P[2];
+  int pos = id + s;
+  if (periodic && pos == nd) pos = 0;
+  return pos + Pd * (it1 + nt1 * it2);
+}
+
+// Step 1: sweeps, own traces, q-point operation.
+template <int K, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads)
+    split_cell_forward(const __grid_constant__ ApplyParams<double> P, const __grid_constant__ SplitArrays SA) {
+  using T = double;
+  constexpr int K2 = K * K, K3 = K2 * K;
+  constexpr int NTR = SplitFields<OP>::NTR;
+  constexpr bool kEO = K >= 5;
+  const int C = P.C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3]
+  T* G = U + C * K3;                      // [3][C][K3]
+  const Tables<T>& tb = P.tab;
+  const Geometry<T>& gm = P.geo;
+  const int tid = threadIdx.x;
+  const int lc = tid / K2;
+  const int ln = tid - lc * K2;
+  const int la = ln % K, lb = ln / K;
+  const int64_t cell0 = P.cell_begin + (int64_t)blockIdx.x * C;
+  const int64_t cell = cell0 + lc;
+  const bool active = cell < P.cell_end;
+  const int nloc = (int)min((int64_t)C, P.cell_end - cell0);
+  T* Uc = U + lc * K3;
+  T* G0 = G + lc * K3;
+  T* G1 = G + (C + lc) * K3;
+  T* G2 = G + (2 * C + lc) * K3;
+  int ijk[3];
+  {
+    const unsigned c = (unsigned)(active ? cell : cell0);
+    const unsigned q = c / (unsigned)gm.n[0];
+    ijk[0] = (int)(c - q * (unsigned)gm.n[0]);
+    ijk[1] = (int)(q % (unsigned)gm.n[1]);
+    ijk[2] = (int)(q / (unsigned)gm.n[1]);
+  }
+  for (int i = tid; i < nloc * K3; i += blockDim.x) U[i] = P.src[cell0 * K3 + i];
+  __syncthreads();
+  auto sweep_S = [&](int base, int stride) {
+    if constexpr (kEO) eo_apply<K, EO_S>(tb, Uc, base, stride);
+    else line_apply<K, false, K>(tb.S, Uc, base, stride);
+  };
+  auto sweep_D = [&](int base, int stride, T* out) {
+    if constexpr (kEO) eo_derivative_to<K>(tb, Uc, base, stride, out, base, stride);
+    else line_apply_to<K, K>(tb.D, Uc, base, stride, out, base, stride);
+  };
+  if (active) sweep_S(K * (la + K * lb), 1);
+  __syncthreads();
+  if (active) sweep_S(la + K2 * lb, K);
+  __syncthreads();
+  if (active) sweep_S(la + K * lb, K2);
+  __syncthreads();
+  if (OP == OP_SIPG) {
+    if (active) {
+      sweep_D(K * (la + K * lb), 1, G0);
+      sweep_D(la + K2 * lb, K, G1);
+      sweep_D(la + K * lb, K2, G2);
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+
+  // own traces on the six faces: this cell is slot 1 of its lower face
+  // (s = 0) and slot 0 of its upper face (s = 1)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int base = line_base<K>(d, la, lb);
+    const int strd = d == 0 ? 1 : d == 1 ? K : K2;
+    T lu[K], lg[3][K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      lu[j] = Uc[base + j * strd];
+      if (OP == OP_SIPG) {
+        lg[0][j] = G0[base + j * strd];
+        lg[1][j] = G1[base + j * strd];
+        lg[2][j] = G2[base + j * strd];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      T v[NTR];
+#pragma unroll
+      for (int f = 0; f < NTR; ++f) v[f] = T(0);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const T e = tb.E[s][j];
+        v[0] = fma(e, lu[j], v[0]);
+        if (OP == OP_SIPG) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[1 + c] = fma(e, lg[c][j], v[1 + c]);
+        }
+      }
+      const int fid = split_face_id(ijk, d, s, gm.n, gm.P, gm.periodic);
+      T* out = SA.tr[d] + ((int64_t)(fid * 2 + (1 - s)) * NTR) * K2 + ln;
+#pragma unroll
+      for (int f = 0; f < NTR; ++f) out[f * K2] = v[f];
+    }
+  }
+
+  // q-point operation: the gradient-test fields t_c at the Gauss points
+  const T wa = tb.W[la], wb = tb.W[lb];
+#pragma unroll
+  for (int z = 0; z < K; ++z) {
+    const int pt = la + K * (lb + K * z);
+    const int64_t qi = cell * K3 + pt;
+    T t0, t1, t2;
+    if (OP == OP_SIPG) {
+      const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
+      if (GEO == GEO_CART) {
+        T w = wa * wb * tb.W[z] * gm.cart_detj;
+        if (gm.kq) w *= gm.kq[ijk[0] * K + la];
+        t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
+        t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
+        t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
+      } else if (GEO == GEO_FULL) {
+        const T* cp = gm.cell + qi;
+        const int64_t n = gm.ncq;
+        T J[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+        const T jw = cp[9 * n];
+        // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
+        const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
+        const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
+        const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+        t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
+        t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
+        t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+      } else {
+        const T* cp = gm.cell + qi;
+        const int64_t n = gm.ncq;
+        const T a00 = cp[0], a01 = cp[n], a02 = cp[2 * n], a11 = cp[3 * n], a12 = cp[4 * n], a22 = cp[5 * n];
+        t0 = a00 * g0 + a01 * g1 + a02 * g2;
+        t1 = a01 * g0 + a11 * g1 + a12 * g2;
+        t2 = a02 * g0 + a12 * g1 + a22 * g2;
+      }
+    } else {
+      const T uq = Uc[pt];
+      T b0, b1, b2;
+      if (GEO == GEO_CART) {
+        const T w = -wa * wb * tb.W[z] * gm.cart_detj;
+        b0 = w * gm.cart_jinv[0] * gm.vel[0];
+        b1 = w * gm.cart_jinv[1] * gm.vel[1];
+        b2 = w * gm.cart_jinv[2] * gm.vel[2];
+      } else if (GEO == GEO_FULL) {
+        const T* cp = gm.cell + qi;
+        const int64_t n = gm.ncq;
+        T J[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
+        const T jw = -cp[9 * n];
+        b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
+        b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
+        b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+      } else {
+        const T* cp = gm.cell + qi;
+        const int64_t n = gm.ncq;
+        b0 = cp[0];
+        b1 = cp[n];
+        b2 = cp[2 * n];
+      }
+      t0 = b0 * uq;
+      t1 = b1 * uq;
+      t2 = b2 * uq;
+    }
+    SA.tq[qi] = t0;
+    SA.tq[gm.ncq + qi] = t1;
+    SA.tq[2 * gm.ncq + qi] = t2;
+  }
+}
+
+// Step 2: one flux evaluation per face point of direction D, for both slots.
+// K^2 threads per face, FB faces per block.
+template <int K, int GEO, int OP, int D>
+__global__ void __launch_bounds__(Shape<K>::max_threads)
+    split_face(const __grid_constant__ ApplyParams<double> P, const __grid_constant__ SplitArrays SA, int FB) {
+  using T = double;
+  constexpr int K2 = K * K;
+  constexpr int NTR = SplitFields<OP>::NTR, NFT = SplitFields<OP>::NFT;
+  constexpr int t1d = D == 0 ? 1 : 0, t2d = D == 2 ? 1 : 2;
+  const Tables<T>& tb = P.tab;
+  const Geometry<T>& gm = P.geo;
+  const int lf = threadIdx.x / K2, fp = threadIdx.x - lf * K2;
+  const int la = fp % K, lb = fp / K;
+  const int nd = gm.n[D], nt1 = gm.n[t1d], nt2 = gm.n[t2d];
+  const int Pd = gm.P[D];
+  const int64_t nfaces = (int64_t)Pd * nt1 * nt2;
+  const int64_t fid = (int64_t)blockIdx.x * FB + lf;
+  if (lf >= FB || fid >= nfaces) return;  // no barrier in this kernel
+  const int pos = (int)(fid % Pd);
+  const int64_t r = fid / Pd;
+  const int it1 = (int)(r % nt1);
+  const bool has[2] = {gm.periodic || pos >= 1, gm.periodic || pos < nd};
+  // both slots' traces: u and the reference gradient of each side's cell
+  T u[2] = {T(0), T(0)}, g[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+    if (!has[sl]) continue;
+    const T* tr = SA.tr[D] + (fid * 2 + sl) * NTR * K2 + fp;
+    u[sl] = tr[0];
+    if (OP == OP_SIPG) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[sl][c] = tr[(1 + c) * K2];
+    }
+  }
+  const T cjd = gm.cart_jinv[D];
+#pragma unroll
+  for (int so = 0; so < 2; ++so) {
+    if (!has[so]) continue;
+    const int sn = 1 - so;
+    const bool interior = has[sn];
+    T* ft = SA.ft[D] + (fid * 2 + so) * NFT * K2 + fp;
+    if (OP == OP_SIPG) {
+      // j_n per slot (each side's own outward normal: +d for slot 0)
+      T jo[3], jn[3], fjxw, tau;
+      if (GEO == GEO_CART) {
+        const T j = so == 0 ? cjd : -cjd;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          jo[c] = c == D ? j : T(0);
+          jn[c] = -jo[c];
+        }
+        T kap = T(1);
+        if (gm.kq) kap = D == 0 ? gm.kf[pos] : gm.kq[it1 * K + la];
+        fjxw = kap * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
+        tau = gm.cart_tau[D];
+      } else {
+        const T* f = gm.face[D] + fid * K2 + fp;
+        const int64_t nfq = gm.nfq[D];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          jo[c] = f[(so * 3 + c) * nfq];
+          jn[c] = f[(sn * 3 + c) * nfq];
+        }
+        fjxw = f[6 * nfq];
+        tau = gm.tau[D][fid];
+      }
+      const T dno = jo[0] * g[so][0] + jo[1] * g[so][1] + jo[2] * g[so][2];
+      T tv, tg;
+      if (interior) {
+        // the neighbour's derivative along this side's outward normal
+        const T dnn = -(jn[0] * g[sn][0] + jn[1] * g[sn][1] + jn[2] * g[sn][2]);
+        const T jump = u[so] - u[sn];
+        tv = fjxw * (tau * jump - T(0.5) * (dno + dnn));
+        tg = T(-0.5) * fjxw * jump;
+      } else {
+        tv = fjxw * (T(2) * tau * u[so] - dno);
+        tg = -fjxw * u[so];
+      }
+      ft[0] = tv;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ft[(1 + c) * K2] = tg * jo[c];
+    } else {
+      T cn;
+      if (GEO == GEO_CART) cn = gm.vel[D] * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
+      else cn = gm.face[D][fid * K2 + fp];
+      const T cno = so == 0 ? cn : -cn;  // c.n da w with n this side's outward normal
+      ft[0] = interior ? T(0.5) * cno * (u[so] + u[sn]) + T(0.5) * fabs(cno) * (u[so] - u[sn])
+                       : fabs(cno) * u[so];
+    }
+  }
+}
+
+// Step 3: injection of the face test coefficients, integration, dst.
+template <int K, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads)
+    split_cell_backward(const __grid_constant__ ApplyParams<double> P, const __grid_constant__ SplitArrays SA) {
+  using T = double;
+  constexpr int K2 = K * K, K3 = K2 * K;
+  constexpr int NFT = SplitFields<OP>::NFT;
+  constexpr bool kEO = K >= 5;
+  const int C = P.C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3]
+  T* G = U + C * K3;                      // [3][C][K3]
+  T* FT = G + 3 * C * K3;                 // [C][3][2][NFT][K2]
+  const Tables<T>& tb = P.tab;
+  const Geometry<T>& gm = P.geo;
+  const int tid = threadIdx.x;
+  const int lc = tid / K2;
+  const int ln = tid - lc * K2;
+  const int la = ln % K, lb = ln / K;
+  const int64_t cell0 = P.cell_begin + (int64_t)blockIdx.x * C;
+  const int64_t cell = cell0 + lc;
+  const bool active = cell < P.cell_end;
+  const int nloc = (int)min((int64_t)C, P.cell_end - cell0);
+  T* Uc = U + lc * K3;
+  T* G0 = G + lc * K3;
+  T* G1 = G + (C + lc) * K3;
+  T* G2 = G + (2 * C + lc) * K3;
+  for (int i = tid; i < nloc * K3; i += blockDim.x) {
+    const int64_t q = cell0 * K3 + i;
+    G[i] = SA.tq[q];
+    G[C * K3 + i] = SA.tq[gm.ncq + q];
+    G[2 * C * K3 + i] = SA.tq[2 * gm.ncq + q];
+  }
+  if (active) {
+    int ijk[3];
+    const unsigned c = (unsigned)cell;
+    const unsigned q = c / (unsigned)gm.n[0];
+    ijk[0] = (int)(c - q * (unsigned)gm.n[0]);
+    ijk[1] = (int)(q % (unsigned)gm.n[1]);
+    ijk[2] = (int)(q / (unsigned)gm.n[1]);
+    // this cell's slot of face (d, s) is 1 - s
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int fid = split_face_id(ijk, d, s, gm.n, gm.P, gm.periodic);
+        const T* src = SA.ft[d] + ((int64_t)(fid * 2 + (1 - s)) * NFT) * K2 + ln;
+        T* dst = FT + (((lc * 3 + d) * 2 + s) * NFT) * K2 + ln;
+#pragma unroll
+        for (int f = 0; f < NFT; ++f) dst[f * K2] = src[f * K2];
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const T e0a = tb.E[0][la], e1a = tb.E[1][la], e0b = tb.E[0][lb], e1b = tb.E[1][lb];
+    const T* ftc = FT + lc * 6 * NFT * K2;
+#pragma unroll
+    for (int z = 0; z < K; ++z) {
+      const int pt = la + K * (lb + K * z);
+      // x faces at (y=lb, z), y faces at (x=la, z), z faces at (x=la, y=lb)
+      const T* fx0 = ftc + (0 * 2 + 0) * NFT * K2 + lb + K * z;
+      const T* fx1 = ftc + (0 * 2 + 1) * NFT * K2 + lb + K * z;
+      const T* fy0 = ftc + (1 * 2 + 0) * NFT * K2 + la + K * z;
+      const T* fy1 = ftc + (1 * 2 + 1) * NFT * K2 + la + K * z;
+      const T* fz0 = ftc + (2 * 2 + 0) * NFT * K2 + la + K * lb;
+      const T* fz1 = ftc + (2 * 2 + 1) * NFT * K2 + la + K * lb;
+      const T ez0 = tb.E[0][z], ez1 = tb.E[1][z];
+      auto inj = [&](int f) {
+        T a = e0a * fx0[f * K2];
+        a = fma(e1a, fx1[f * K2], a);
+        a = fma(e0b, fy0[f * K2], a);
+        a = fma(e1b, fy1[f * K2], a);
+        a = fma(ez0, fz0[f * K2], a);
+        return fma(ez1, fz1[f * K2], a);
+      };
+      Uc[pt] = inj(0);
+      if (OP == OP_SIPG) {
+        G0[pt] += inj(1);
+        G1[pt] += inj(2);
+        G2[pt] += inj(3);
+      }
+    }
+  }
+  __syncthreads();
+  auto sweep_DT = [&](const T* t, int base, int stride) {
+    if constexpr (kEO) eo_add_derivative_transposed<K>(tb, t, Uc, base, stride);
+    else line_add_transposed<K, K>(tb.D, t, Uc, base, stride);
+  };
+  auto sweep_ST = [&](int base, int stride) {
+    if constexpr (kEO) eo_apply<K, EO_ST>(tb, Uc, base, stride);
+    else line_apply<K, true, K>(tb.S, Uc, base, stride);
+  };
+  if (active) sweep_DT(G0, K * (la + K * lb), 1);
+  __syncthreads();
+  if (active) sweep_DT(G1, la + K2 * lb, K);
+  __syncthreads();
+  if (active) {
+    sweep_DT(G2, la + K * lb, K2);
+    sweep_ST(la + K * lb, K2);
+  }
+  __syncthreads();
+  if (active) sweep_ST(la + K2 * lb, K);
+  __syncthreads();
+  if (active) sweep_ST(K * (la + K * lb), 1);
+  __syncthreads();
+  {
+    double* o = P.dst + cell0 * K3;
+    const double* s = P.src + cell0 * K3;
+    double acc = 0.0;
+    const bool dot = P.dot_partial != nullptr;
+    for (int i = tid; i < nloc * K3; i += blockDim.x) {
+      o[i] = U[i];
+      if (dot) acc += U[i] * s[i];
+    }
+    if (dot) {
+      double* red = G;  // free now
+      red[tid] = acc;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
+        P.dot_partial[blockIdx.x] = t;
+      }
+    }
+  }
+}
+
+// Shared-memory bytes of the split kernels (C cells per block).
+__host__ __device__ constexpr int split_smem_forward(int k, int C) { return 4 * C * k * k * k * 8; }
+__host__ __device__ constexpr int split_smem_backward(int k, int op, int C) {
+  return (4 * C * k * k * k + C * 6 * (op == OP_SIPG ? 4 : 1) * k * k) * 8;
+}
+
+template <int K, int GEO, int OP>
+cudaError_t launch_split(const ApplyLaunch& L) {
+  ApplyParams<double> P;
+  P.tab = *static_cast<const Tables<double>*>(L.tables);
+  P.geo = *static_cast<const Geometry<double>*>(L.geometry);
+  P.src = static_cast<const double*>(L.src);
+  P.dst = static_cast<double*>(L.dst);
+  P.dot_partial = L.dot_partial;
+  const int C = (L.cpb >= 1 && L.cpb <= cells_per_block(K)) ? L.cpb : cells_per_block(K);
+  P.C = C;
+  P.cell_begin = L.cell_begin;
+  P.cell_end = L.cell_end;
+  const SplitArrays SA = *static_cast<const SplitArrays*>(L.split);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(split_cell_forward<K, GEO, OP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         split_smem_forward(K, cells_per_block(K)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(split_cell_backward<K, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               split_smem_backward(K, OP, cells_per_block(K)));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int64_t grid = (L.cell_end - L.cell_begin + C - 1) / C;
+  if (grid <= 0) return cudaSuccess;
+  split_cell_forward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_forward(K, C), L.stream>>>(P, SA);
+  const int FB = cells_per_block(K);  // faces per block of the face kernel
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int64_t nf = (int64_t)P.geo.P[d] * P.geo.n[t1] * P.geo.n[t2];
+    const unsigned fgrid = (unsigned)((nf + FB - 1) / FB);
+    if (d == 0) split_face<K, GEO, OP, 0><<<fgrid, FB * K * K, 0, L.stream>>>(P, SA, FB);
+    if (d == 1) split_face<K, GEO, OP, 1><<<fgrid, FB * K * K, 0, L.stream>>>(P, SA, FB);
+    if (d == 2) split_face<K, GEO, OP, 2><<<fgrid, FB * K * K, 0, L.stream>>>(P, SA, FB);
+  }
+  split_cell_backward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_backward(K, OP, C), L.stream>>>(P, SA);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_apply_split(const ApplyLaunch& L) {
+  if (L.op == OP_SIPG) {
+    if (L.geo == GEO_CART) return launch_split<K, GEO_CART, OP_SIPG>(L);
+    if (L.geo == GEO_FULL) return launch_split<K, GEO_FULL, OP_SIPG>(L);
+    return launch_split<K, GEO_MERGED, OP_SIPG>(L);
+  }
+  if (L.geo == GEO_CART) return launch_split<K, GEO_CART, OP_ADV>(L);
+  if (L.geo == GEO_FULL) return launch_split<K, GEO_FULL, OP_ADV>(L);
+  return launch_split<K, GEO_MERGED, OP_ADV>(L);
+}
+
+}  // namespace dg

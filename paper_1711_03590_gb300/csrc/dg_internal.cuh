@@ -70,6 +70,14 @@ struct Geometry {
   T vel[3];             // advection velocity
 };
 
+// Work arrays of the face-loop variant of the binary64 apply (device
+// pointers; dg_apply_split.cuh).
+struct SplitArrays {
+  double* tr[3];  // own traces per face of direction d: [face][slot][NTR][k^2]
+  double* ft[3];  // test coefficients per face: [face][slot][NFT][k^2]
+  double* tq;     // gradient-test fields at the Gauss points: [3][n_cells k^3]
+};
+
 // Host-side description of one apply launch.
 struct ApplyLaunch {
   int k;
@@ -85,6 +93,8 @@ struct ApplyLaunch {
   int cpb;               // cells per block (1 .. cells_per_block(k))
   int64_t cell_begin;    // the launch covers cells cell_begin .. cell_end - 1 (neighbours anywhere);
   int64_t cell_end;      // binary32: cell_begin a multiple of f32_geometry_block(k)
+  int face_mode;         // binary64: 0 element-centric (fused kernel), 1 face loop (split kernels)
+  const void* split;     // SplitArrays* of the face loop (whole mesh only)
 };
 
 // Largest number of cells per block of the apply kernel for k points per
