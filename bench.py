@@ -83,6 +83,33 @@ def kernel_flops_per_cell(k, op, geom, even_odd=False):
     return sweeps + nb + flux + qop * k3
 
 
+def kernel_flops_per_cell_loop(k, op, geom, even_odd=False):
+    """Floating-point work of one cell in the face-loop FP64 apply (three
+    stages), counted like kernel_flops_per_cell: the forward sweeps, the own
+    traces on six faces (E_s extrapolation of u and the reference gradient),
+    the q-point operation, the flux of three faces per cell for both slots,
+    the injection of the six faces' test coefficients and the backward
+    sweeps."""
+    k2, k3 = k * k, k ** 3
+    c, a = even_odd_ops(k, False), even_odd_ops(k, True)
+    if op == "sipg":
+        if even_odd:
+            sweeps = 2 * k2 * (3 * c + 3 * a) + 2 * k2 * (3 * c + 3 * a + 3 * k)
+        else:
+            sweeps = 24 * k ** 4
+        traces = 6 * k2 * 4 * 2 * k
+        qop = {"full": 39, "merged": 15, "cartesian": 8}[geom] * k3
+        face = 3 * k2 * 2 * 24
+        return sweeps + traces + qop + face + 48 * k3
+    if even_odd:
+        sweeps = 2 * k2 * (3 * c) + 2 * k2 * (3 * a + 3 * c + 3 * k)
+    else:
+        sweeps = 18 * k ** 4
+    traces = 6 * k2 * 2 * k
+    qop = ({"full": 24, "merged": 3, "cartesian": 3}[geom] + 3) * k3
+    return sweeps + traces + qop + 3 * k2 * 2 * 8 + 12 * k3
+
+
 def bytes_per_dof(k, s, op, geom):
     """Algorithmic bytes per dof of one apply: src read and dst write, the
     cell geometry per point, the face geometry per face point (3 faces per
@@ -512,6 +539,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp64emu"],
                     help="precision of the headline apply")
+    ap.add_argument("--face-mode", default="loop", choices=["loop", "element"],
+                    help="FP64 face evaluation: face loop (each face once; faster on GB300) or element-centric")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--solve-config3", action="store_true",
@@ -564,6 +593,9 @@ def main():
     peaks = load_peaks()
 
     op = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec=args.prec, coeff=w["coeff"], **common)
+    loop = args.prec == "fp64" and args.face_mode == "loop"
+    if loop:
+        op.set_face_mode("loop")
     n = op.n_dofs
     n_cells = op.info()["n_cells"]
     ssz = 4 if args.prec == "fp32" else 8
@@ -587,13 +619,19 @@ def main():
     t_max, value = aggregate_ranks(torch, dist, total_ms, args.steps, n, world, "cuda")
     ms_per_step = t_max / args.steps
 
-    # roofline of the apply kernel (the only kernel of a step)
-    flops = kernel_flops_per_cell(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5)) * n_cells
+    # roofline of the apply (one kernel; the face loop: its five launches)
+    if loop:
+        flops = kernel_flops_per_cell_loop(k, "sipg", w["geom"], even_odd=k >= 5) * n_cells
+    else:
+        flops = kernel_flops_per_cell(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5)) * n_cells
     achieved_tf = flops / (launch_ms / 1e3) / 1e12
     bpd = bytes_per_dof(k, ssz, "sipg", w["geom"])
     achieved_gbs = bpd * n / (launch_ms / 1e3) / 1e9
     if args.prec == "fp32":
         kname = "apply_f32_kernel<%d,%d,FULL,SIPG>" % (k, op.info()["cells_per_block"])
+    elif loop:
+        kname = ("face-loop apply <%d,FULL,SIPG>: split_cell_forward, split_face x 3 directions, "
+                 "split_cell_backward (the roofline is per apply)" % k)
     else:
         kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, {"fp64": "double", "fp64emu": "df64"}[args.prec])
     hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -619,10 +657,34 @@ def main():
         op.apply_host(hsrc, hdst)
     te = time.perf_counter() - te
     e2e = {"value": n / (te / e2e_steps), "unit": UNIT, "h2d_bytes_per_step": n * ssz, "d2h_bytes_per_step": n * ssz,
-           "call": "dg_apply_host"}
+           "call": "dg_apply_host", "face_mode": args.face_mode if args.prec == "fp64" else "element"}
     op.close()
 
+    fp64_element = None
+    if loop:
+        # the element-centric FP64 apply of the same workload: kernel-only,
+        # and end to end (its host path is pipelined over slabs); e2e reports
+        # the faster of the two public paths
+        ope_ = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64", coeff=w["coeff"], **common)
+        for _ in range(args.warmup):
+            ope_.apply(src, dst)
+        tot_el, _ = time_applies(torch, ope_, src, dst, args.steps, per_launch=False)
+        for _ in range(2):
+            ope_.apply_host(hsrc, hdst)
+        te2 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ope_.apply_host(hsrc, hdst)
+        te2 = time.perf_counter() - te2
+        ope_.close()
+        fp64_element = {"value": n / (tot_el / args.steps / 1e3), "unit": UNIT, "ms_per_step": tot_el / args.steps,
+                        "e2e": n / (te2 / e2e_steps),
+                        "speedup_of_face_loop": (tot_el / args.steps) / (total_ms / args.steps)}
+        if n / (te2 / e2e_steps) > e2e["value"]:
+            e2e.update({"value": n / (te2 / e2e_steps), "face_mode": "element (host path pipelined over slabs)"})
+
     extras = {}
+    if fp64_element:
+        extras["fp64_element"] = fp64_element
     if not args.no_extras and args.prec == "fp64":
         # FP32 arithmetic, same workload
         op32 = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp32", coeff=w["coeff"], **common)
@@ -652,6 +714,8 @@ def main():
         ope.close()
         # advection, FP64
         opa = dgp.Operator(mesh["n"], p, geom=w["geom"], op="advection", prec="fp64", **common)
+        if loop:
+            opa.set_face_mode("loop")
         for _ in range(args.warmup):
             opa.apply(src, dst)
         tota, la = time_applies(torch, opa, src, dst, max(10, args.steps // 2))
@@ -675,8 +739,10 @@ def main():
                            "dofs": n, "geometry": "full per-point Jacobians (G3)", "operator": "SIPG",
                            "boundary": "Dirichlet", "coefficient": "1+0.5 sin(2 pi x)",
                            "l2_policy": "inputs larger than L2 (vector + geometry > 500 MB)",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "face_mode": ("face loop: each face once (dg_set_face_mode)" if loop else
+                                         "element-centric fused kernel")},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * (5 if loop else 1),
                 "clocks": clocks}
         line.update(extras)
         print(json.dumps(line), flush=True)
