@@ -84,12 +84,12 @@ def kernel_flops_per_cell(k, op, geom, even_odd=False):
 
 
 def kernel_flops_per_cell_loop(k, op, geom, even_odd=False):
-    """Floating-point work of one cell in the face-loop FP64 apply (three
-    stages), counted like kernel_flops_per_cell: the forward sweeps, the own
-    traces on six faces (E_s extrapolation of u and the reference gradient),
-    the q-point operation, the flux of three faces per cell for both slots,
-    the injection of the six faces' test coefficients and the backward
-    sweeps."""
+    """Floating-point work of one cell in the face-loop FP64 apply (two
+    launches), counted like kernel_flops_per_cell: the forward sweeps, the
+    own traces on six faces (E_s extrapolation of u and the reference
+    gradient), the q-point operation; then the flux on the six faces tested
+    on this cell's side, the injection of their test coefficients and the
+    backward sweeps."""
     k2, k3 = k * k, k ** 3
     c, a = even_odd_ops(k, False), even_odd_ops(k, True)
     if op == "sipg":
@@ -99,7 +99,7 @@ def kernel_flops_per_cell_loop(k, op, geom, even_odd=False):
             sweeps = 24 * k ** 4
         traces = 6 * k2 * 4 * 2 * k
         qop = {"full": 39, "merged": 15, "cartesian": 8}[geom] * k3
-        face = 3 * k2 * 2 * 24
+        face = 6 * k2 * 24
         return sweeps + traces + qop + face + 48 * k3
     if even_odd:
         sweeps = 2 * k2 * (3 * c) + 2 * k2 * (3 * a + 3 * c + 3 * k)
@@ -107,7 +107,7 @@ def kernel_flops_per_cell_loop(k, op, geom, even_odd=False):
         sweeps = 18 * k ** 4
     traces = 6 * k2 * 2 * k
     qop = ({"full": 24, "merged": 3, "cartesian": 3}[geom] + 3) * k3
-    return sweeps + traces + qop + 3 * k2 * 2 * 8 + 12 * k3
+    return sweeps + traces + qop + 6 * k2 * 8 + 12 * k3
 
 
 def bytes_per_dof(k, s, op, geom):
@@ -246,6 +246,7 @@ def solve_metrics(torch, dgp, args, n=16, p=3, rtol=1e-10, repeats=20):
     repeated mixed solves from a zero initial guess."""
     kw = dict(geom="full", periodic=False, mapping=1, amplitude=0.1, coeff=1)
     o64 = dgp.Operator(n, p, prec="fp64", **kw)
+    o64.set_face_mode(args.face_mode)
     o32 = dgp.Operator(n, p, prec="fp32", **kw)
     rhs = o64.rhs(1)
     torch.cuda.synchronize()
@@ -398,16 +399,18 @@ def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rat
 
 
 def config3_metrics(torch, dgp, rtol=1e-10, cases=(("cartesian_64^3_p3", 64, 3, 0), ("deformed_48^3_p3", 48, 3, 1),
-                                                   ("deformed_48^3_p5", 48, 5, 1))):
+                                                   ("deformed_48^3_p5", 48, 5, 1)), face_mode="loop"):
     """Mixed precision at full size: manufactured Poisson problems solved to
-    rtol by plain FP64 CG, by the mixed solver (FP64 outer residual) and by
-    the mixed solver with the emulated-FP64 outer residual; wall time,
+    rtol by plain FP64 CG, by the mixed solver (FP64 outer residual; the FP64
+    operator in the given face mode) and by the mixed solver with the
+    emulated-FP64 outer residual; wall time,
     iterations, L2 errors against the exact solution and the difference
     between the mixed and the FP64 solutions."""
     out = {}
     for name, n, p, mapping in cases:
         kw = dict(geom="full" if mapping else "cartesian", mapping=mapping, amplitude=0.1, coeff=mapping)
         o64 = dgp.Operator(n, p, prec="fp64", **kw)
+        o64.set_face_mode(face_mode)
         o32 = dgp.Operator(n, p, prec="fp32", **kw)
         oe = dgp.Operator(n, p, prec="fp64emu", **kw)
         rhs = o64.rhs(mapping)
@@ -540,7 +543,8 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp64emu"],
                     help="precision of the headline apply")
     ap.add_argument("--face-mode", default="loop", choices=["loop", "element"],
-                    help="FP64 face evaluation: face loop (each face once; faster on GB300) or element-centric")
+                    help="FP64 face evaluation: face loop (neighbour traces read, not recomputed; faster on GB300) "
+                         "or element-centric")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--solve-config3", action="store_true",
@@ -582,7 +586,7 @@ def main():
         return
     if args.solve_config3:
         if rank == 0:
-            print(json.dumps({"solve_config3": config3_metrics(torch, dgp)}), flush=True)
+            print(json.dumps({"solve_config3": config3_metrics(torch, dgp, face_mode=args.face_mode)}), flush=True)
         return
 
     wname = "deformed_dirichlet_32^3_p%d" % args.degree
@@ -619,7 +623,7 @@ def main():
     t_max, value = aggregate_ranks(torch, dist, total_ms, args.steps, n, world, "cuda")
     ms_per_step = t_max / args.steps
 
-    # roofline of the apply (one kernel; the face loop: its five launches)
+    # roofline of the apply (one kernel; the face loop: its two launches)
     if loop:
         flops = kernel_flops_per_cell_loop(k, "sipg", w["geom"], even_odd=k >= 5) * n_cells
     else:
@@ -630,8 +634,8 @@ def main():
     if args.prec == "fp32":
         kname = "apply_f32_kernel<%d,%d,FULL,SIPG>" % (k, op.info()["cells_per_block"])
     elif loop:
-        kname = ("face-loop apply <%d,FULL,SIPG>: split_cell_forward, split_face x 3 directions, "
-                 "split_cell_backward (the roofline is per apply)" % k)
+        kname = ("face-loop apply <%d,FULL,SIPG>: split_cell_forward + split_cell_backward "
+                 "(the roofline is per apply)" % k)
     else:
         kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, {"fp64": "double", "fp64emu": "df64"}[args.prec])
     hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -663,8 +667,7 @@ def main():
     fp64_element = None
     if loop:
         # the element-centric FP64 apply of the same workload: kernel-only,
-        # and end to end (its host path is pipelined over slabs); e2e reports
-        # the faster of the two public paths
+        # and end to end; e2e reports the faster of the two public paths
         ope_ = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64", coeff=w["coeff"], **common)
         for _ in range(args.warmup):
             ope_.apply(src, dst)
@@ -680,7 +683,7 @@ def main():
                         "e2e": n / (te2 / e2e_steps),
                         "speedup_of_face_loop": (tot_el / args.steps) / (total_ms / args.steps)}
         if n / (te2 / e2e_steps) > e2e["value"]:
-            e2e.update({"value": n / (te2 / e2e_steps), "face_mode": "element (host path pipelined over slabs)"})
+            e2e.update({"value": n / (te2 / e2e_steps), "face_mode": "element"})
 
     extras = {}
     if fp64_element:
@@ -740,9 +743,9 @@ def main():
                            "boundary": "Dirichlet", "coefficient": "1+0.5 sin(2 pi x)",
                            "l2_policy": "inputs larger than L2 (vector + geometry > 500 MB)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "face_mode": ("face loop: each face once (dg_set_face_mode)" if loop else
-                                         "element-centric fused kernel")},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * (5 if loop else 1),
+                           "face_mode": ("face loop: two launches, neighbour traces read (dg_set_face_mode)"
+                                         if loop else "element-centric fused kernel")},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * (2 if loop else 1),
                 "clocks": clocks}
         line.update(extras)
         print(json.dumps(line), flush=True)

@@ -155,16 +155,16 @@ dg_status dg_set_stream(dg_handle *h, void *stream);
 dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
 
 /* Face evaluation of the DG_FP64 apply.  DG_FACE_ELEMENT (default): one
- * fused kernel, every cell evaluates its six faces (each interior face twice,
- * the neighbour's traces re-interpolated from its dofs).  DG_FACE_LOOP: three
- * launches -- cells write their own face traces and q-point fields, one
- * kernel per face direction evaluates each face once for both sides (the
- * paper's face loop, Algorithm 1 steps (iii)-(iv), here without atomics),
- * cells inject and integrate -- trading memory traffic for FP64 arithmetic.
- * Same results up to rounding.  DG_FACE_LOOP allocates its work arrays
- * (about 28 + 24 doubles per dof at p = 4) here; it covers whole meshes only,
- * so dg_apply_host does not pipeline it.  Other precisions: DG_ERR_UNSUPPORTED.
- * Synchronous. */
+ * fused kernel, every cell evaluates its six faces (the neighbour's traces
+ * re-interpolated from its dofs).  DG_FACE_LOOP: two launches -- cells write
+ * their own face traces (u and the reference gradient, per face and side) and
+ * q-point fields; then cells read both sides' traces of their six faces, form
+ * the flux tested on their own side, inject and integrate (the paper's
+ * separate cell and face work, Algorithm 1 steps (ii)-(iv), without atomics)
+ * -- trading memory traffic for FP64 arithmetic.  Same results up to
+ * rounding.  DG_FACE_LOOP allocates its work arrays here: 24/k + 3 doubles
+ * per dof for SIPG (62 bytes per dof at p = 4), 6/k + 3 for advection.
+ * Other precisions: DG_ERR_UNSUPPORTED.  Synchronous. */
 typedef enum { DG_FACE_ELEMENT = 0, DG_FACE_LOOP = 1 } dg_face_mode;
 dg_status dg_set_face_mode(dg_handle *h, int mode);
 
@@ -175,9 +175,9 @@ dg_status dg_set_face_mode(dg_handle *h, int mode);
  * Synchronous. */
 dg_status dg_autotune(dg_handle *h, int *best_cpb, double *best_ms);
 
-/* dst = A src on the device (Algorithm 1 steps (ii)-(iv); one kernel launch:
- * each cell computes its cell integral and its six face integrals tested on
- * itself and sets its dst entries).  src and dst: device pointers to n_dofs
+/* dst = A src on the device (Algorithm 1 steps (ii)-(iv); one kernel launch,
+ * two with DG_FACE_LOOP: each cell computes its cell integral and its six
+ * face integrals tested on itself and sets its dst entries).  src and dst: device pointers to n_dofs
  * scalars of the handle's precision; src == dst, or overlapping ranges, give
  * DG_ERR_ARG.  Asynchronous. */
 dg_status dg_apply(dg_handle *h, const void *src, void *dst);
@@ -186,7 +186,8 @@ dg_status dg_apply(dg_handle *h, const void *src, void *dst);
  * copies the result back, and waits for the stream.  Pinned host memory
  * makes the copies asynchronous DMA; on non-periodic meshes whose z-planes
  * hold a multiple of 64 cells the work is pipelined over up to 8 slabs of
- * z-planes (copies in, applies and copies out overlap; the result is the
+ * z-planes (copies in, applies and copies out overlap; with DG_FACE_LOOP a
+ * slab's second launch follows the next slab's first; the result is the
  * same bits as dg_apply).  Device staging buffers, two copy streams, a
  * second compute stream and their events are created on the first call and
  * kept by the handle. */

@@ -281,7 +281,7 @@ struct dg_handle {
   int face_mode;
   dg::SplitArrays split;
   cudaStream_t h2d_stream, d2h_stream, cmp_stream;
-  cudaEvent_t pipe_ev[2 * kHostSlabs + 2];
+  cudaEvent_t pipe_ev[3 * kHostSlabs + 2];
   std::string err;
 };
 
@@ -831,7 +831,7 @@ int64_t apply_blocks(const dg_handle* h) {
 }
 
 dg_status launch_apply_range(dg_handle* h, const void* src, void* dst, double* dot_partial, int64_t cell_begin,
-                             int64_t cell_end, cudaStream_t stream) {
+                             int64_t cell_end, cudaStream_t stream, int split_stage = 0) {
   dg::ApplyLaunch L;
   L.k = h->k;
   L.prec = h->prec;
@@ -851,9 +851,8 @@ dg_status launch_apply_range(dg_handle* h, const void* src, void* dst, double* d
   L.cell_begin = cell_begin;
   L.cell_end = cell_end;
   L.face_mode = h->face_mode;
+  L.split_stage = split_stage;
   L.split = &h->split;
-  if (h->face_mode == 1 && (cell_begin != 0 || cell_end != h->n_cells))
-    return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply covers the whole mesh");
   cudaError_t e;
   switch (h->k) {
     case 2: e = dg::launch_apply_k2(L, h->n_cells); break;
@@ -1052,7 +1051,6 @@ void free_handle(dg_handle* h) {
   dev_free(h, h->bw);
   for (int d = 0; d < 3; ++d) {
     dev_free(h, h->split.tr[d]);
-    dev_free(h, h->split.ft[d]);
   }
   dev_free(h, h->split.tq);
   if (h->cg_stream) cudaStreamDestroy(h->cg_stream);
@@ -1353,6 +1351,8 @@ dg_status dg_apply(dg_handle* h, const void* src, void* dst) {
 // has arrived; its result is copied back on a second copy stream while later
 // slabs are computed.  Results are the same as one
 // dg_apply (every cell's arithmetic is independent of the launch range).
+// The face loop runs its forward launch per slab as the slabs arrive and
+// slab s's backward launch once slab s+1's forward launch is done.
 // Periodic meshes in z (the first slab needs the last) and meshes whose
 // z-planes do not align with the kernels' cell blocks use a single slab.
 dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
@@ -1371,8 +1371,7 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
   }
   const int64_t plane = (int64_t)h->mesh.n[0] * h->mesh.n[1];
   const int nz = h->mesh.n[2];
-  int slabs =
-      (!h->mesh.periodic && h->face_mode == 0 && plane % 64 == 0 && nz >= 4) ? std::min(kHostSlabs, nz / 2) : 1;
+  int slabs = (!h->mesh.periodic && plane % 64 == 0 && nz >= 4) ? std::min(kHostSlabs, nz / 2) : 1;
   const int64_t k3 = (int64_t)h->k * h->k * h->k;
   auto cell_of_slab = [&](int s) { return plane * ((int64_t)nz * s / slabs); };
   cudaEvent_t* ev_in = h->pipe_ev;              // slab s on the device
@@ -1389,6 +1388,36 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
     DG_CUDA(h, cudaMemcpyAsync(static_cast<char*>(h->stage_src) + off, static_cast<const char*>(src_host) + off, len,
                                cudaMemcpyHostToDevice, h->h2d_stream));
     DG_CUDA(h, cudaEventRecord(ev_in[s], h->h2d_stream));
+  }
+  if (h->face_mode == DG_FACE_LOOP) {
+    // face loop: forward launches on the handle's stream as the slabs
+    // arrive; slab s's backward launch, on the second compute stream, once
+    // the forward launch of slab s + 1 (which writes the upper neighbours'
+    // traces) is done; a backward launch overlaps the next forward launch
+    cudaEvent_t* ev_fwd = h->pipe_ev + 2 * kHostSlabs + 2;
+    for (int s = 0; s < slabs; ++s) {
+      DG_CUDA(h, cudaStreamWaitEvent(h->stream, ev_in[s], 0));
+      if ((st = launch_apply_range(h, h->stage_src, h->stage_dst, nullptr, cell_of_slab(s), cell_of_slab(s + 1),
+                                   h->stream, 1)) != DG_OK)
+        return st;
+      DG_CUDA(h, cudaEventRecord(ev_fwd[s], h->stream));
+    }
+    for (int s = 0; s < slabs; ++s) {
+      const int64_t c0 = cell_of_slab(s), c1 = cell_of_slab(s + 1);
+      DG_CUDA(h, cudaStreamWaitEvent(h->cmp_stream, ev_fwd[std::min(s + 1, slabs - 1)], 0));
+      if ((st = launch_apply_range(h, h->stage_src, h->stage_dst, nullptr, c0, c1, h->cmp_stream, 2)) != DG_OK)
+        return st;
+      DG_CUDA(h, cudaEventRecord(ev_out[s], h->cmp_stream));
+      DG_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, ev_out[s], 0));
+      const size_t off = (size_t)(c0 * k3) * scal, len = (size_t)((c1 - c0) * k3) * scal;
+      DG_CUDA(h, cudaMemcpyAsync(static_cast<char*>(dst_host) + off, static_cast<const char*>(h->stage_dst) + off,
+                                 len, cudaMemcpyDeviceToHost, h->d2h_stream));
+    }
+    DG_CUDA(h, cudaEventRecord(ev_cmp, h->cmp_stream));
+    DG_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cmp, 0));
+    DG_CUDA(h, cudaStreamSynchronize(h->d2h_stream));
+    DG_CUDA(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
   }
   for (int s = 0; s < slabs; ++s) {
     const int64_t c0 = cell_of_slab(s), c1 = cell_of_slab(s + 1);
@@ -1562,7 +1591,7 @@ dg_status dg_set_face_mode(dg_handle* h, int mode) {
   if (mode == DG_FACE_LOOP && h->prec != DG_FP64)
     return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply is implemented for DG_FP64");
   if (mode == DG_FACE_LOOP && !h->split.tq) {
-    // traces and test coefficients per face and slot, gradient-test fields per point
+    // traces per face and slot, gradient-test fields per point
     const int k2 = h->k * h->k;
     const int nf = h->op == DG_OP_SIPG ? 4 : 1;
     dg_status st;
@@ -1572,7 +1601,6 @@ dg_status dg_set_face_mode(dg_handle* h, int mode) {
                             h->mesh.n[t2];
       const size_t bytes = sizeof(double) * faces * 2 * nf * k2;
       if ((st = dev_alloc(h, (void**)&h->split.tr[d], bytes)) != DG_OK) return st;
-      if ((st = dev_alloc(h, (void**)&h->split.ft[d], bytes)) != DG_OK) return st;
     }
     if ((st = dev_alloc(h, (void**)&h->split.tq, sizeof(double) * 3 * h->n_dofs)) != DG_OK) return st;
     DG_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -1,32 +1,35 @@
-// Face-loop variant of the binary64 apply: every face is evaluated once.
+// Face-loop variant of the binary64 apply: the neighbour's traces are read,
+// not recomputed.
 //
 // The fused kernel (dg_apply.cuh) is element-centric: each cell evaluates
-// its six faces, so every interior face is computed twice, and the
-// neighbour's traces are re-interpolated from its Gauss-Lobatto dofs (S_f,
-// D_f and the in-face sweeps of Eq. face_integral).  On GB300 the binary64
-// apply is bound by the FP64 pipe (1/64 of the binary32 rate) while HBM is
-// nearly idle, so this variant trades memory traffic for arithmetic, in the
-// spirit of the paper's face loop with a two-sided write (Algorithm 1 steps
-// (iii)-(iv) over faces), without atomics:
+// its six faces and re-interpolates the neighbour's traces from its
+// Gauss-Lobatto dofs (S_f, D_f and the in-face sweeps of Eq. face_integral).
+// On GB300 the binary64 apply is bound by the FP64 pipe (1/64 of the binary32
+// rate) while HBM is nearly idle, so this variant trades memory traffic for
+// arithmetic, in the spirit of the paper's separate cell and face loops
+// (Algorithm 1 steps (ii)-(iv)), without atomics, in two launches:
 //
 //   1. cell kernel: gather, S (x) S (x) S and D^co sweeps; the cell's own
 //      traces on its six faces (u and the reference gradient, by the
-//      Gauss-collocation extrapolation E_s) are written per face and slot;
-//      the q-point operation (Sec. 5 geometry) writes the gradient-test
-//      fields at the Gauss points;
-//   2. face kernel (one launch per direction): per face point, both slots'
-//      traces and the face geometry give the numerical flux once (Eq.
-//      poisson_sip / advection) and the test coefficients of both sides
-//      (value and reference gradient, Algorithm 1 step (iii)(c)) are written
-//      per face and slot;
-//   3. cell kernel: the gradient-test fields and the six faces' test
-//      coefficients of this cell's slot are injected (transpose of E_s) and
+//      Gauss-collocation extrapolation E_s) are written per face and slot
+//      (slot 0: the cell below the face along its direction, slot 1: the
+//      cell above); the q-point operation (Sec. 5 geometry) writes the
+//      gradient-test fields at the Gauss points;
+//   2. cell kernel: for each face point of its six faces, the numerical
+//      flux (Eq. poisson_sip / advection) from both slots' traces and the
+//      face geometry, tested on this cell's side (value and reference
+//      gradient, Algorithm 1 step (iii)(c)); the gradient-test fields and
+//      the faces' test coefficients are injected (transpose of E_s) and
 //      integrated (D^co^T, S^T (x) S^T (x) S^T); dst is set.
 //
+// Each side's flux evaluation is its own (the paper's face loop evaluates
+// once and adds into both sides; here each side writes only its own cell).
 // Work arrays (per operator, allocated when the mode is selected): traces
-// and test coefficients [face][slot][field][k^2] per direction, and three
-// gradient-test fields [field][cell][k^3].  The results equal the fused
-// kernel's up to rounding (same method, other operation order).
+// [face][slot][field][k^2] per direction and three gradient-test fields
+// [field][cell][k^3].  A launch covers a range of cells; the backward launch
+// of a range needs the forward launch of the range and of its neighbours.
+// The results equal the fused kernel's up to rounding (same method, other
+// operation order).
 #pragma once
 
 #include <cstdint>
@@ -222,111 +225,84 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
   }
 }
 
-// Step 2: one flux evaluation per face point of direction D, for both slots.
-// K^2 threads per face, FB faces per block.
-template <int K, int GEO, int OP, int D>
-__global__ void __launch_bounds__(Shape<K>::max_threads)
-    split_face(const __grid_constant__ ApplyParams<double> P, const __grid_constant__ SplitArrays SA, int FB) {
+// Numerical flux at face point fp (qa = fp mod K along t1, qb along t2) of
+// face fid of direction d, tested on slot so (Eq. poisson_sip / advection,
+// Algorithm 1 step (iii)(c)): u, g are both slots' traces (value and
+// reference gradient; the other slot's are read only if `interior`).  Writes
+// the value test and (SIPG) the reference-gradient test of slot so to
+// ft[0], ft[fs], ft[2 fs], ft[3 fs].
+template <int K, int GEO, int OP>
+__device__ __forceinline__ void split_slot_flux(const Tables<double>& tb, const Geometry<double>& gm, int d,
+                                                int64_t fid, int pos, int it1, int fp, int so, bool interior,
+                                                const double (&u)[2], const double (&g)[2][3], double* ft, int fs) {
   using T = double;
   constexpr int K2 = K * K;
-  constexpr int NTR = SplitFields<OP>::NTR, NFT = SplitFields<OP>::NFT;
-  constexpr int t1d = D == 0 ? 1 : 0, t2d = D == 2 ? 1 : 2;
-  const Tables<T>& tb = P.tab;
-  const Geometry<T>& gm = P.geo;
-  const int lf = threadIdx.x / K2, fp = threadIdx.x - lf * K2;
   const int la = fp % K, lb = fp / K;
-  const int nd = gm.n[D], nt1 = gm.n[t1d], nt2 = gm.n[t2d];
-  const int Pd = gm.P[D];
-  const int64_t nfaces = (int64_t)Pd * nt1 * nt2;
-  const int64_t fid = (int64_t)blockIdx.x * FB + lf;
-  if (lf >= FB || fid >= nfaces) return;  // no barrier in this kernel
-  const int pos = (int)(fid % Pd);
-  const int64_t r = fid / Pd;
-  const int it1 = (int)(r % nt1);
-  const bool has[2] = {gm.periodic || pos >= 1, gm.periodic || pos < nd};
-  // both slots' traces: u and the reference gradient of each side's cell
-  T u[2] = {T(0), T(0)}, g[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+  const int sn = 1 - so;
+  const T cjd = gm.cart_jinv[d];
+  if (OP == OP_SIPG) {
+    // j_n per slot (each side's own outward normal: +d for slot 0)
+    T jo[3], jn[3], fjxw, tau;
+    if (GEO == GEO_CART) {
+      const T j = so == 0 ? cjd : -cjd;
 #pragma unroll
-  for (int sl = 0; sl < 2; ++sl) {
-    if (!has[sl]) continue;
-    const T* tr = SA.tr[D] + (fid * 2 + sl) * NTR * K2 + fp;
-    u[sl] = tr[0];
-    if (OP == OP_SIPG) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) g[sl][c] = tr[(1 + c) * K2];
-    }
-  }
-  const T cjd = gm.cart_jinv[D];
-#pragma unroll
-  for (int so = 0; so < 2; ++so) {
-    if (!has[so]) continue;
-    const int sn = 1 - so;
-    const bool interior = has[sn];
-    T* ft = SA.ft[D] + (fid * 2 + so) * NFT * K2 + fp;
-    if (OP == OP_SIPG) {
-      // j_n per slot (each side's own outward normal: +d for slot 0)
-      T jo[3], jn[3], fjxw, tau;
-      if (GEO == GEO_CART) {
-        const T j = so == 0 ? cjd : -cjd;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          jo[c] = c == D ? j : T(0);
-          jn[c] = -jo[c];
-        }
-        T kap = T(1);
-        if (gm.kq) kap = D == 0 ? gm.kf[pos] : gm.kq[it1 * K + la];
-        fjxw = kap * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
-        tau = gm.cart_tau[D];
-      } else {
-        const T* f = gm.face[D] + fid * K2 + fp;
-        const int64_t nfq = gm.nfq[D];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          jo[c] = f[(so * 3 + c) * nfq];
-          jn[c] = f[(sn * 3 + c) * nfq];
-        }
-        fjxw = f[6 * nfq];
-        tau = gm.tau[D][fid];
+      for (int c = 0; c < 3; ++c) {
+        jo[c] = c == d ? j : T(0);
+        jn[c] = -jo[c];
       }
-      const T dno = jo[0] * g[so][0] + jo[1] * g[so][1] + jo[2] * g[so][2];
-      T tv, tg;
-      if (interior) {
-        // the neighbour's derivative along this side's outward normal
-        const T dnn = -(jn[0] * g[sn][0] + jn[1] * g[sn][1] + jn[2] * g[sn][2]);
-        const T jump = u[so] - u[sn];
-        tv = fjxw * (tau * jump - T(0.5) * (dno + dnn));
-        tg = T(-0.5) * fjxw * jump;
-      } else {
-        tv = fjxw * (T(2) * tau * u[so] - dno);
-        tg = -fjxw * u[so];
-      }
-      ft[0] = tv;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) ft[(1 + c) * K2] = tg * jo[c];
+      T kap = T(1);
+      if (gm.kq) kap = d == 0 ? gm.kf[pos] : gm.kq[it1 * K + la];
+      fjxw = kap * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
+      tau = gm.cart_tau[d];
     } else {
-      T cn;
-      if (GEO == GEO_CART) cn = gm.vel[D] * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
-      else cn = gm.face[D][fid * K2 + fp];
-      const T cno = so == 0 ? cn : -cn;  // c.n da w with n this side's outward normal
-      ft[0] = interior ? T(0.5) * cno * (u[so] + u[sn]) + T(0.5) * fabs(cno) * (u[so] - u[sn])
-                       : fabs(cno) * u[so];
+      const T* f = gm.face[d] + fid * K2 + fp;
+      const int64_t nfq = gm.nfq[d];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        jo[c] = f[(so * 3 + c) * nfq];
+        jn[c] = f[(sn * 3 + c) * nfq];
+      }
+      fjxw = f[6 * nfq];
+      tau = gm.tau[d][fid];
     }
+    const T dno = jo[0] * g[so][0] + jo[1] * g[so][1] + jo[2] * g[so][2];
+    T tv, tg;
+    if (interior) {
+      // the neighbour's derivative along this side's outward normal
+      const T dnn = -(jn[0] * g[sn][0] + jn[1] * g[sn][1] + jn[2] * g[sn][2]);
+      const T jump = u[so] - u[sn];
+      tv = fjxw * (tau * jump - T(0.5) * (dno + dnn));
+      tg = T(-0.5) * fjxw * jump;
+    } else {
+      tv = fjxw * (T(2) * tau * u[so] - dno);
+      tg = -fjxw * u[so];
+    }
+    ft[0] = tv;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ft[(1 + c) * fs] = tg * jo[c];
+  } else {
+    T cn;
+    if (GEO == GEO_CART) cn = gm.vel[d] * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
+    else cn = gm.face[d][fid * K2 + fp];
+    const T cno = so == 0 ? cn : -cn;  // c.n da w with n this side's outward normal
+    ft[0] = interior ? T(0.5) * cno * (u[so] + u[sn]) + T(0.5) * fabs(cno) * (u[so] - u[sn]) : fabs(cno) * u[so];
   }
 }
 
-// Step 3: injection of the face test coefficients, integration, dst.
+// Step 2: the numerical flux of this cell's slot on its six faces from both
+// slots' traces, injection of the test coefficients, integration, dst.
 template <int K, int GEO, int OP>
 __global__ void __launch_bounds__(Shape<K>::max_threads)
     split_cell_backward(const __grid_constant__ ApplyParams<double> P, const __grid_constant__ SplitArrays SA) {
   using T = double;
   constexpr int K2 = K * K, K3 = K2 * K;
-  constexpr int NFT = SplitFields<OP>::NFT;
+  constexpr int NTR = SplitFields<OP>::NTR, NFT = SplitFields<OP>::NFT;
   constexpr bool kEO = K >= 5;
   const int C = P.C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3]
   T* G = U + C * K3;                      // [3][C][K3]
-  T* FT = G + 3 * C * K3;                 // [C][3][2][NFT][K2]
+  T* FT = G + 3 * C * K3;                 // [C][3][2][NFT][K2]: test coefficients of the six faces
   const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
   const int tid = threadIdx.x;
@@ -360,10 +336,24 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const int fid = split_face_id(ijk, d, s, gm.n, gm.P, gm.periodic);
-        const T* src = SA.ft[d] + ((int64_t)(fid * 2 + (1 - s)) * NFT) * K2 + ln;
         T* dst = FT + (((lc * 3 + d) * 2 + s) * NFT) * K2 + ln;
+        const int id = ijk[d], nd = gm.n[d];
+        const bool interior = gm.periodic || (s ? id + 1 < nd : id >= 1);
+        int pos = id + s;
+        if (gm.periodic && pos == nd) pos = 0;
+        const int it1 = d == 0 ? ijk[1] : ijk[0];
+        T u[2] = {T(0), T(0)}, g[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
 #pragma unroll
-        for (int f = 0; f < NFT; ++f) dst[f * K2] = src[f * K2];
+        for (int sl = 0; sl < 2; ++sl) {
+          if (sl == s && !interior) continue;  // slot s is the neighbour's
+          const T* tr = SA.tr[d] + ((int64_t)fid * 2 + sl) * NTR * K2 + ln;
+          u[sl] = tr[0];
+          if (OP == OP_SIPG) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g[sl][c] = tr[(1 + c) * K2];
+          }
+        }
+        split_slot_flux<K, GEO, OP>(tb, gm, d, fid, pos, it1, ln, 1 - s, interior, u, g, dst, K2);
       }
     }
   }
@@ -474,17 +464,10 @@ cudaError_t launch_split(const ApplyLaunch& L) {
   }
   const int64_t grid = (L.cell_end - L.cell_begin + C - 1) / C;
   if (grid <= 0) return cudaSuccess;
-  split_cell_forward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_forward(K, C), L.stream>>>(P, SA);
-  const int FB = cells_per_block(K);  // faces per block of the face kernel
-  for (int d = 0; d < 3; ++d) {
-    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    const int64_t nf = (int64_t)P.geo.P[d] * P.geo.n[t1] * P.geo.n[t2];
-    const unsigned fgrid = (unsigned)((nf + FB - 1) / FB);
-    if (d == 0) split_face<K, GEO, OP, 0><<<fgrid, FB * K * K, 0, L.stream>>>(P, SA, FB);
-    if (d == 1) split_face<K, GEO, OP, 1><<<fgrid, FB * K * K, 0, L.stream>>>(P, SA, FB);
-    if (d == 2) split_face<K, GEO, OP, 2><<<fgrid, FB * K * K, 0, L.stream>>>(P, SA, FB);
-  }
-  split_cell_backward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_backward(K, OP, C), L.stream>>>(P, SA);
+  if (L.split_stage != 2)
+    split_cell_forward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_forward(K, C), L.stream>>>(P, SA);
+  if (L.split_stage != 1)
+    split_cell_backward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_backward(K, OP, C), L.stream>>>(P, SA);
   return cudaGetLastError();
 }
 

@@ -74,7 +74,6 @@ struct Geometry {
 // pointers; dg_apply_split.cuh).
 struct SplitArrays {
   double* tr[3];  // own traces per face of direction d: [face][slot][NTR][k^2]
-  double* ft[3];  // test coefficients per face: [face][slot][NFT][k^2]
   double* tq;     // gradient-test fields at the Gauss points: [3][n_cells k^3]
 };
 
@@ -93,8 +92,11 @@ struct ApplyLaunch {
   int cpb;               // cells per block (1 .. cells_per_block(k))
   int64_t cell_begin;    // the launch covers cells cell_begin .. cell_end - 1 (neighbours anywhere);
   int64_t cell_end;      // binary32: cell_begin a multiple of f32_geometry_block(k)
-  int face_mode;         // binary64: 0 element-centric (fused kernel), 1 face loop (split kernels)
-  const void* split;     // SplitArrays* of the face loop (whole mesh only)
+  int face_mode;         // binary64: 0 element-centric (fused kernel), 1 face loop (two launches)
+  int split_stage;       // face loop: 0 the whole apply, 1 the cell-forward launch only, 2 the
+                         // backward launch only (cell ranges: the forward launch of every
+                         // neighbour of the range must have run)
+  const void* split;     // SplitArrays* of the face loop
 };
 
 // Largest number of cells per block of the apply kernel for k points per
