@@ -286,8 +286,8 @@ def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget
     meshes with n^3 cells, n log-uniform in [8, 48], degrees uniform in 1..7
     (G3 geometry, kappa variable, Dirichlet).  Compares one dg_batch_launch
     (autotuned tile shapes, 8 graph branches) with the same applies issued one
-    by one on a stream.  Meshes beyond the device-memory budget are dropped
-    (their count is reported)."""
+    by one on a stream; FP64 operators in the bench's face mode.  Meshes
+    beyond the device-memory budget are dropped (their count is reported)."""
     rng = np.random.default_rng(seed)
     ns = np.round(np.exp(rng.uniform(np.log(8), np.log(48), count))).astype(int)
     ps = rng.integers(1, 8, count)
@@ -299,12 +299,16 @@ def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget
         for n, p in zip(ns, ps):
             k = int(p) + 1
             dofs = int(n) ** 3 * k ** 3
-            need = dofs * (bytes_per_dof(k, s, "sipg", "full") + 2 * s) / 1e9
+            loop = prec == "fp64" and args.face_mode == "loop"
+            work = (24.0 / k + 3.0) * 8 if loop else 0.0  # face-loop traces and gradient-test fields
+            need = dofs * (bytes_per_dof(k, s, "sipg", "full") + 2 * s + work) / 1e9
             if used + need > budget_gb:
                 skipped += 1
                 continue
             used += need
             op = dgp.Operator(int(n), int(p), geom="full", prec=prec, mapping=1, amplitude=0.1, coeff=1)
+            if loop:
+                op.set_face_mode("loop")
             ops.append(op)
             srcs.append(torch.tensor(dg_inputs.src_vector(op.n_dofs, int(n) * 31 + int(p)), dtype=op.dtype,
                                      device="cuda"))
@@ -333,6 +337,7 @@ def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget
         t_seq = e0.elapsed_time(e1) / reps
         dgp.dg_batch_destroy(b)
         out[prec] = {"operators": len(ops), "skipped_for_memory": skipped, "dofs": total,
+                     "face_mode": "loop" if prec == "fp64" and args.face_mode == "loop" else "element",
                      "ms_per_batch_launch": t_batch, "dofs_per_s": total / (t_batch / 1e3),
                      "ms_sequential_applies": t_seq, "speedup_vs_sequential": t_seq / t_batch,
                      "cells_per_block_by_degree": {

@@ -71,6 +71,14 @@ __device__ __forceinline__ void f32_prefetch_bulk_l2(const void* p, unsigned byt
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Asynchronous 4-byte global-to-shared copies (staging without a register
+// round trip); completed by f32_cp_async_wait before the next barrier.
+__device__ __forceinline__ void f32_cp_async4(float* s, const float* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void f32_cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __host__ __device__ constexpr int f32_min_blocks(int k, int C) {
   return (k <= 6 ? 900 : 700) / (C * k * k) > 0 ? (k <= 6 ? 900 : 700) / (C * k * k) : 1;
 }
@@ -137,13 +145,40 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     i2 = (int)(q / (unsigned)gm.n[1]);
   }
 
-  // lines of the y and z neighbours through this thread's face points,
-  // loaded before the first barrier so that their latency overlaps the
-  // staging below (short lines only: register budget); boundary sides read
-  // the own cell (their data is not used)
+  // y and z neighbours.  SIPG with per-point geometry and short lines: the
+  // four blocks of C cells at offsets -n0, +n0, -n0 n1, +n0 n1 from the
+  // block's first cell are contiguous in memory and are staged into shared
+  // memory with coalesced asynchronous copies (chunk 0 in G0, chunks 1-3 in
+  // FB, both free until phase 2); cells whose neighbour is not at that
+  // offset (periodic wrap) read it from global memory, boundary sides read
+  // the own cell (their data is not used).  Otherwise (the Cartesian kernel
+  // is arithmetic-bound and staging slowed it down) the lines through the
+  // thread's face points are loaded into registers before the first barrier
+  // (advection: only the face layer), so that their latency overlaps the
+  // staging below.
   constexpr bool EARLY = K <= 6;
-  float wyz[EARLY ? 4 : 1][EARLY ? K : 1];
-  if constexpr (EARLY) {
+  constexpr bool STAGE_YZ = EARLY && TANG && 3 * K3 <= 6 * FSB;
+  auto yz_chunk = [&](int j) -> float* { return j == 0 ? G0 : FB + (j - 1) * C * K3; };
+  float wyz[EARLY && !STAGE_YZ ? 4 : 1][EARLY && !STAGE_YZ ? K : 1];
+  if constexpr (STAGE_YZ) {
+    const int n0 = gm.n[0], n01 = gm.n[0] * gm.n[1];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int off = j == 0 ? -n0 : j == 1 ? n0 : j == 2 ? -n01 : n01;
+      const int cb = cell0 + off;  // first cell of the chunk
+      const int lo = cb < 0 ? -cb * K3 : 0;
+      const int64_t rem = ((int64_t)ncell - cb) * K3;  // elements from the chunk start to the end
+      const int hi = rem < C * K3 ? (int)rem : C * K3;
+      float* dstc = yz_chunk(j);
+      const float* srcc = P.src + (int64_t)cb * K3;
+      static_assert((C * K3) % NT == 0, "chunk staging rounds");
+#pragma unroll
+      for (int r = 0; r < C * K3 / NT; ++r) {
+        const int e = tid + r * NT;
+        if (e >= lo && e < hi) f32_cp_async4(dstc + e, srcc + e);
+      }
+    }
+  } else if constexpr (EARLY) {
     const int n0 = gm.n[0], n01 = gm.n[0] * gm.n[1];
     const int per = gm.periodic;
     const int ny[2] = {i1 > 0 ? cell - n0 : per ? cell + (gm.n[1] - 1) * n0 : cell,
@@ -156,8 +191,12 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       const float* pz = P.src + (size_t)nz[s] * K3 + a + K * b;
 #pragma unroll
       for (int l = 0; l < K; ++l) {
-        wyz[s][l] = py[l * K];
-        wyz[2 + s][l] = pz[l * K2];
+        if (SIPG || l == (s ? 0 : K - 1)) {
+          wyz[s][l] = py[l * K];
+          wyz[2 + s][l] = pz[l * K2];
+        } else {
+          wyz[s][l] = wyz[2 + s][l] = 0.f;
+        }
       }
     }
   }
@@ -177,7 +216,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
     for (int r = 0; r < (NR + NT - 1) / NT; ++r) {
       const unsigned e = tid + r * NT;
-      if (e >= lo && e < hi) R[e] = P.src[base + e];
+      if (e >= lo && e < hi) f32_cp_async4(R + e, P.src + base + e);
     }
   }
   // neighbour cells and face ids of the six faces (d, s), one thread each;
@@ -200,6 +239,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     const int e0 = d == 0 ? gm.P[0] : gm.n[0], e1 = d == 1 ? gm.P[1] : gm.n[1];
     FID[t * C + lc] = f0 + e0 * (f1 + e1 * f2);
   }
+  f32_cp_async_wait();
   __syncthreads();
 
   // start the HBM fetch of this block's cell geometry (read in phase 6)
@@ -247,13 +287,27 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
         for (int l = 0; l < K; ++l) w[l] = p[l];
       }
+    } else if constexpr (STAGE_YZ) {
+      const int nstep = d == 1 ? gm.n[0] : gm.n[0] * gm.n[1];
+      if (nb == cell + (s ? nstep : -nstep)) {
+        const float* p = yz_chunk(t - 2) + lc * K3 + off;
+#pragma unroll
+        for (int l = 0; l < K; ++l) w[l] = p[l * str];
+      } else if (nb >= 0) {
+        const float* p = P.src + (size_t)nb * K3 + off;
+#pragma unroll
+        for (int l = 0; l < K; ++l) w[l] = p[l * str];
+      } else {
+#pragma unroll
+        for (int l = 0; l < K; ++l) w[l] = R[(lc + 1) * RS + off + l * str];
+      }
     } else if constexpr (EARLY) {
 #pragma unroll
       for (int l = 0; l < K; ++l) w[l] = wyz[t - 2][l];
     } else {
       const float* p = P.src + (size_t)(nb >= 0 ? nb : cell) * K3 + off;
 #pragma unroll
-      for (int l = 0; l < K; ++l) w[l] = p[l * str];
+      for (int l = 0; l < K; ++l) w[l] = (SIPG || l == (s ? 0 : K - 1)) ? p[l * str] : 0.f;
     }
     FA[(t * FSA + fpt) * C + lc] = s ? w[0] : w[K - 1];
     if (SIPG) {
