@@ -217,9 +217,11 @@ def aggregate_ranks(torch, dist, total_ms, steps, units_per_step, world, device)
     return t_max, world * units_per_step * steps / (t_max / 1e3)
 
 
-def time_applies(torch, op, src, dst, steps, per_launch=True):
-    """Device time of `steps` applies on the operator's stream (CUDA events),
-    and the average duration of one apply launch from per-launch events."""
+def time_applies(torch, op, src, dst, steps, per_launch=False):
+    """Device time of `steps` back-to-back applies on the operator's stream
+    (CUDA events around the whole region), and the average duration of one
+    apply: total / steps, or (per_launch) the mean of per-apply event pairs,
+    which add a few microseconds of event overhead to the region."""
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -281,7 +283,7 @@ def solve_metrics(torch, dgp, args, n=16, p=3, rtol=1e-10, repeats=20):
             "solves_per_s": 1.0 / float(np.mean(lat))}
 
 
-def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget_gb=40.0, seed=4):
+def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget_gb=120.0, seed=4):
     """Many independent operators in one graph launch: count deformed-cube
     meshes with n^3 cells, n log-uniform in [8, 48], degrees uniform in 1..7
     (G3 geometry, kappa variable, Dirichlet).  Compares one dg_batch_launch
@@ -448,8 +450,9 @@ def degree_sweep_metrics(torch, dgp, steps=30):
     """Apply throughput for p = 1..8 in FP64 and FP32 on the 32^3 mesh and on
     the paper's larger-than-cache size schedule (128^3 for p = 1-2, 64^3 for
     p = 3-5, 32^3 for p = 6-8), Cartesian, G3 (deformed, full Jacobians) and
-    G4 (deformed, merged coefficients); DoFs/s from the mean per-launch CUDA
-    event time after warm-up, and the HBM fraction of the algorithmic bytes."""
+    G4 (deformed, merged coefficients); FP64 element-centric and face loop;
+    DoFs/s from the mean per-apply CUDA event time after warm-up, and the HBM
+    fraction of the algorithmic bytes."""
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
     rows = []
@@ -458,8 +461,10 @@ def degree_sweep_metrics(torch, dgp, steps=30):
             if sched == "paper" and n == 32:
                 continue
             for geom, mapping in (("cartesian", 0), ("full", 1), ("merged", 1)):
-                for prec in ("fp64", "fp32"):
-                    o = dgp.Operator(n, p, geom=geom, prec=prec, mapping=mapping, amplitude=0.1, coeff=1)
+                for prec in ("fp64", "fp64-loop", "fp32"):
+                    o = dgp.Operator(n, p, geom=geom, prec=prec[:4], mapping=mapping, amplitude=0.1, coeff=1)
+                    if prec == "fp64-loop":
+                        o.set_face_mode("loop")
                     src = torch.tensor(dg_inputs.src_vector(o.n_dofs, 3), dtype=o.dtype, device="cuda")
                     dst = torch.empty_like(src)
                     for _ in range(3):
@@ -676,7 +681,7 @@ def main():
         ope_ = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64", coeff=w["coeff"], **common)
         for _ in range(args.warmup):
             ope_.apply(src, dst)
-        tot_el, _ = time_applies(torch, ope_, src, dst, args.steps, per_launch=False)
+        tot_el, _ = time_applies(torch, ope_, src, dst, args.steps)
         for _ in range(2):
             ope_.apply_host(hsrc, hdst)
         te2 = time.perf_counter()

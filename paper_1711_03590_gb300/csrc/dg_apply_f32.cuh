@@ -17,8 +17,11 @@
 //    an odd length so that no line direction has bank conflicts, and the face
 //    buffers are padded per face for the in-face line tasks.
 //  * The block's source cells and their x-neighbours are staged with
-//    coalesced loads; the y/z neighbours' lines through the thread's face
-//    points are loaded before the first barrier.
+//    coalesced loads (asynchronous copies from k = 5 on); the y/z
+//    neighbours' lines through the thread's face points are loaded before
+//    the first barrier, or (k = 5, 6 with per-point geometry) the four
+//    neighbouring blocks of C cells are staged whole with coalesced
+//    asynchronous copies.
 //  * The 1D sweeps keep their line in registers (k loads, k^2 FMAs, k
 //    stores); the z-line owner computes the z-derivative from registers.
 //  * The in-face sum factorization of the neighbours' traces (Eq.
@@ -145,19 +148,23 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     i2 = (int)(q / (unsigned)gm.n[1]);
   }
 
-  // y and z neighbours.  SIPG with per-point geometry and short lines: the
-  // four blocks of C cells at offsets -n0, +n0, -n0 n1, +n0 n1 from the
-  // block's first cell are contiguous in memory and are staged into shared
-  // memory with coalesced asynchronous copies (chunk 0 in G0, chunks 1-3 in
-  // FB, both free until phase 2); cells whose neighbour is not at that
-  // offset (periodic wrap) read it from global memory, boundary sides read
-  // the own cell (their data is not used).  Otherwise (the Cartesian kernel
-  // is arithmetic-bound and staging slowed it down) the lines through the
-  // thread's face points are loaded into registers before the first barrier
+  // y and z neighbours.  SIPG with per-point geometry, k = 5, 6: the four
+  // blocks of C cells at offsets -n0, +n0, -n0 n1, +n0 n1 from the block's
+  // first cell are contiguous in memory and are staged into shared memory
+  // with coalesced asynchronous copies (chunk 0 in G0, chunks 1-3 in FB, both
+  // free until phase 2); cells whose neighbour is not at that offset
+  // (periodic wrap) read it from global memory, boundary sides read the own
+  // cell (their data is not used).  Otherwise the lines through the thread's
+  // face points are loaded into registers before the first barrier
   // (advection: only the face layer), so that their latency overlaps the
-  // staging below.
+  // staging below.  (Measured against the register path: +9% at k = 6, +-0
+  // at k = 5; slower for k <= 4 and for the arithmetic-bound Cartesian
+  // kernel.)
   constexpr bool EARLY = K <= 6;
-  constexpr bool STAGE_YZ = EARLY && TANG && 3 * K3 <= 6 * FSB;
+  constexpr bool STAGE_YZ = EARLY && K >= 5 && TANG && 3 * K3 <= 6 * FSB;
+  // the source staging below also uses asynchronous copies from k = 5 on
+  // (+1-4% at k = 7, 8; slower for k <= 4)
+  constexpr bool ASYNC_R = K >= 5;
   auto yz_chunk = [&](int j) -> float* { return j == 0 ? G0 : FB + (j - 1) * C * K3; };
   float wyz[EARLY && !STAGE_YZ ? 4 : 1][EARLY && !STAGE_YZ ? K : 1];
   if constexpr (STAGE_YZ) {
@@ -172,10 +179,15 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
       float* dstc = yz_chunk(j);
       const float* srcc = P.src + (int64_t)cb * K3;
       static_assert((C * K3) % NT == 0, "chunk staging rounds");
+      if (lo == 0 && hi == C * K3) {  // whole chunk inside the mesh (block-uniform)
 #pragma unroll
-      for (int r = 0; r < C * K3 / NT; ++r) {
-        const int e = tid + r * NT;
-        if (e >= lo && e < hi) f32_cp_async4(dstc + e, srcc + e);
+        for (int r = 0; r < C * K3 / NT; ++r) f32_cp_async4(dstc + tid + r * NT, srcc + tid + r * NT);
+      } else {
+#pragma unroll
+        for (int r = 0; r < C * K3 / NT; ++r) {
+          const int e = tid + r * NT;
+          if (e >= lo && e < hi) f32_cp_async4(dstc + e, srcc + e);
+        }
       }
     }
   } else if constexpr (EARLY) {
@@ -216,7 +228,10 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
 #pragma unroll
     for (int r = 0; r < (NR + NT - 1) / NT; ++r) {
       const unsigned e = tid + r * NT;
-      if (e >= lo && e < hi) f32_cp_async4(R + e, P.src + base + e);
+      if (e >= lo && e < hi) {
+        if constexpr (ASYNC_R) f32_cp_async4(R + e, P.src + base + e);
+        else R[e] = P.src[base + e];
+      }
     }
   }
   // neighbour cells and face ids of the six faces (d, s), one thread each;
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
     const int e0 = d == 0 ? gm.P[0] : gm.n[0], e1 = d == 1 ? gm.P[1] : gm.n[1];
     FID[t * C + lc] = f0 + e0 * (f1 + e1 * f2);
   }
-  f32_cp_async_wait();
+  if constexpr (ASYNC_R || STAGE_YZ) f32_cp_async_wait();
   __syncthreads();
 
   // start the HBM fetch of this block's cell geometry (read in phase 6)
