@@ -66,10 +66,6 @@ struct F32Shape {
   static constexpr int NT = C * K2;  // threads per block
 };
 
-// Resident blocks per SM the register allocation is sized for: about 900
-// threads per SM up to k = 6 (72-80 registers), fewer for the longer lines
-// of k >= 7 so that they do not spill; the shared memory of that many blocks
-// fits as well.
 __device__ __forceinline__ void f32_prefetch_bulk_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
@@ -82,12 +78,20 @@ __device__ __forceinline__ void f32_cp_async4(float* s, const float* g) {
 }
 __device__ __forceinline__ void f32_cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-__host__ __device__ constexpr int f32_min_blocks(int k, int C) {
-  return (k <= 6 ? 900 : 700) / (C * k * k) > 0 ? (k <= 6 ? 900 : 700) / (C * k * k) : 1;
+// Resident blocks per SM the register allocation is sized for: about 900
+// threads per SM up to k = 6 (72-80 registers), fewer for the longer lines
+// of k >= 7 so that they do not spill; 1000 for advection, whose smaller
+// kernel fits 56 registers without spilling (k = 5: five blocks of 200
+// threads, 5% faster than four); the shared memory of that many blocks fits
+// as well.
+__host__ __device__ constexpr int f32_min_blocks(int k, int C, int op) {
+  return (op == OP_ADV ? 1000 : k <= 6 ? 900 : 700) / (C * k * k) > 0
+             ? (op == OP_ADV ? 1000 : k <= 6 ? 900 : 700) / (C * k * k)
+             : 1;
 }
 
 template <int K, int C, int GEO, int OP>
-__global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C))
+__global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
     apply_f32_kernel(const __grid_constant__ ApplyParams<float> P) {
   using Sh = F32Shape<K, C>;
   constexpr int K2 = Sh::K2, K3 = Sh::K3, XS = Sh::XS, YS = Sh::YS, NP = Sh::NP, NT = Sh::NT;
@@ -946,7 +950,7 @@ cudaError_t launch_f32_one(const ApplyLaunch& L, int64_t n_cells) {
     if (e != cudaSuccess) return e;
     // shared-memory carveout for the intended resident blocks (percent of
     // the 228 KB maximum); the rest of the unified cache stays L1
-    const int want = f32_min_blocks(K, C) * (smem + 1024);
+    const int want = f32_min_blocks(K, C, OP) * (smem + 1024);
     const int pct = want >= 228 * 1024 ? 100 : (want * 100 + 228 * 1024 - 1) / (228 * 1024);
     e = cudaFuncSetAttribute(apply_f32_kernel<K, C, GEO, OP>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     if (e != cudaSuccess) return e;
