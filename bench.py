@@ -714,17 +714,24 @@ def main():
                                        "alu_tflops": tf32, "alu_peak_tflops": FP32_PEAK_TFLOPS}}
         op32.close()
         # emulated FP64 (double-float on the FP32 pipe), same workload and vectors
-        ope = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64emu", coeff=w["coeff"], **common)
-        for _ in range(args.warmup):
-            ope.apply(src, dst)
-        tote, le = time_applies(torch, ope, src, dst, args.steps)
+        emu = {}
+        for mode in (("element", "loop") if loop else ("element",)):
+            ope = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64emu", coeff=w["coeff"], **common)
+            ope.set_face_mode(mode)
+            for _ in range(args.warmup):
+                ope.apply(src, dst)
+            emu[mode], _ = time_applies(torch, ope, src, dst, args.steps)
+            ope.close()
+        best = min(emu, key=emu.get)
+        tote = emu[best]
         extras["fp64_emulated"] = {
             "value": n / (tote / args.steps / 1e3), "unit": UNIT, "ms_per_step": tote / args.steps,
+            "face_mode": best,
+            "ms_per_step_by_face_mode": {m: t / args.steps for m, t in emu.items()},
             "arithmetic": "double-float (pairs of binary32, error-free transformations) on the FP32 pipe; "
                           "FP64 vectors; parity with the FP64 oracle at 1e-12",
             "speedup_vs_fp64": (total_ms / args.steps) / (tote / args.steps),
-            "hbm": {"achieved": bpd * n / (le / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}}
-        ope.close()
+            "hbm": {"achieved": bpd * n / (tote / args.steps / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}}
         # advection, FP64
         opa = dgp.Operator(mesh["n"], p, geom=w["geom"], op="advection", prec="fp64", **common)
         if loop:

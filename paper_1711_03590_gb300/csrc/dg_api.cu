@@ -1588,8 +1588,8 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
 dg_status dg_set_face_mode(dg_handle* h, int mode) {
   if (!h) return DG_ERR_ARG;
   if (mode != DG_FACE_ELEMENT && mode != DG_FACE_LOOP) return fail(h, DG_ERR_ARG, "unknown face mode");
-  if (mode == DG_FACE_LOOP && h->prec != DG_FP64)
-    return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply is implemented for DG_FP64");
+  if (mode == DG_FACE_LOOP && h->prec == DG_FP32)
+    return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply is implemented for DG_FP64 and DG_FP64_EMU");
   if (mode == DG_FACE_LOOP && !h->split.tq) {
     // traces per face and slot, gradient-test fields per point
     const int k2 = h->k * h->k;

@@ -776,7 +776,7 @@ namespace dg {
 
 template <int K>
 cudaError_t launch_apply(const ApplyLaunch& L, int64_t n_cells) {
-  if (L.prec == 0 && L.face_mode != 0) return launch_apply_split<K>(L);
+  if (L.prec != 1 && L.face_mode != 0) return launch_apply_split<K>(L);
   if (L.prec == 0) return launch_prec<K, double>(L, n_cells);
   if (L.prec == 1) return launch_apply_f32<K>(L, n_cells);
   return launch_prec<K, df64>(L, n_cells);

@@ -33,6 +33,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 namespace dg {
 
@@ -56,18 +57,38 @@ __device__ __forceinline__ int split_face_id(const int ijk[3], int d, int s, con
   return pos + Pd * (it1 + nt1 * it2);
 }
 
-// Step 1: sweeps, own traces, q-point operation.
-template <int K, int GEO, int OP>
+// Shared tables of the double-float kernels (rolled loops read their
+// matrices from shared memory): E_0, E_1, W, S, D.
+template <int K>
+__host__ __device__ constexpr int split_table_scalars() {
+  return 3 * K + 2 * K * K;
+}
+
+// Step 1: sweeps, own traces, q-point operation.  T: double (binary64) or
+// df64 (double-float on the FP32 pipe; vectors, traces and gradient-test
+// fields are stored as 8-byte values either way).
+template <int K, typename T, int GEO, int OP>
 __global__ void __launch_bounds__(Shape<K>::max_threads)
-    split_cell_forward(const __grid_constant__ ApplyParams<double> P, const __grid_constant__ SplitArrays SA) {
-  using T = double;
+    split_cell_forward(const __grid_constant__ ApplyParams<T> P, const __grid_constant__ SplitArrays SA) {
+  using A = Arith<T>;
   constexpr int K2 = K * K, K3 = K2 * K;
   constexpr int NTR = SplitFields<OP>::NTR;
-  constexpr bool kEO = K >= 5;
+  constexpr bool kCompact = std::is_same<T, df64>::value;
+  constexpr bool kEO = !kCompact && K >= 5;
+  constexpr int kUq = kCompact ? 1 : K;  // unroll of the sweep output loops
+  constexpr int kUz = kCompact ? 1 : K;  // unroll of the q-point loop
+  constexpr int kUd = kCompact ? 1 : 3;  // unroll of the trace-direction loop
   const int C = P.C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3]
   T* G = U + C * K3;                      // [3][C][K3]
+  T* sE = G + 3 * C * K3;                 // [2][K] (double-float only)
+  T* sW = sE + 2 * K;                     // [K]
+  T* sS = sW + K;                         // [K][K]
+  T* sD = sS + K2;                        // [K][K]
+  T* const tr_out[3] = {reinterpret_cast<T*>(SA.tr[0]), reinterpret_cast<T*>(SA.tr[1]),
+                        reinterpret_cast<T*>(SA.tr[2])};
+  T* const tq_out = reinterpret_cast<T*>(SA.tq);
   const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
   const int tid = threadIdx.x;
@@ -90,15 +111,28 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
     ijk[1] = (int)(q % (unsigned)gm.n[1]);
     ijk[2] = (int)(q / (unsigned)gm.n[1]);
   }
-  for (int i = tid; i < nloc * K3; i += blockDim.x) U[i] = P.src[cell0 * K3 + i];
+  for (int i = tid; i < nloc * K3; i += blockDim.x) U[i] = A::load(P.src + cell0 * K3 + i);
+  if constexpr (kCompact) {
+    if (tid < 2 * K) sE[tid] = tb.E[tid / K][tid % K];
+    if (tid < K) sW[tid] = tb.W[tid];
+    for (int i = tid; i < K2; i += blockDim.x) {
+      sS[i] = tb.S[i];
+      sD[i] = tb.D[i];
+    }
+  }
   __syncthreads();
+  const T* mS = kCompact ? sS : tb.S;
+  const T* mD = kCompact ? sD : tb.D;
+  const T* mE0 = kCompact ? sE : tb.E[0];
+  const T* mE1 = kCompact ? sE + K : tb.E[1];
+  const T* mW = kCompact ? sW : tb.W;
   auto sweep_S = [&](int base, int stride) {
     if constexpr (kEO) eo_apply<K, EO_S>(tb, Uc, base, stride);
-    else line_apply<K, false, K>(tb.S, Uc, base, stride);
+    else line_apply<K, false, kUq>(mS, Uc, base, stride);
   };
   auto sweep_D = [&](int base, int stride, T* out) {
     if constexpr (kEO) eo_derivative_to<K>(tb, Uc, base, stride, out, base, stride);
-    else line_apply_to<K, K>(tb.D, Uc, base, stride, out, base, stride);
+    else line_apply_to<K, kUq>(mD, Uc, base, stride, out, base, stride);
   };
   if (active) sweep_S(K * (la + K * lb), 1);
   __syncthreads();
@@ -118,7 +152,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
 
   // own traces on the six faces: this cell is slot 1 of its lower face
   // (s = 0) and slot 0 of its upper face (s = 1)
-#pragma unroll
+#pragma unroll(kUd)
   for (int d = 0; d < 3; ++d) {
     const int base = line_base<K>(d, la, lb);
     const int strd = d == 0 ? 1 : d == 1 ? K : K2;
@@ -139,7 +173,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
       for (int f = 0; f < NTR; ++f) v[f] = T(0);
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        const T e = tb.E[s][j];
+        const T e = s ? mE1[j] : mE0[j];
         v[0] = fma(e, lu[j], v[0]);
         if (OP == OP_SIPG) {
 #pragma unroll
@@ -147,15 +181,15 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
         }
       }
       const int fid = split_face_id(ijk, d, s, gm.n, gm.P, gm.periodic);
-      T* out = SA.tr[d] + ((int64_t)(fid * 2 + (1 - s)) * NTR) * K2 + ln;
+      T* out = (d == 0 ? tr_out[0] : d == 1 ? tr_out[1] : tr_out[2]) + ((int64_t)(fid * 2 + (1 - s)) * NTR) * K2 + ln;
 #pragma unroll
       for (int f = 0; f < NTR; ++f) out[f * K2] = v[f];
     }
   }
 
   // q-point operation: the gradient-test fields t_c at the Gauss points
-  const T wa = tb.W[la], wb = tb.W[lb];
-#pragma unroll
+  const T wa = mW[la], wb = mW[lb];
+#pragma unroll(kUz)
   for (int z = 0; z < K; ++z) {
     const int pt = la + K * (lb + K * z);
     const int64_t qi = cell * K3 + pt;
@@ -163,7 +197,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
     if (OP == OP_SIPG) {
       const T g0 = G0[pt], g1 = G1[pt], g2 = G2[pt];
       if (GEO == GEO_CART) {
-        T w = wa * wb * tb.W[z] * gm.cart_detj;
+        T w = wa * wb * mW[z] * gm.cart_detj;
         if (gm.kq) w *= gm.kq[ijk[0] * K + la];
         t0 = w * gm.cart_jinv[0] * gm.cart_jinv[0] * g0;
         t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
@@ -194,7 +228,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
       const T uq = Uc[pt];
       T b0, b1, b2;
       if (GEO == GEO_CART) {
-        const T w = -wa * wb * tb.W[z] * gm.cart_detj;
+        const T w = -(wa * wb * mW[z] * gm.cart_detj);
         b0 = w * gm.cart_jinv[0] * gm.vel[0];
         b1 = w * gm.cart_jinv[1] * gm.vel[1];
         b2 = w * gm.cart_jinv[2] * gm.vel[2];
@@ -219,9 +253,9 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
       t1 = b1 * uq;
       t2 = b2 * uq;
     }
-    SA.tq[qi] = t0;
-    SA.tq[gm.ncq + qi] = t1;
-    SA.tq[2 * gm.ncq + qi] = t2;
+    tq_out[qi] = t0;
+    tq_out[gm.ncq + qi] = t1;
+    tq_out[2 * gm.ncq + qi] = t2;
   }
 }
 
@@ -231,11 +265,10 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
 // reference gradient; the other slot's are read only if `interior`).  Writes
 // the value test and (SIPG) the reference-gradient test of slot so to
 // ft[0], ft[fs], ft[2 fs], ft[3 fs].
-template <int K, int GEO, int OP>
-__device__ __forceinline__ void split_slot_flux(const Tables<double>& tb, const Geometry<double>& gm, int d,
-                                                int64_t fid, int pos, int it1, int fp, int so, bool interior,
-                                                const double (&u)[2], const double (&g)[2][3], double* ft, int fs) {
-  using T = double;
+template <int K, typename T, int GEO, int OP>
+__device__ __forceinline__ void split_slot_flux(const T* W, const Geometry<T>& gm, int d, int64_t fid, int pos,
+                                                int it1, int fp, int so, bool interior, const T (&u)[2],
+                                                const T (&g)[2][3], T* ft, int fs) {
   constexpr int K2 = K * K;
   const int la = fp % K, lb = fp / K;
   const int sn = 1 - so;
@@ -252,7 +285,7 @@ __device__ __forceinline__ void split_slot_flux(const Tables<double>& tb, const 
       }
       T kap = T(1);
       if (gm.kq) kap = d == 0 ? gm.kf[pos] : gm.kq[it1 * K + la];
-      fjxw = kap * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
+      fjxw = kap * W[la] * W[lb] * gm.cart_detj * cjd;
       tau = gm.cart_tau[d];
     } else {
       const T* f = gm.face[d] + fid * K2 + fp;
@@ -282,7 +315,7 @@ __device__ __forceinline__ void split_slot_flux(const Tables<double>& tb, const 
     for (int c = 0; c < 3; ++c) ft[(1 + c) * fs] = tg * jo[c];
   } else {
     T cn;
-    if (GEO == GEO_CART) cn = gm.vel[d] * tb.W[la] * tb.W[lb] * gm.cart_detj * cjd;
+    if (GEO == GEO_CART) cn = gm.vel[d] * W[la] * W[lb] * gm.cart_detj * cjd;
     else cn = gm.face[d][fid * K2 + fp];
     const T cno = so == 0 ? cn : -cn;  // c.n da w with n this side's outward normal
     ft[0] = interior ? T(0.5) * cno * (u[so] + u[sn]) + T(0.5) * fabs(cno) * (u[so] - u[sn]) : fabs(cno) * u[so];
@@ -291,18 +324,29 @@ __device__ __forceinline__ void split_slot_flux(const Tables<double>& tb, const 
 
 // Step 2: the numerical flux of this cell's slot on its six faces from both
 // slots' traces, injection of the test coefficients, integration, dst.
-template <int K, int GEO, int OP>
+template <int K, typename T, int GEO, int OP>
 __global__ void __launch_bounds__(Shape<K>::max_threads)
-    split_cell_backward(const __grid_constant__ ApplyParams<double> P, const __grid_constant__ SplitArrays SA) {
-  using T = double;
+    split_cell_backward(const __grid_constant__ ApplyParams<T> P, const __grid_constant__ SplitArrays SA) {
+  using A = Arith<T>;
   constexpr int K2 = K * K, K3 = K2 * K;
   constexpr int NTR = SplitFields<OP>::NTR, NFT = SplitFields<OP>::NFT;
-  constexpr bool kEO = K >= 5;
+  constexpr bool kCompact = std::is_same<T, df64>::value;
+  constexpr bool kEO = !kCompact && K >= 5;
+  constexpr int kUq = kCompact ? 1 : K;  // unroll of the sweep output loops
+  constexpr int kUz = kCompact ? 1 : K;  // unroll of the injection loop
+  constexpr int kUd = kCompact ? 1 : 3;  // unroll of the face-direction loop
   const int C = P.C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // [C][K3]
   T* G = U + C * K3;                      // [3][C][K3]
   T* FT = G + 3 * C * K3;                 // [C][3][2][NFT][K2]: test coefficients of the six faces
+  T* sE = FT + C * 6 * NFT * K2;          // [2][K] (double-float only)
+  T* sW = sE + 2 * K;                     // [K]
+  T* sS = sW + K;                         // [K][K]
+  T* sD = sS + K2;                        // [K][K]
+  const T* const tr_in[3] = {reinterpret_cast<const T*>(SA.tr[0]), reinterpret_cast<const T*>(SA.tr[1]),
+                             reinterpret_cast<const T*>(SA.tr[2])};
+  const T* const tq_in = reinterpret_cast<const T*>(SA.tq);
   const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
   const int tid = threadIdx.x;
@@ -319,10 +363,24 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
   T* G2 = G + (2 * C + lc) * K3;
   for (int i = tid; i < nloc * K3; i += blockDim.x) {
     const int64_t q = cell0 * K3 + i;
-    G[i] = SA.tq[q];
-    G[C * K3 + i] = SA.tq[gm.ncq + q];
-    G[2 * C * K3 + i] = SA.tq[2 * gm.ncq + q];
+    G[i] = tq_in[q];
+    G[C * K3 + i] = tq_in[gm.ncq + q];
+    G[2 * C * K3 + i] = tq_in[2 * gm.ncq + q];
   }
+  if constexpr (kCompact) {
+    if (tid < 2 * K) sE[tid] = tb.E[tid / K][tid % K];
+    if (tid < K) sW[tid] = tb.W[tid];
+    for (int i = tid; i < K2; i += blockDim.x) {
+      sS[i] = tb.S[i];
+      sD[i] = tb.D[i];
+    }
+  }
+  const T* mS = kCompact ? sS : tb.S;
+  const T* mD = kCompact ? sD : tb.D;
+  const T* mE0 = kCompact ? sE : tb.E[0];
+  const T* mE1 = kCompact ? sE + K : tb.E[1];
+  const T* mW = kCompact ? sW : tb.W;
+  if constexpr (kCompact) __syncthreads();  // the shared tables are read below
   if (active) {
     int ijk[3];
     const unsigned c = (unsigned)cell;
@@ -331,9 +389,9 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
     ijk[1] = (int)(q % (unsigned)gm.n[1]);
     ijk[2] = (int)(q / (unsigned)gm.n[1]);
     // this cell's slot of face (d, s) is 1 - s
-#pragma unroll
+#pragma unroll(kUd)
     for (int d = 0; d < 3; ++d) {
-#pragma unroll
+#pragma unroll(kUd == 1 ? 1 : 2)
       for (int s = 0; s < 2; ++s) {
         const int fid = split_face_id(ijk, d, s, gm.n, gm.P, gm.periodic);
         T* dst = FT + (((lc * 3 + d) * 2 + s) * NFT) * K2 + ln;
@@ -346,22 +404,22 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl) {
           if (sl == s && !interior) continue;  // slot s is the neighbour's
-          const T* tr = SA.tr[d] + ((int64_t)fid * 2 + sl) * NTR * K2 + ln;
+          const T* tr = (d == 0 ? tr_in[0] : d == 1 ? tr_in[1] : tr_in[2]) + ((int64_t)fid * 2 + sl) * NTR * K2 + ln;
           u[sl] = tr[0];
           if (OP == OP_SIPG) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) g[sl][c] = tr[(1 + c) * K2];
           }
         }
-        split_slot_flux<K, GEO, OP>(tb, gm, d, fid, pos, it1, ln, 1 - s, interior, u, g, dst, K2);
+        split_slot_flux<K, T, GEO, OP>(mW, gm, d, fid, pos, it1, ln, 1 - s, interior, u, g, dst, K2);
       }
     }
   }
   __syncthreads();
   if (active) {
-    const T e0a = tb.E[0][la], e1a = tb.E[1][la], e0b = tb.E[0][lb], e1b = tb.E[1][lb];
+    const T e0a = mE0[la], e1a = mE1[la], e0b = mE0[lb], e1b = mE1[lb];
     const T* ftc = FT + lc * 6 * NFT * K2;
-#pragma unroll
+#pragma unroll(kUz)
     for (int z = 0; z < K; ++z) {
       const int pt = la + K * (lb + K * z);
       // x faces at (y=lb, z), y faces at (x=la, z), z faces at (x=la, y=lb)
@@ -371,7 +429,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
       const T* fy1 = ftc + (1 * 2 + 1) * NFT * K2 + la + K * z;
       const T* fz0 = ftc + (2 * 2 + 0) * NFT * K2 + la + K * lb;
       const T* fz1 = ftc + (2 * 2 + 1) * NFT * K2 + la + K * lb;
-      const T ez0 = tb.E[0][z], ez1 = tb.E[1][z];
+      const T ez0 = mE0[z], ez1 = mE1[z];
       auto inj = [&](int f) {
         T a = e0a * fx0[f * K2];
         a = fma(e1a, fx1[f * K2], a);
@@ -391,11 +449,11 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
   __syncthreads();
   auto sweep_DT = [&](const T* t, int base, int stride) {
     if constexpr (kEO) eo_add_derivative_transposed<K>(tb, t, Uc, base, stride);
-    else line_add_transposed<K, K>(tb.D, t, Uc, base, stride);
+    else line_add_transposed<K, kUq>(mD, t, Uc, base, stride);
   };
   auto sweep_ST = [&](int base, int stride) {
     if constexpr (kEO) eo_apply<K, EO_ST>(tb, Uc, base, stride);
-    else line_apply<K, true, K>(tb.S, Uc, base, stride);
+    else line_apply<K, true, kUq>(mS, Uc, base, stride);
   };
   if (active) sweep_DT(G0, K * (la + K * lb), 1);
   __syncthreads();
@@ -416,11 +474,11 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
     double acc = 0.0;
     const bool dot = P.dot_partial != nullptr;
     for (int i = tid; i < nloc * K3; i += blockDim.x) {
-      o[i] = U[i];
-      if (dot) acc += U[i] * s[i];
+      A::store(o + i, U[i]);
+      if (dot) acc += A::to_double(U[i]) * s[i];
     }
     if (dot) {
-      double* red = G;  // free now
+      double* red = reinterpret_cast<double*>(G);  // free now
       red[tid] = acc;
       __syncthreads();
       if (tid == 0) {
@@ -432,17 +490,21 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
   }
 }
 
-// Shared-memory bytes of the split kernels (C cells per block).
-__host__ __device__ constexpr int split_smem_forward(int k, int C) { return 4 * C * k * k * k * 8; }
+// Shared-memory bytes of the split kernels (C cells per block; 8-byte
+// scalars, plus the double-float kernels' tables).
+__host__ __device__ constexpr int split_smem_forward(int k, int C) {
+  return (4 * C * k * k * k + 3 * k + 2 * k * k) * 8;
+}
 __host__ __device__ constexpr int split_smem_backward(int k, int op, int C) {
-  return (4 * C * k * k * k + C * 6 * (op == OP_SIPG ? 4 : 1) * k * k) * 8;
+  return (4 * C * k * k * k + C * 6 * (op == OP_SIPG ? 4 : 1) * k * k + 3 * k + 2 * k * k) * 8;
 }
 
-template <int K, int GEO, int OP>
+template <int K, typename T, int GEO, int OP>
 cudaError_t launch_split(const ApplyLaunch& L) {
-  ApplyParams<double> P;
-  P.tab = *static_cast<const Tables<double>*>(L.tables);
-  P.geo = *static_cast<const Geometry<double>*>(L.geometry);
+  static_assert(sizeof(T) == 8, "traces and gradient-test fields are 8-byte scalars");
+  ApplyParams<T> P;
+  P.tab = *static_cast<const Tables<T>*>(L.tables);
+  P.geo = *static_cast<const Geometry<T>*>(L.geometry);
   P.src = static_cast<const double*>(L.src);
   P.dst = static_cast<double*>(L.dst);
   P.dot_partial = L.dot_partial;
@@ -453,11 +515,11 @@ cudaError_t launch_split(const ApplyLaunch& L) {
   const SplitArrays SA = *static_cast<const SplitArrays*>(L.split);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(split_cell_forward<K, GEO, OP>,
+    cudaError_t e = cudaFuncSetAttribute(split_cell_forward<K, T, GEO, OP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          split_smem_forward(K, cells_per_block(K)));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(split_cell_backward<K, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(split_cell_backward<K, T, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                split_smem_backward(K, OP, cells_per_block(K)));
     if (e != cudaSuccess) return e;
     configured = true;
@@ -465,22 +527,29 @@ cudaError_t launch_split(const ApplyLaunch& L) {
   const int64_t grid = (L.cell_end - L.cell_begin + C - 1) / C;
   if (grid <= 0) return cudaSuccess;
   if (L.split_stage != 2)
-    split_cell_forward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_forward(K, C), L.stream>>>(P, SA);
+    split_cell_forward<K, T, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_forward(K, C), L.stream>>>(P, SA);
   if (L.split_stage != 1)
-    split_cell_backward<K, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_backward(K, OP, C), L.stream>>>(P, SA);
+    split_cell_backward<K, T, GEO, OP>
+        <<<(unsigned)grid, C * K * K, split_smem_backward(K, OP, C), L.stream>>>(P, SA);
   return cudaGetLastError();
 }
 
+template <int K, typename T>
+cudaError_t launch_apply_split_t(const ApplyLaunch& L) {
+  if (L.op == OP_SIPG) {
+    if (L.geo == GEO_CART) return launch_split<K, T, GEO_CART, OP_SIPG>(L);
+    if (L.geo == GEO_FULL) return launch_split<K, T, GEO_FULL, OP_SIPG>(L);
+    return launch_split<K, T, GEO_MERGED, OP_SIPG>(L);
+  }
+  if (L.geo == GEO_CART) return launch_split<K, T, GEO_CART, OP_ADV>(L);
+  if (L.geo == GEO_FULL) return launch_split<K, T, GEO_FULL, OP_ADV>(L);
+  return launch_split<K, T, GEO_MERGED, OP_ADV>(L);
+}
+
+// Binary64 (prec 0) and double-float (prec 2) face loops.
 template <int K>
 cudaError_t launch_apply_split(const ApplyLaunch& L) {
-  if (L.op == OP_SIPG) {
-    if (L.geo == GEO_CART) return launch_split<K, GEO_CART, OP_SIPG>(L);
-    if (L.geo == GEO_FULL) return launch_split<K, GEO_FULL, OP_SIPG>(L);
-    return launch_split<K, GEO_MERGED, OP_SIPG>(L);
-  }
-  if (L.geo == GEO_CART) return launch_split<K, GEO_CART, OP_ADV>(L);
-  if (L.geo == GEO_FULL) return launch_split<K, GEO_FULL, OP_ADV>(L);
-  return launch_split<K, GEO_MERGED, OP_ADV>(L);
+  return L.prec == 0 ? launch_apply_split_t<K, double>(L) : launch_apply_split_t<K, df64>(L);
 }
 
 }  // namespace dg
