@@ -1318,7 +1318,8 @@ dg_status dg_info(const dg_handle* h, dg_info_t* info) {
   info->cells_per_block = h->cpb;
   info->threads_per_block = h->cpb * h->k * h->k;
   info->shared_bytes_per_block = h->prec == DG_FP32 ? dg::f32_smem_bytes(h->k, h->op, h->cpb)
-                                                    : dg::smem_bytes_per_block(h->k, h->op, 8, h->cpb);
+                                 : h->face_mode == DG_FACE_LOOP ? dg::split_smem_backward(h->k, h->op, h->cpb)
+                                                                : dg::smem_bytes_per_block(h->k, h->op, 8, h->cpb);
   info->blocks = apply_blocks(h);
   const std::vector<int> tc = tile_choices(h);
   for (int i = 0; i < 24; ++i) info->tile_choices[i] = i < (int)tc.size() ? tc[i] : 0;
@@ -1605,6 +1606,11 @@ dg_status dg_set_face_mode(dg_handle* h, int mode) {
     if ((st = dev_alloc(h, (void**)&h->split.tq, sizeof(double) * 3 * h->n_dofs)) != DG_OK) return st;
     DG_CUDA(h, cudaStreamSynchronize(h->stream));
   }
+  // an unchanged default tile shape follows the mode's default
+  const int def_old = h->face_mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec)
+                                                    : dg::cells_per_block(h->k);
+  if (h->prec != DG_FP32 && h->cpb == def_old)
+    h->cpb = mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec) : dg::cells_per_block(h->k);
   h->face_mode = mode;
   return DG_OK;
 }
@@ -1620,7 +1626,8 @@ dg_status dg_set_cells_per_block(dg_handle* h, int cpb) {
     h->cpb = cpb;
     return DG_OK;
   }
-  if (cpb == 0) cpb = dg::cells_per_block(h->k);
+  if (cpb == 0)
+    cpb = h->face_mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec) : dg::cells_per_block(h->k);
   if (cpb < 1 || cpb > dg::cells_per_block(h->k))
     return fail(h, DG_ERR_ARG, "cells per block must be in 1.." + std::to_string(dg::cells_per_block(h->k)));
   h->cpb = cpb;

@@ -490,15 +490,6 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
   }
 }
 
-// Shared-memory bytes of the split kernels (C cells per block; 8-byte
-// scalars, plus the double-float kernels' tables).
-__host__ __device__ constexpr int split_smem_forward(int k, int C) {
-  return (4 * C * k * k * k + 3 * k + 2 * k * k) * 8;
-}
-__host__ __device__ constexpr int split_smem_backward(int k, int op, int C) {
-  return (4 * C * k * k * k + C * 6 * (op == OP_SIPG ? 4 : 1) * k * k + 3 * k + 2 * k * k) * 8;
-}
-
 template <int K, typename T, int GEO, int OP>
 cudaError_t launch_split(const ApplyLaunch& L) {
   static_assert(sizeof(T) == 8, "traces and gradient-test fields are 8-byte scalars");

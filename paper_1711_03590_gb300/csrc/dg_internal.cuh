@@ -107,6 +107,23 @@ __host__ __device__ constexpr int cells_per_block(int k) {
   return k == 2 ? 64 : k == 3 ? 28 : k == 4 ? 16 : k == 5 ? 10 : k == 6 ? 7 : k == 7 ? 5 : k == 8 ? 4 : 3;
 }
 
+// Default cells per block of the face-loop kernels (binary64, prec 0;
+// double-float, prec 2), from a sweep of 1 .. cells_per_block(k) on the 32^3
+// deformed mesh (G3 SIPG) on GB300; any value 1 .. cells_per_block(k) is valid.
+__host__ __device__ constexpr int split_cells_per_block(int k, int prec) {
+  return prec == 0 ? (k <= 3 ? 24 : k == 4 ? 8 : k == 5 ? 5 : k == 6 ? 6 : k == 7 ? 5 : 3)
+                   : (k == 2 ? 24 : k == 3 ? 10 : k == 4 ? 4 : k == 5 ? 5 : k == 6 ? 3 : k == 7 ? 5 : 1);
+}
+
+// Shared-memory bytes of the face-loop kernels (C cells per block; 8-byte
+// scalars, plus the double-float kernels' tables).
+__host__ __device__ constexpr int split_smem_forward(int k, int C) {
+  return (4 * C * k * k * k + 3 * k + 2 * k * k) * 8;
+}
+__host__ __device__ constexpr int split_smem_backward(int k, int op, int C) {
+  return (4 * C * k * k * k + C * 6 * (op == OP_SIPG ? 4 : 1) * k * k + 3 * k + 2 * k * k) * 8;
+}
+
 // Cell-block width of the binary32 kernel's cell geometry layout (the largest
 // of its compiled tile shapes, which all divide it).
 __host__ __device__ constexpr int f32_geometry_block(int k) {

@@ -129,3 +129,22 @@ def test_emulated_face_loop_cg():
     assert float((x1 - x2).norm() / x2.norm()) < 1e-8
     o.close()
     ref.close()
+
+
+def test_face_mode_tile_defaults():
+    """Selecting a face mode moves an unchanged default tile shape to that
+    mode's default and back; an explicitly chosen one stays."""
+    for prec in ("fp64", "fp64emu"):
+        o = dgp.Operator((4, 4, 4), 4, prec=prec)
+        elem = o.info()["cells_per_block"]
+        o.set_face_mode("loop")
+        loop = o.info()["cells_per_block"]
+        assert 1 <= loop <= elem
+        o.set_face_mode("element")
+        assert o.info()["cells_per_block"] == elem
+        o.set_cells_per_block(3)
+        o.set_face_mode("loop")
+        assert o.info()["cells_per_block"] == 3
+        o.set_cells_per_block(0)  # the mode's default
+        assert o.info()["cells_per_block"] == loop
+        o.close()
