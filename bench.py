@@ -127,6 +127,25 @@ def bytes_per_dof(k, s, op, geom):
     return vec + cell + face
 
 
+# DRAM traffic per apply (ncu dram__bytes_read.sum + dram__bytes_write.sum,
+# one capture each, all launches of the apply) of the 32^3 deformed p = 4 G3
+# SIPG workload, keyed by (arithmetic, face mode, degree, cells per block);
+# reported only for exactly that launch configuration, and to be re-taken
+# whenever the kernel changes.
+MEASURED_TRAFFIC = {
+    ("fp64", "loop", 4, 5): 1005.98e6,
+    ("fp64", "element", 4, 10): 556.6e6,
+    ("fp64emu", "element", 4, 10): 554.4e6,
+    ("fp32", "element", 4, 8): 234.4e6,
+}
+
+
+def measured_traffic(prec, face_mode, degree, cpb, workload):
+    if workload != "deformed_dirichlet_32^3_p%d" % degree:
+        return None
+    return MEASURED_TRAFFIC.get((prec, face_mode, degree, cpb))
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -648,12 +667,16 @@ def main():
                  "(the roofline is per apply)" % k)
     else:
         kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, {"fp64": "double", "fp64emu": "df64"}[args.prec])
+    traffic = measured_traffic(args.prec, "loop" if loop else "element", p, op.info()["cells_per_block"], wname)
+    tsrc = ("ncu capture of this launch configuration: dram__bytes_read.sum + dram__bytes_write.sum per apply"
+            if traffic else None)
     hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-           "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": kname, "bytes_per_dof": bpd,
-           "peak_source": peaks.get("source")}
+           "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc, "kernel": kname,
+           "bytes_per_dof": bpd, "algorithmic_bytes_per_launch": bpd * n, "peak_source": peaks.get("source")}
     if args.prec == "fp64":
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kname,
+                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic, "traffic_source": tsrc,
+                    "kernel": kname,
                     "flops_per_launch": flops,
                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
                     "hbm": hbm}
@@ -711,6 +734,9 @@ def main():
         extras["fp32"] = {"value": n / (tot32 / args.steps / 1e3), "unit": UNIT, "ms_per_step": tot32 / args.steps,
                           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                        "frac": gbs / peaks["hbm_gbs"], "bytes_per_dof": b32,
+                                       "traffic": measured_traffic("fp32", "element", p, op32.info()["cells_per_block"],
+                                                                   wname),
+                                       "kernel": "apply_f32_kernel<%d,%d,FULL,SIPG>" % (k, op32.info()["cells_per_block"]),
                                        "alu_tflops": tf32, "alu_peak_tflops": FP32_PEAK_TFLOPS}}
         op32.close()
         # emulated FP64 (double-float on the FP32 pipe), same workload and vectors
