@@ -4,8 +4,8 @@ Tolerances (norm-wise relative, |y_gpu - y_ref|_2 / |y_ref|_2): 1e-12 for
 FP64 arithmetic, 1e-5 for FP32 arithmetic.  Small meshes compare every
 entry with the oracle's cell-by-cell route; the 32^3 deformed workload
 compares sampled cells (boundary corners and a seeded sample) at full size,
-in the launch configurations the benchmark times (FP64 in both face modes,
-FP32, emulated FP64).
+in the launch configurations the benchmark times (FP64 and emulated FP64 in
+both face modes, FP32).
 """
 import numpy as np
 import pytest
@@ -21,7 +21,7 @@ if not torch.cuda.is_available():
 
 import paper_1711_03590_gb300 as dgp  # noqa: E402
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp64emu": 1e-12, "fp64-loop": 1e-12}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp64emu": 1e-12, "fp64-loop": 1e-12, "fp64emu-loop": 1e-12}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,9 +35,10 @@ def _rel(a, b):
 
 
 def _gpu_apply(mesh, p, geom, form, prec, u):
-    """The GPU apply; prec "fp64-loop" is the FP64 operator in face-loop mode."""
-    loop = prec == "fp64-loop"
-    prec = "fp64" if loop else prec
+    """The GPU apply; prec "<p>-loop" is the operator of arithmetic <p> in
+    face-loop mode."""
+    loop = prec.endswith("-loop")
+    prec = prec[:-len("-loop")] if loop else prec
     op = dgp.Operator(mesh["n"], p, geom=geom, op=form.get("op", "sipg"), prec=prec,
                       periodic=mesh.get("periodic", False), mapping=mesh.get("mapping", 0),
                       amplitude=mesh.get("amplitude", 0.1), coeff=form.get("coeff", 0),
@@ -96,13 +97,13 @@ def test_small_meshes_all_degrees(p, case, op):
     form = dict(op=op, coeff=1 if (op == "sipg" and case % 2 == 1) else 0, velocity=dg_inputs.VELOCITY)
     u = dg_inputs.src_vector(n, seed=100 + p)
     ref = oracle.apply(mesh, p, form, u)
-    for prec in ("fp64", "fp32", "fp64emu", "fp64-loop"):
+    for prec in ("fp64", "fp32", "fp64emu", "fp64-loop", "fp64emu-loop"):
         got = _gpu_apply(mesh, p, geom, form, prec, u)
         assert _rel(got, ref) < TOL[prec], (prec, _rel(got, ref))
 
 
 @pytest.mark.parametrize("p", [1, 2, 4, 8])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp64emu", "fp64-loop"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp64emu", "fp64-loop", "fp64emu-loop"])
 def test_full_size_deformed_sampled(p, prec):
     """32^3 deformed mesh, full per-point Jacobians, kappa variable,
     Dirichlet: full-size GPU apply, compared on sampled cells (all eight
