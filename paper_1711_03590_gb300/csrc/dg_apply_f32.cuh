@@ -79,14 +79,14 @@ __device__ __forceinline__ void f32_cp_async4(float* s, const float* g) {
 __device__ __forceinline__ void f32_cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Resident blocks per SM the register allocation is sized for: about 900
-// threads per SM up to k = 6 (72-80 registers), fewer for the longer lines
-// of k >= 7 so that they do not spill; 1000 for advection, whose smaller
-// kernel fits 56 registers without spilling (k = 5: five blocks of 200
-// threads, 5% faster than four); the shared memory of that many blocks fits
-// as well.
+// threads per SM up to k = 8 (72-80 registers without spills; at k = 7, 8
+// 7-13% faster than the 700 that the longer lines of k = 9 keep, which
+// spill otherwise); 1000 for advection, whose smaller kernel fits 56
+// registers without spilling (k = 5: five blocks of 200 threads, 5% faster
+// than four); the shared memory of that many blocks fits as well.
 __host__ __device__ constexpr int f32_min_blocks(int k, int C, int op) {
-  return (op == OP_ADV ? 1000 : k <= 6 ? 900 : 700) / (C * k * k) > 0
-             ? (op == OP_ADV ? 1000 : k <= 6 ? 900 : 700) / (C * k * k)
+  return (op == OP_ADV ? 1000 : k <= 8 ? 900 : 700) / (C * k * k) > 0
+             ? (op == OP_ADV ? 1000 : k <= 8 ? 900 : 700) / (C * k * k)
              : 1;
 }
 
