@@ -442,7 +442,8 @@ class Operator:
         dg_set_cells_per_block(self.handle, cpb)
 
     def set_face_mode(self, mode):
-        """"element" (fused kernel, default) or "loop" (each face once; FP64)."""
+        """"element" (fused kernel, default) or "loop" (two launches, the
+        neighbours' traces read from memory; FP64 and emulated FP64)."""
         dg_set_face_mode(self.handle, {"element": DG_FACE_ELEMENT, "loop": DG_FACE_LOOP}.get(mode, mode))
 
     def autotune(self):

@@ -277,7 +277,7 @@ struct dg_handle {
   // host-buffer apply staging, and the copy streams and events of its slab
   // pipeline (created on first use)
   void *stage_src, *stage_dst;
-  // face-loop variant of the binary64 apply (dg_set_face_mode)
+  // face evaluation of the binary64 / double-float apply (dg_set_face_mode)
   int face_mode;
   dg::SplitArrays split;
   cudaStream_t h2d_stream, d2h_stream, cmp_stream;
