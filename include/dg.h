@@ -149,12 +149,13 @@ dg_status dg_set_stream(dg_handle *h, void *stream);
 /* Tile shape of the apply kernel: cells per CUDA block (k^2 threads each).
  * Valid values are listed in dg_info_t.tile_choices: for DG_FP64 and
  * DG_FP64_EMU any value 1 .. floor(256 / k^2) (the autotuner tries a subset),
- * for DG_FP32 one of the two compiled shapes.  0 restores the default.
- * Results do not depend on it (each cell's arithmetic is the same); an
- * invalid value returns DG_ERR_ARG.  Synchronous. */
+ * for DG_FP32 one of the two compiled shapes.  0 restores the default
+ * (which for DG_FACE_LOOP is its own per-degree default).  Results do not
+ * depend on it (each cell's arithmetic is the same); an invalid value
+ * returns DG_ERR_ARG.  Synchronous. */
 dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
 
-/* Face evaluation of the DG_FP64 apply.  DG_FACE_ELEMENT (default): one
+/* Face evaluation of the DG_FP64 / DG_FP64_EMU apply.  DG_FACE_ELEMENT (default): one
  * fused kernel, every cell evaluates its six faces (the neighbour's traces
  * re-interpolated from its dofs).  DG_FACE_LOOP: two launches -- cells write
  * their own face traces (u and the reference gradient, per face and side) and
@@ -164,7 +165,9 @@ dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
  * -- trading memory traffic for FP64 arithmetic.  Same results up to
  * rounding.  DG_FACE_LOOP allocates its work arrays here: 24/k + 3 doubles
  * per dof for SIPG (62 bytes per dof at p = 4), 6/k + 3 for advection.
- * DG_FP64 and DG_FP64_EMU handles; DG_FP32: DG_ERR_UNSUPPORTED.
+ * DG_FP64 and DG_FP64_EMU handles; DG_FP32: DG_ERR_UNSUPPORTED.  A tile
+ * shape still at the previous mode's default moves to the new mode's
+ * default; one set with dg_set_cells_per_block or dg_autotune stays.
  * Synchronous. */
 typedef enum { DG_FACE_ELEMENT = 0, DG_FACE_LOOP = 1 } dg_face_mode;
 dg_status dg_set_face_mode(dg_handle *h, int mode);
