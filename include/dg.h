@@ -166,9 +166,8 @@ dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
  * rounding.  DG_FACE_LOOP allocates its work arrays here: 24/k + 3 doubles
  * per dof for SIPG (62 bytes per dof at p = 4), 6/k + 3 for advection.
  * DG_FP64 and DG_FP64_EMU handles; DG_FP32: DG_ERR_UNSUPPORTED.  A tile
- * shape still at the previous mode's default moves to the new mode's
- * default; one set with dg_set_cells_per_block or dg_autotune stays.
- * Synchronous. */
+ * shape equal to the previous mode's default moves to the new mode's
+ * default; any other stays.  Synchronous. */
 typedef enum { DG_FACE_ELEMENT = 0, DG_FACE_LOOP = 1 } dg_face_mode;
 dg_status dg_set_face_mode(dg_handle *h, int mode);
 
