@@ -111,7 +111,7 @@ __host__ __device__ constexpr int cells_per_block(int k) {
 // double-float, prec 2), from a sweep of 1 .. cells_per_block(k) on the 32^3
 // deformed mesh (G3 SIPG) on GB300; any value 1 .. cells_per_block(k) is valid.
 __host__ __device__ constexpr int split_cells_per_block(int k, int prec) {
-  return prec == 0 ? (k <= 3 ? 24 : k == 4 ? 8 : k == 5 ? 5 : k == 6 ? 6 : k == 7 ? 5 : 3)
+  return prec == 0 ? (k <= 3 ? 24 : k == 4 ? 8 : k == 5 ? 5 : k == 6 ? 7 : k == 7 ? 5 : 3)
                    : (k == 2 ? 24 : k == 3 ? 10 : k == 4 ? 4 : k == 5 ? 5 : k == 6 ? 3 : k == 7 ? 5 : 1);
 }
 
