@@ -1273,7 +1273,7 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   h->op = opts->op;
   h->n_cells = nc;
   h->n_dofs = nc * k * k * k;
-  h->cpb = h->prec == DG_FP32 ? dg::f32_tile_default(k) : dg::cells_per_block(k);
+  h->cpb = h->prec == DG_FP32 ? dg::f32_tile_default(k) : dg::element_cells_per_block(k, h->prec);
   h->stream = static_cast<cudaStream_t>(stream);
   build_tables(k, h->t64);
   h->tabd = cast_tables<double>(k, h->t64);
@@ -1608,9 +1608,10 @@ dg_status dg_set_face_mode(dg_handle* h, int mode) {
   }
   // an unchanged default tile shape follows the mode's default
   const int def_old = h->face_mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec)
-                                                    : dg::cells_per_block(h->k);
+                                                    : dg::element_cells_per_block(h->k, h->prec);
   if (h->prec != DG_FP32 && h->cpb == def_old)
-    h->cpb = mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec) : dg::cells_per_block(h->k);
+    h->cpb = mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec)
+                                  : dg::element_cells_per_block(h->k, h->prec);
   h->face_mode = mode;
   return DG_OK;
 }
@@ -1627,7 +1628,8 @@ dg_status dg_set_cells_per_block(dg_handle* h, int cpb) {
     return DG_OK;
   }
   if (cpb == 0)
-    cpb = h->face_mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec) : dg::cells_per_block(h->k);
+    cpb = h->face_mode == DG_FACE_LOOP ? dg::split_cells_per_block(h->k, h->prec)
+                                       : dg::element_cells_per_block(h->k, h->prec);
   if (cpb < 1 || cpb > dg::cells_per_block(h->k))
     return fail(h, DG_ERR_ARG, "cells per block must be in 1.." + std::to_string(dg::cells_per_block(h->k)));
   h->cpb = cpb;

@@ -107,12 +107,17 @@ __host__ __device__ constexpr int cells_per_block(int k) {
   return k == 2 ? 64 : k == 3 ? 28 : k == 4 ? 16 : k == 5 ? 10 : k == 6 ? 7 : k == 7 ? 5 : k == 8 ? 4 : 3;
 }
 
-// Default cells per block of the face-loop kernels (binary64, prec 0;
-// double-float, prec 2), from a sweep of 1 .. cells_per_block(k) on the 32^3
-// deformed mesh (G3 SIPG) on GB300; any value 1 .. cells_per_block(k) is valid.
+// Default cells per block of the element-centric kernel and of the
+// face-loop kernels (binary64, prec 0; double-float, prec 2), from sweeps of
+// 1 .. cells_per_block(k) on the 32^3 deformed mesh (G3 SIPG) on GB300; any
+// value 1 .. cells_per_block(k) is valid, and dg_autotune picks per operator.
+__host__ __device__ constexpr int element_cells_per_block(int k, int prec) {
+  return prec == 0 ? (k == 2 ? 8 : k == 3 ? 7 : k == 4 ? 8 : k == 5 ? 5 : k == 6 ? 6 : k == 7 ? 3 : k == 8 ? 2 : 3)
+                   : (k == 2 ? 16 : k == 3 ? 7 : k == 4 ? 8 : k == 5 ? 5 : k == 6 ? 6 : k == 7 ? 3 : k == 8 ? 2 : 3);
+}
 __host__ __device__ constexpr int split_cells_per_block(int k, int prec) {
   return prec == 0 ? (k <= 3 ? 24 : k == 4 ? 8 : k == 5 ? 5 : k == 6 ? 7 : k == 7 ? 5 : 3)
-                   : (k == 2 ? 24 : k == 3 ? 10 : k == 4 ? 4 : k == 5 ? 5 : k == 6 ? 3 : k == 7 ? 5 : 1);
+                   : (k == 2 ? 24 : k == 3 ? 7 : k == 4 ? 4 : k == 5 ? 5 : k == 6 ? 7 : k == 7 ? 5 : 1);
 }
 
 // Shared-memory bytes of the face-loop kernels (C cells per block; 8-byte
