@@ -571,6 +571,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp64emu"],
                     help="precision of the headline apply")
+    ap.add_argument("--cells-per-block", type=int, default=0,
+                    help="tile shape of the headline operator (0: the operator's default)")
     ap.add_argument("--face-mode", default="loop", choices=["loop", "element"],
                     help="FP64 face evaluation: face loop (neighbour traces read, not recomputed; faster on GB300) "
                          "or element-centric")
@@ -629,6 +631,9 @@ def main():
     loop = args.prec == "fp64" and args.face_mode == "loop"
     if loop:
         op.set_face_mode("loop")
+    if args.cells_per_block:
+        op.set_cells_per_block(args.cells_per_block)
+    cpb_used = op.info()["cells_per_block"]
     n = op.n_dofs
     n_cells = op.info()["n_cells"]
     ssz = 4 if args.prec == "fp32" else 8
@@ -786,6 +791,7 @@ def main():
                            "boundary": "Dirichlet", "coefficient": "1+0.5 sin(2 pi x)",
                            "l2_policy": "inputs larger than L2 (vector + geometry > 500 MB)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
+                           "cells_per_block": cpb_used,
                            "face_mode": ("face loop: two launches, neighbour traces read (dg_set_face_mode)"
                                          if loop else "element-centric fused kernel")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * (2 if loop else 1),
