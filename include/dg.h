@@ -163,8 +163,10 @@ dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
  * the flux tested on their own side, inject and integrate (the paper's
  * separate cell and face work, Algorithm 1 steps (ii)-(iv), without atomics)
  * -- trading memory traffic for FP64 arithmetic.  Same results up to
- * rounding.  DG_FACE_LOOP allocates its work arrays here: 24/k + 3 doubles
- * per dof for SIPG (62 bytes per dof at p = 4), 6/k + 3 for advection.
+ * rounding.  DG_FACE_LOOP allocates its work arrays here (on first use; they
+ * stay with the handle until dg_destroy): 24/k + 3 doubles per dof for SIPG
+ * (62 bytes per dof at p = 4), 6/k + 3 for advection.  DG_ERR_OOM if they do
+ * not fit (the mode is then unchanged).
  * DG_FP64 and DG_FP64_EMU handles; DG_FP32: DG_ERR_UNSUPPORTED.  A tile
  * shape equal to the previous mode's default moves to the new mode's
  * default; any other stays.  Synchronous. */

@@ -1595,15 +1595,24 @@ dg_status dg_set_face_mode(dg_handle* h, int mode) {
     // traces per face and slot, gradient-test fields per point
     const int k2 = h->k * h->k;
     const int nf = h->op == DG_OP_SIPG ? 4 : 1;
-    dg_status st;
-    for (int d = 0; d < 3; ++d) {
+    dg_status st = DG_OK;
+    for (int d = 0; d < 3 && st == DG_OK; ++d) {
       const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
       const int64_t faces = (int64_t)(h->mesh.periodic ? h->mesh.n[d] : h->mesh.n[d] + 1) * h->mesh.n[t1] *
                             h->mesh.n[t2];
       const size_t bytes = sizeof(double) * faces * 2 * nf * k2;
-      if ((st = dev_alloc(h, (void**)&h->split.tr[d], bytes)) != DG_OK) return st;
+      st = dev_alloc(h, (void**)&h->split.tr[d], bytes);
     }
-    if ((st = dev_alloc(h, (void**)&h->split.tq, sizeof(double) * 3 * h->n_dofs)) != DG_OK) return st;
+    if (st == DG_OK) st = dev_alloc(h, (void**)&h->split.tq, sizeof(double) * 3 * h->n_dofs);
+    if (st != DG_OK) {  // nothing half-allocated stays behind; the mode is unchanged
+      for (auto& p : h->split.tr) {
+        dev_free(h, p);
+        p = nullptr;
+      }
+      dev_free(h, h->split.tq);
+      h->split.tq = nullptr;
+      return st;
+    }
     DG_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   // an unchanged default tile shape follows the mode's default
