@@ -89,3 +89,23 @@ def test_even_odd_operation_count():
         if k >= 5:
             assert centro < k * k
     assert bench.even_odd_ops(5, False) == 21 and bench.even_odd_ops(5, True) == 20
+
+
+def test_flop_models_of_the_two_face_modes():
+    """The face loop's flop count (bench roofline) is below the
+    element-centric one at every degree: it drops the neighbour's
+    re-interpolation and evaluates each side's flux once; the even-odd form
+    lowers both from k = 5 on."""
+    import bench
+    for k in range(2, 10):
+        for op in ("sipg", "advection"):
+            for geom in ("full", "merged", "cartesian"):
+                for eo in (False, True):
+                    loop = bench.kernel_flops_per_cell_loop(k, op, geom, even_odd=eo)
+                    elem = bench.kernel_flops_per_cell(k, op, geom, even_odd=eo)
+                    assert 0 < loop < elem, (k, op, geom, eo)
+                if k >= 5:
+                    assert (bench.kernel_flops_per_cell_loop(k, op, geom, even_odd=True)
+                            < bench.kernel_flops_per_cell_loop(k, op, geom, even_odd=False))
+    # p = 4, G3 SIPG: 268 flop/dof with the even-odd sweeps
+    assert round(bench.kernel_flops_per_cell_loop(5, "sipg", "full", even_odd=True) / 125) == 268
