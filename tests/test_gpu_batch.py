@@ -20,6 +20,10 @@ CASES = [
     dict(n=(4, 4, 4), p=2, geom="merged", prec="fp64", periodic=True, mapping=1, coeff=0, op="advection"),
     dict(n=(4, 4, 4), p=5, geom="full", prec="fp32", periodic=True, mapping=1, coeff=1, op="sipg"),
     dict(n=(6, 6, 6), p=4, geom="full", prec="fp64", periodic=False, mapping=1, coeff=1, op="sipg"),
+    # face-loop operators (two launches each, work arrays per handle)
+    dict(n=(5, 6, 4), p=3, geom="full", prec="fp64", periodic=False, mapping=1, coeff=1, op="sipg", face="loop"),
+    dict(n=(4, 4, 4), p=5, geom="merged", prec="fp64emu", periodic=True, mapping=1, coeff=0, op="advection",
+         face="loop"),
 ]
 
 
@@ -30,6 +34,8 @@ def test_batch_equals_individual_applies(branches, autotune):
     for i, c in enumerate(CASES):
         op = dgp.Operator(c["n"], c["p"], geom=c["geom"], op=c["op"], prec=c["prec"], periodic=c["periodic"],
                           mapping=c["mapping"], coeff=c["coeff"])
+        if c.get("face"):
+            op.set_face_mode(c["face"])
         src = torch.tensor(dg_inputs.src_vector(op.n_dofs, 40 + i), dtype=op.dtype, device="cuda")
         refs.append(op.apply(src).clone())
         ops.append(op)
