@@ -1374,7 +1374,17 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
   const int nz = h->mesh.n[2];
   int slabs = (!h->mesh.periodic && plane % 64 == 0 && nz >= 4) ? std::min(kHostSlabs, nz / 2) : 1;
   const int64_t k3 = (int64_t)h->k * h->k * h->k;
-  auto cell_of_slab = [&](int s) { return plane * ((int64_t)nz * s / slabs); };
+  // slab boundaries in z-planes: one-plane first and last slabs (the
+  // pipeline's fill -- the first copy in -- and drain -- the last slab's
+  // compute and copy out -- are short), the planes between split evenly
+  auto plane_of_slab = [&](int s) -> int64_t {
+    if (slabs < 4) return (int64_t)nz * s / slabs;
+    if (s == 0) return 0;
+    if (s == slabs) return nz;
+    if (s == slabs - 1) return nz - 1;
+    return 1 + (int64_t)(nz - 2) * (s - 1) / (slabs - 2);
+  };
+  auto cell_of_slab = [&](int s) { return plane * plane_of_slab(s); };
   cudaEvent_t* ev_in = h->pipe_ev;              // slab s on the device
   cudaEvent_t* ev_out = h->pipe_ev + kHostSlabs;  // slab s computed
   cudaEvent_t ev_start = h->pipe_ev[2 * kHostSlabs], ev_cmp = h->pipe_ev[2 * kHostSlabs + 1];
