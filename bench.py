@@ -574,8 +574,8 @@ def main():
     ap.add_argument("--cells-per-block", type=int, default=0,
                     help="tile shape of the headline operator (0: the operator's default)")
     ap.add_argument("--face-mode", default="loop", choices=["loop", "element"],
-                    help="FP64 face evaluation: face loop (neighbour traces read, not recomputed; faster on GB300) "
-                         "or element-centric")
+                    help="FP64 / emulated-FP64 face evaluation: face loop (neighbour traces read, not recomputed; "
+                         "faster on GB300) or element-centric")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--solve-config3", action="store_true",
@@ -628,7 +628,7 @@ def main():
     peaks = load_peaks()
 
     op = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec=args.prec, coeff=w["coeff"], **common)
-    loop = args.prec == "fp64" and args.face_mode == "loop"
+    loop = args.prec in ("fp64", "fp64emu") and args.face_mode == "loop"
     if loop:
         op.set_face_mode("loop")
     if args.cells_per_block:
@@ -659,7 +659,7 @@ def main():
 
     # roofline of the apply (one kernel; the face loop: its two launches)
     if loop:
-        flops = kernel_flops_per_cell_loop(k, "sipg", w["geom"], even_odd=k >= 5) * n_cells
+        flops = kernel_flops_per_cell_loop(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5)) * n_cells
     else:
         flops = kernel_flops_per_cell(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5)) * n_cells
     achieved_tf = flops / (launch_ms / 1e3) / 1e12
@@ -668,8 +668,8 @@ def main():
     if args.prec == "fp32":
         kname = "apply_f32_kernel<%d,%d,FULL,SIPG>" % (k, op.info()["cells_per_block"])
     elif loop:
-        kname = ("face-loop apply <%d,FULL,SIPG>: split_cell_forward + split_cell_backward "
-                 "(the roofline is per apply)" % k)
+        kname = ("face-loop apply <%d,%s,FULL,SIPG>: split_cell_forward + split_cell_backward "
+                 "(the roofline is per apply)" % (k, {"fp64": "double", "fp64emu": "df64"}[args.prec]))
     else:
         kname = "apply_kernel<%d,%s,FULL,SIPG>" % (k, {"fp64": "double", "fp64emu": "df64"}[args.prec])
     traffic = measured_traffic(args.prec, "loop" if loop else "element", p, op.info()["cells_per_block"], wname)
@@ -699,11 +699,11 @@ def main():
         op.apply_host(hsrc, hdst)
     te = time.perf_counter() - te
     e2e = {"value": n / (te / e2e_steps), "unit": UNIT, "h2d_bytes_per_step": n * ssz, "d2h_bytes_per_step": n * ssz,
-           "call": "dg_apply_host", "face_mode": args.face_mode if args.prec == "fp64" else "element"}
+           "call": "dg_apply_host", "face_mode": "loop" if loop else "element"}
     op.close()
 
     fp64_element = None
-    if loop:
+    if loop and args.prec == "fp64":
         # the element-centric FP64 apply of the same workload: kernel-only,
         # and end to end; e2e reports the faster of the two public paths
         ope_ = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec="fp64", coeff=w["coeff"], **common)
