@@ -55,14 +55,16 @@ def even_odd_ops(k, anti):
     return 2 * h + h * (h2 + h + 2) + ((h if anti else h2) if k % 2 else 0)
 
 
-def kernel_flops_per_cell(k, op, geom, even_odd=False):
+def kernel_flops_per_cell(k, op, geom, even_odd=False, folded=False):
     """Floating-point work of one cell in the apply kernels as implemented,
     counted as 2 per arithmetic instruction (an FMA, or an add or multiply
     that takes an FMA slot of the pipe): tensor-product sweeps on the cell,
     the neighbour's face-normal and in-face interpolation, the own-side face
     traces and flux at every face point, the quadrature-point operation and
     the injection of the face coefficients.  even_odd: the cell sweeps in
-    even-odd form (the binary64 kernel for k >= 5)."""
+    even-odd form (the binary64 kernel for k >= 5).  folded: full Jacobians
+    stored with the weight folded in (binary64 storage), three instructions
+    fewer per quadrature point."""
     k2, k3, k4 = k * k, k ** 3, k ** 4
     if op == "sipg":
         if even_odd:   # 3 S + 3 S^T (centrosymmetric), 3 D + 3 D^T (anti), D^T accumulated
@@ -71,7 +73,7 @@ def kernel_flops_per_cell(k, op, geom, even_odd=False):
             sweeps = 24 * k4                   # 12 sweeps (3 S, 3 D^co, 3 D^T, 3 S^T), k^4 FMA each
         nb = 6 * 2 * (k3 + 4 * k3)        # 6 faces: D_f (k^3 FMA) + 2 fields x 2 in-face sweeps
         flux = 6 * k2 * (2 * 6 * k + 20)  # own value + 3 gradients, 2 neighbour tangential, flux
-        qop = {"full": 39, "merged": 15, "cartesian": 8}[geom] + 48  # q-op + 24 FMA injection
+        qop = {"full": 39 - (6 if folded else 0), "merged": 15, "cartesian": 8}[geom] + 48  # + 24 FMA injection
         return sweeps + nb + flux + qop * k3
     if even_odd:
         sweeps = 2 * k2 * (6 * even_odd_ops(k, False) + 3 * even_odd_ops(k, True) + 3 * k)
@@ -83,7 +85,7 @@ def kernel_flops_per_cell(k, op, geom, even_odd=False):
     return sweeps + nb + flux + qop * k3
 
 
-def kernel_flops_per_cell_loop(k, op, geom, even_odd=False):
+def kernel_flops_per_cell_loop(k, op, geom, even_odd=False, folded=False):
     """Floating-point work of one cell in the face-loop FP64 apply (two
     launches), counted like kernel_flops_per_cell: the forward sweeps, the
     own traces on six faces (E_s extrapolation of u and the reference
@@ -98,7 +100,7 @@ def kernel_flops_per_cell_loop(k, op, geom, even_odd=False):
         else:
             sweeps = 24 * k ** 4
         traces = 6 * k2 * 4 * 2 * k
-        qop = {"full": 39, "merged": 15, "cartesian": 8}[geom] * k3
+        qop = {"full": 39 - (6 if folded else 0), "merged": 15, "cartesian": 8}[geom] * k3
         face = 6 * k2 * 24
         return sweeps + traces + qop + face + 48 * k3
     if even_odd:
@@ -113,14 +115,15 @@ def kernel_flops_per_cell_loop(k, op, geom, even_odd=False):
 def bytes_per_dof(k, s, op, geom):
     """Algorithmic bytes per dof of one apply: src read and dst write, the
     cell geometry per point, the face geometry per face point (3 faces per
-    cell, k^2 points each) and the penalty per face.  SIPG face arrays: both
-    sides' J^{-T} n and kappa da w (7 values) in binary64; in binary32 one
-    J^{-T} e_d (the two sides' vectors differ only in sign) and kappa da w
-    (4 values)."""
+    cell, k^2 points each) and the penalty per face.  SIPG cell arrays with
+    full Jacobians: sqrt(kappa JxW) J^{-1} (9 values) in binary64, J^{-1} and
+    kappa JxW (10) in binary32.  SIPG face arrays: both sides' J^{-T} n and
+    kappa da w (7 values) in binary64; in binary32 one J^{-T} e_d (the two
+    sides' vectors differ only in sign) and kappa da w (4 values)."""
     vec = 2 * s
     if geom == "cartesian":
         return vec
-    cell = {("sipg", "full"): 10, ("advection", "full"): 10, ("sipg", "merged"): 6,
+    cell = {("sipg", "full"): 9 if s == 8 else 10, ("advection", "full"): 10, ("sipg", "merged"): 6,
             ("advection", "merged"): 3}[(op, geom)] * s
     nfa = (4 if s == 4 else 7) if op == "sipg" else 1
     face = nfa * s * 3 / k + (3 * s / k ** 3 if op == "sipg" else 0)
@@ -133,9 +136,7 @@ def bytes_per_dof(k, s, op, geom):
 # reported only for exactly that launch configuration, and to be re-taken
 # whenever the kernel changes.
 MEASURED_TRAFFIC = {
-    ("fp64", "loop", 4, 5): 1005.98e6,
-    ("fp64", "element", 4, 10): 556.6e6,
-    ("fp64emu", "element", 4, 10): 554.4e6,
+    ("fp64", "loop", 4, 5): 962.9e6,
     ("fp32", "element", 4, 8): 234.4e6,
 }
 
@@ -659,9 +660,11 @@ def main():
 
     # roofline of the apply (one kernel; the face loop: its two launches)
     if loop:
-        flops = kernel_flops_per_cell_loop(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5)) * n_cells
+        flops = kernel_flops_per_cell_loop(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5),
+                                           folded=args.prec != "fp32") * n_cells
     else:
-        flops = kernel_flops_per_cell(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5)) * n_cells
+        flops = kernel_flops_per_cell(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5),
+                                      folded=args.prec != "fp32") * n_cells
     achieved_tf = flops / (launch_ms / 1e3) / 1e12
     bpd = bytes_per_dof(k, ssz, "sipg", w["geom"])
     achieved_gbs = bpd * n / (launch_ms / 1e3) / 1e9

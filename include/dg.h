@@ -61,7 +61,9 @@ typedef enum { DG_OP_SIPG = 0, DG_OP_ADVECTION = 1 } dg_op;
  *             table over x positions).
  *  AFFINE:    reserved; dg_setup returns DG_ERR_UNSUPPORTED.
  *  FULL_JAC:  variant G3: per cell quadrature point J^{-1} (9 values) and
- *             det J * w (* kappa for SIPG) (1 value); per face quadrature
+ *             det J * w (* kappa for SIPG) (1 value) -- for SIPG in binary64
+ *             and double-float storage the weight is folded in as
+ *             sqrt(kappa det J w) J^{-1} (9 values); per face quadrature
  *             point and side n.J^{-T} (3 values each, Design Choice
  *             "normal times inverse Jacobian") and kappa*da*w (1 value), and
  *             one penalty per face.  Advection stores c.n da w (1 value) per

@@ -342,6 +342,7 @@ struct SetupParams {
   double penalty;  // penalty_scale (p+1)^2
   int cblk;        // cell arrays: 0 = structure of arrays, else cell-blocked with this width
   int ncomp;       // number of cell arrays
+  int fold;        // full Jacobians, SIPG, binary64 storage: sqrt(kappa JxW) folded into J^{-1}
   int face_minor;  // face arrays: 0 = [array][face][point]; 1 = blocks of kFaceBlock faces,
                    // [face block][array][point][face in block], faces numbered like cells
                    // (x fastest; the face position replaces the index along d)
@@ -430,7 +431,11 @@ __global__ void setup_cell_geometry(const SetupParams S, int64_t n_cells, T* out
     auto at = [&](int m) -> int64_t {
       return S.cblk ? (((c / S.cblk) * S.ncomp + m) * (int64_t)k3 + q) * S.cblk + c % S.cblk : m * ncq + idx;
     };
-    if (S.geom == dg::GEO_FULL) {
+    if (S.geom == dg::GEO_FULL && S.fold) {
+      // kappa JxW J^{-1} J^{-T} = (s J^{-1}) (s J^{-1})^T with s = sqrt(kappa JxW)
+      const double sw = sqrt(kappa_of(S, x) * jxw);
+      for (int m = 0; m < 9; ++m) out[at(m)] = (T)(sw * Ji[m]);
+    } else if (S.geom == dg::GEO_FULL) {
       for (int m = 0; m < 9; ++m) out[at(m)] = (T)Ji[m];
       out[at(9)] = (T)(S.op == dg::OP_SIPG ? kappa_of(S, x) * jxw : jxw);
     } else if (S.op == dg::OP_SIPG) {
@@ -945,8 +950,12 @@ dg_status setup_geometry(dg_handle* h) {
 
   const bool cart = h->geom == DG_GEOM_CARTESIAN;
   int ncell_arrays = 0;
+  // full Jacobians for SIPG in binary64 storage (FP64 and double-float
+  // operators): sqrt(kappa JxW) J^{-1}, 9 arrays; otherwise J^{-1} and the
+  // weight, 10 arrays (the binary32 kernel keeps the weight separate)
+  S.fold = h->geom == DG_GEOM_FULL_JAC && h->op == DG_OP_SIPG && h->prec != DG_FP32;
   if (!cart) {
-    if (h->geom == DG_GEOM_FULL_JAC) ncell_arrays = 10;
+    if (h->geom == DG_GEOM_FULL_JAC) ncell_arrays = S.fold ? 9 : 10;
     else ncell_arrays = h->op == DG_OP_SIPG ? 6 : 3;
   }
   // binary32: cell-blocked layout padded to whole blocks (zero padding)

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   // 0. start the HBM fetch of this block's cell geometry into L2; it is read
   // in phase 4, after the sweeps and face work
   if (GEO != GEO_CART) {
-    constexpr int NA = GEO == GEO_FULL ? 10 : (OP == OP_SIPG ? 6 : 3);
+    constexpr int NA = GEO == GEO_FULL ? (OP == OP_SIPG ? 9 : 10) : (OP == OP_SIPG ? 6 : 3);
     const char* base = reinterpret_cast<const char*>(gm.cell + cell0 * K3);
     const int64_t bytes = (int64_t)nloc * K3 * (int64_t)sizeof(T);
     const int lines = (int)((bytes + 127) / 128) + 1;
@@ -620,16 +620,16 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
           t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
         } else if (GEO == GEO_FULL) {
+          // stored: s J^{-1} with s = sqrt(kappa JxW); grad_x u = J^{-T}
+          // grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux = (sJ^{-1}) (sJ^{-1})^T grad_xi u
           const T* cp = gm.cell + qi;
           const int64_t n = gm.ncq;
           T J[9];
 #pragma unroll
           for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-          const T jw = cp[9 * n];
-          // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
-          const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
-          const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
-          const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+          const T x0 = J[0] * g0 + J[3] * g1 + J[6] * g2;
+          const T x1 = J[1] * g0 + J[4] * g1 + J[7] * g2;
+          const T x2 = J[2] * g0 + J[5] * g1 + J[8] * g2;
           t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
           t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
           t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;

@@ -203,16 +203,15 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
         t1 = w * gm.cart_jinv[1] * gm.cart_jinv[1] * g1;
         t2 = w * gm.cart_jinv[2] * gm.cart_jinv[2] * g2;
       } else if (GEO == GEO_FULL) {
+        // stored: s J^{-1} with s = sqrt(kappa JxW), so t = (sJ^{-1}) (sJ^{-1})^T grad_xi u
         const T* cp = gm.cell + qi;
         const int64_t n = gm.ncq;
         T J[9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) J[m] = cp[m * n];
-        const T jw = cp[9 * n];
-        // grad_x u = J^{-T} grad_xi u, flux = kappa JxW grad_x u, t = J^{-1} flux
-        const T x0 = jw * (J[0] * g0 + J[3] * g1 + J[6] * g2);
-        const T x1 = jw * (J[1] * g0 + J[4] * g1 + J[7] * g2);
-        const T x2 = jw * (J[2] * g0 + J[5] * g1 + J[8] * g2);
+        const T x0 = J[0] * g0 + J[3] * g1 + J[6] * g2;
+        const T x1 = J[1] * g0 + J[4] * g1 + J[7] * g2;
+        const T x2 = J[2] * g0 + J[5] * g1 + J[8] * g2;
         t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
         t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
         t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;

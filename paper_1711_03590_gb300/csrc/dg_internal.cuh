@@ -51,7 +51,8 @@ struct Geometry {
   int P[3];
   // FULL / MERGED cell arrays: structure of arrays, stride ncq = n_cells k^3
   // (binary64 and double-float); binary32: cell-blocked, see f32_geometry_block
-  const T* __restrict__ cell;  // FULL SIPG: 9 J^{-1} + 1 kappa JxW; FULL ADV: 9 + 1 JxW;
+  const T* __restrict__ cell;  // FULL SIPG: 9 sqrt(kappa JxW) J^{-1} (binary32: 9 J^{-1} + 1 kappa JxW);
+                               // FULL ADV: 9 J^{-1} + 1 JxW;
                                // MERGED SIPG: 6; MERGED ADV: 3
   int64_t ncq;
   // face arrays per direction (stride nfq[d] = nfaces_d k^2)
