@@ -62,9 +62,10 @@ def kernel_flops_per_cell(k, op, geom, even_odd=False, folded=False):
     the neighbour's face-normal and in-face interpolation, the own-side face
     traces and flux at every face point, the quadrature-point operation and
     the injection of the face coefficients.  even_odd: the cell sweeps in
-    even-odd form (the binary64 kernel for k >= 5).  folded: full Jacobians
-    stored with the weight folded in (binary64 storage), three instructions
-    fewer per quadrature point."""
+    even-odd form (the binary64 kernel for k >= 5).  folded: binary64
+    storage with the weights folded into the stored vectors (full Jacobians:
+    three instructions fewer per quadrature point; faces with per-point
+    geometry: two fewer per face point and side)."""
     k2, k3, k4 = k * k, k ** 3, k ** 4
     if op == "sipg":
         if even_odd:   # 3 S + 3 S^T (centrosymmetric), 3 D + 3 D^T (anti), D^T accumulated
@@ -72,7 +73,7 @@ def kernel_flops_per_cell(k, op, geom, even_odd=False, folded=False):
         else:
             sweeps = 24 * k4                   # 12 sweeps (3 S, 3 D^co, 3 D^T, 3 S^T), k^4 FMA each
         nb = 6 * 2 * (k3 + 4 * k3)        # 6 faces: D_f (k^3 FMA) + 2 fields x 2 in-face sweeps
-        flux = 6 * k2 * (2 * 6 * k + 20)  # own value + 3 gradients, 2 neighbour tangential, flux
+        flux = 6 * k2 * (2 * 6 * k + 20 - (4 if folded and geom != "cartesian" else 0))  # traces + flux
         qop = {"full": 39 - (6 if folded else 0), "merged": 15, "cartesian": 8}[geom] + 48  # + 24 FMA injection
         return sweeps + nb + flux + qop * k3
     if even_odd:
@@ -101,7 +102,7 @@ def kernel_flops_per_cell_loop(k, op, geom, even_odd=False, folded=False):
             sweeps = 24 * k ** 4
         traces = 6 * k2 * 4 * 2 * k
         qop = {"full": 39 - (6 if folded else 0), "merged": 15, "cartesian": 8}[geom] * k3
-        face = 6 * k2 * 24
+        face = 6 * k2 * (24 - (4 if folded and geom != "cartesian" else 0))
         return sweeps + traces + qop + face + 48 * k3
     if even_odd:
         sweeps = 2 * k2 * (3 * c) + 2 * k2 * (3 * a + 3 * c + 3 * k)
@@ -136,7 +137,7 @@ def bytes_per_dof(k, s, op, geom):
 # reported only for exactly that launch configuration, and to be re-taken
 # whenever the kernel changes.
 MEASURED_TRAFFIC = {
-    ("fp64", "loop", 4, 5): 962.9e6,
+    ("fp64", "loop", 4, 5): 962.3e6,
     ("fp32", "element", 4, 8): 234.4e6,
 }
 

@@ -66,8 +66,10 @@ typedef enum { DG_OP_SIPG = 0, DG_OP_ADVECTION = 1 } dg_op;
  *             sqrt(kappa det J w) J^{-1} (9 values); per face quadrature
  *             point and side n.J^{-T} (3 values each, Design Choice
  *             "normal times inverse Jacobian") and kappa*da*w (1 value), and
- *             one penalty per face.  Advection stores c.n da w (1 value) per
- *             face point instead.
+ *             one penalty per face -- in binary64 and double-float storage
+ *             the vectors are stored times kappa*da*w and the weight times
+ *             the penalty.  Advection stores c.n da w (1 value) per face
+ *             point instead.
  *  MERGED:    variant G4: per cell quadrature point the merged coefficient
  *             kappa det J w J^{-1} J^{-T} (6 values, SIPG) or
  *             -det J w J^{-1} c (3 values, advection); faces as FULL_JAC. */

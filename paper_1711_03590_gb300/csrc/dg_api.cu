@@ -523,9 +523,14 @@ __global__ void setup_face_geometry(const SetupParams S, int d, int64_t n_faces,
       for (int a = 0; a < 3; ++a) out[at(a)] = (T)(has[0] ? jn[0][a] : -jn[1][a]);
       out[at(3)] = (T)(kap * daw);
     } else if (S.op == dg::OP_SIPG) {
+      // both sides' j_n and w = kappa da w; in binary64 storage the weight
+      // is folded in: w j_n per side, and w, which setup_face_tau turns into
+      // w tau (binary32 face_pair storage keeps j_n and w)
+      const double w = kap * daw;
+      const double sc = S.face_minor ? 1.0 : w;
       for (int slot = 0; slot < 2; ++slot)
-        for (int a = 0; a < 3; ++a) out[at(slot * 3 + a)] = (T)jn[slot][a];
-      out[at(6)] = (T)(kap * daw);
+        for (int a = 0; a < 3; ++a) out[at(slot * 3 + a)] = (T)(sc * jn[slot][a]);
+      out[at(6)] = (T)w;
     } else {
       // c.n da w with n the normal pointing to +d (outward normal of the lower side)
       double n[3];
@@ -535,9 +540,15 @@ __global__ void setup_face_geometry(const SetupParams S, int d, int64_t n_faces,
   }
 }
 
+__device__ inline double dg_to_double(double v) { return v; }
+__device__ inline double dg_to_double(float v) { return v; }
+__device__ inline double dg_to_double(df64 v) { return dg::dfp::df_to_double(v); }
+
+// Penalty per face; binary64 storage: also w tau per face point (the face
+// array 6 holds w = kappa da w on entry).
 template <typename T>
 __global__ void setup_face_tau(const SetupParams S, int d, int64_t n_faces, const double* daw, const double* vol,
-                               T* tau) {
+                               T* tau, T* face, int64_t nfq) {
   const int k2 = S.k * S.k;
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n_faces; f += (int64_t)gridDim.x * blockDim.x) {
@@ -557,7 +568,13 @@ __global__ void setup_face_tau(const SetupParams S, int d, int64_t n_faces, cons
       const int64_t c = ijk[0] + (int64_t)S.n[0] * (ijk[1] + (int64_t)S.n[1] * ijk[2]);
       r = fmax(r, A / vol[c]);
     }
-    tau[S.face_minor ? dg::face_minor_id(S.n, S.P, d, f) : f] = (T)(S.penalty * r);
+    const double t = S.penalty * r;
+    tau[S.face_minor ? dg::face_minor_id(S.n, S.P, d, f) : f] = (T)t;
+    if (!S.face_minor)
+      for (int q = 0; q < k2; ++q) {
+        T& wq = face[6 * nfq + f * k2 + q];
+        wq = (T)(t * dg_to_double(wq));
+      }
   }
 }
 
@@ -1007,7 +1024,7 @@ dg_status setup_geometry(dg_handle* h) {
                              h->stream>>>(S, d, nf, static_cast<T*>(h->face_geo[d]), nfq, daw, bad);
     if (h->op == DG_OP_SIPG)
       setup_face_tau<T><<<(unsigned)std::min<int64_t>((nf + threads - 1) / threads, 4096), threads, 0, h->stream>>>(
-          S, d, nf, daw, vol, static_cast<T*>(h->face_tau[d]));
+          S, d, nf, daw, vol, static_cast<T*>(h->face_tau[d]), static_cast<T*>(h->face_geo[d]), nfq);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     dev_free(h, daw);
     if (e != cudaSuccess) st = cuda_fail(h, e, "face geometry kernels");

@@ -367,7 +367,6 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
     const int nt1 = d == 0 ? gm.n[1] : gm.n[0];
     const int Pd = d == 0 ? gm.P[0] : d == 1 ? gm.P[1] : gm.P[2];
     const T* fgeo = d == 0 ? gm.face[0] : d == 1 ? gm.face[1] : gm.face[2];
-    const T* ftau = d == 0 ? gm.tau[0] : d == 1 ? gm.tau[1] : gm.tau[2];
     const int64_t nfqd = d == 0 ? gm.nfq[0] : d == 1 ? gm.nfq[1] : gm.nfq[2];
     const T cjd = d == 0 ? gm.cart_jinv[0] : d == 1 ? gm.cart_jinv[1] : gm.cart_jinv[2];
     const T ctaud = d == 0 ? gm.cart_tau[0] : d == 1 ? gm.cart_tau[1] : gm.cart_tau[2];
@@ -524,7 +523,7 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
           }
           T g[3] = {ag0.get(), ag1.get(), ag2.get()};
           const T dnn = interior ? nbt[K2 + ln] : T(0);
-          T jo[3], dno, fjxw, tau;
+          T jo[3], dno, tv, tg;
           if (GEO == GEO_CART) {
             const T jn = sg * cjd;
             jo[0] = d == 0 ? jn : T(0);
@@ -533,26 +532,33 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
             dno = jn * (d == 0 ? g[0] : d == 1 ? g[1] : g[2]);
             T kap = T(1);
             if (gm.kq) kap = d == 0 ? gm.kf[ijk[0] + s] : gm.kq[ijk[0] * K + la];
-            fjxw = kap * sW[la] * sW[lb] * gm.cart_detj * cjd;
-            tau = ctaud;
+            const T fjxw = kap * sW[la] * sW[lb] * gm.cart_detj * cjd, tau = ctaud;
+            if (interior) {
+              const T jump = u - un;
+              tv = fjxw * (tau * jump - T(0.5) * (dno + dnn));
+              tg = T(-0.5) * fjxw * jump;
+            } else {
+              tv = fjxw * (T(2) * tau * u - dno);
+              tg = -fjxw * u;
+            }
           } else {
+            // stored with the weight w = kappa da w folded in: w j_n per side
+            // (so dno and dnn carry w) and w tau
             const T* fp = fgeo + fid[s] * K2 + ln;
             const int so = 1 - s;  // own slot: the lower side of the face is slot 0
             jo[0] = fp[(so * 3 + 0) * nfqd];
             jo[1] = fp[(so * 3 + 1) * nfqd];
             jo[2] = fp[(so * 3 + 2) * nfqd];
             dno = jo[0] * g[0] + jo[1] * g[1] + jo[2] * g[2];
-            fjxw = fp[6 * nfqd];
-            tau = ftau[fid[s]];
-          }
-          T tv, tg;
-          if (interior) {
-            const T jump = u - un;
-            tv = fjxw * (tau * jump - T(0.5) * (dno + dnn));
-            tg = T(-0.5) * fjxw * jump;
-          } else {
-            tv = fjxw * (T(2) * tau * u - dno);
-            tg = -fjxw * u;
+            const T wtau = fp[6 * nfqd];
+            if (interior) {
+              const T jump = u - un;
+              tv = wtau * jump - T(0.5) * (dno + dnn);
+              tg = T(-0.5) * jump;
+            } else {
+              tv = T(2) * wtau * u - dno;
+              tg = -u;
+            }
           }
           ft[0] = tv;
           ft[K2] = tg * jo[0];

@@ -273,8 +273,10 @@ __device__ __forceinline__ void split_slot_flux(const T* W, const Geometry<T>& g
   const int sn = 1 - so;
   const T cjd = gm.cart_jinv[d];
   if (OP == OP_SIPG) {
-    // j_n per slot (each side's own outward normal: +d for slot 0)
-    T jo[3], jn[3], fjxw, tau;
+    // j_n per slot (each side's own outward normal: +d for slot 0); with
+    // per-point geometry stored as w j_n and w tau (w = kappa da w), so
+    // that dno and dnn carry the weight
+    T jo[3], jn[3], w, wtau;
     if (GEO == GEO_CART) {
       const T j = so == 0 ? cjd : -cjd;
 #pragma unroll
@@ -284,8 +286,8 @@ __device__ __forceinline__ void split_slot_flux(const T* W, const Geometry<T>& g
       }
       T kap = T(1);
       if (gm.kq) kap = d == 0 ? gm.kf[pos] : gm.kq[it1 * K + la];
-      fjxw = kap * W[la] * W[lb] * gm.cart_detj * cjd;
-      tau = gm.cart_tau[d];
+      w = kap * W[la] * W[lb] * gm.cart_detj * cjd;
+      wtau = w * gm.cart_tau[d];
     } else {
       const T* f = gm.face[d] + fid * K2 + fp;
       const int64_t nfq = gm.nfq[d];
@@ -294,20 +296,29 @@ __device__ __forceinline__ void split_slot_flux(const T* W, const Geometry<T>& g
         jo[c] = f[(so * 3 + c) * nfq];
         jn[c] = f[(sn * 3 + c) * nfq];
       }
-      fjxw = f[6 * nfq];
-      tau = gm.tau[d][fid];
+      wtau = f[6 * nfq];
     }
     const T dno = jo[0] * g[so][0] + jo[1] * g[so][1] + jo[2] * g[so][2];
     T tv, tg;
-    if (interior) {
+    if (GEO == GEO_CART) {
+      if (interior) {
+        const T dnn = -(jn[0] * g[sn][0] + jn[1] * g[sn][1] + jn[2] * g[sn][2]);
+        const T jump = u[so] - u[sn];
+        tv = w * (gm.cart_tau[d] * jump - T(0.5) * (dno + dnn));
+        tg = T(-0.5) * w * jump;
+      } else {
+        tv = w * (T(2) * gm.cart_tau[d] * u[so] - dno);
+        tg = -w * u[so];
+      }
+    } else if (interior) {
       // the neighbour's derivative along this side's outward normal
       const T dnn = -(jn[0] * g[sn][0] + jn[1] * g[sn][1] + jn[2] * g[sn][2]);
       const T jump = u[so] - u[sn];
-      tv = fjxw * (tau * jump - T(0.5) * (dno + dnn));
-      tg = T(-0.5) * fjxw * jump;
+      tv = wtau * jump - T(0.5) * (dno + dnn);
+      tg = T(-0.5) * jump;
     } else {
-      tv = fjxw * (T(2) * tau * u[so] - dno);
-      tg = -fjxw * u[so];
+      tv = T(2) * wtau * u[so] - dno;
+      tg = -u[so];
     }
     ft[0] = tv;
 #pragma unroll

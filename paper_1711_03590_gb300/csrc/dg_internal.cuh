@@ -56,8 +56,9 @@ struct Geometry {
                                // MERGED SIPG: 6; MERGED ADV: 3
   int64_t ncq;
   // face arrays per direction (stride nfq[d] = nfaces_d k^2)
-  const T* __restrict__ face[3];  // SIPG: 6 j_n (slot0 xyz, slot1 xyz) + 1 kappa da w; ADV: 1 c.n da w
-                                  // (binary32 SIPG unless face_pair: 3 j_n of slot 0 + 1 kappa da w)
+  const T* __restrict__ face[3];  // SIPG: 6 w j_n (slot0 xyz, slot1 xyz) + 1 w tau, w = kappa da w;
+                                  // ADV: 1 c.n da w (binary32 SIPG: j_n unscaled + w, and unless
+                                  // face_pair only slot 0's 3 j_n + w)
   const T* __restrict__ tau[3];   // SIPG: penalty per face
   int64_t nfq[3];
   int nfc[3];  // faces per direction
