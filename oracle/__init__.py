@@ -7,7 +7,12 @@ sum factorization), and this module only marshals numpy arrays through
 ctypes.
 
 Mesh and form descriptions are plain dicts:
-    mesh = {"n": (nx, ny, nz), "periodic": bool, "mapping": 0|1, "amplitude": a}
+    mesh = {"n": (nx, ny, nz), "periodic": bool, "mapping": 0|1|2, "amplitude": a,
+            "cell_jacobian": "analytic"|"g2"}
+    (mapping 2: the affine shear x_i = X_i + a X_{(i+1) mod 3}; cell_jacobian
+    "g2": the cell term's Jacobian is the collocation derivative of the Gauss
+    points' positions, geometry variant G2 of Sec. 5; faces, penalty, rhs
+    and errors keep the analytic map)
     form = {"op": "sipg"|"advection", "coeff": 0|1,
             "velocity": (c0, c1, c2), "penalty_scale": 1.0}
 
@@ -34,7 +39,8 @@ _lib = None
 
 class _Mesh(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("periodic", ctypes.c_int),
-                ("mapping", ctypes.c_int), ("amplitude", ctypes.c_double)]
+                ("mapping", ctypes.c_int), ("amplitude", ctypes.c_double),
+                ("cell_jacobian", ctypes.c_int)]
 
 
 class _Form(ctypes.Structure):
@@ -88,8 +94,10 @@ def _mesh(m):
     n = m["n"]
     if isinstance(n, int):
         n = (n, n, n)
+    cj = m.get("cell_jacobian", 0)
+    cj = {"analytic": 0, "g2": 1}.get(cj, cj)
     return _Mesh((ctypes.c_int * 3)(*n), int(bool(m.get("periodic", False))),
-                 int(m.get("mapping", 0)), float(m.get("amplitude", 0.0)))
+                 int(m.get("mapping", 0)), float(m.get("amplitude", 0.0)), int(cj))
 
 
 def _form(f):

@@ -49,8 +49,12 @@
 typedef struct {
   int n[3];         /* cells per direction */
   int periodic;     /* 1: periodic in all directions, 0: Dirichlet on all of the boundary */
-  int mapping;      /* 0: identity, 1: x_i = X_i + a sin(pi X) sin(pi Y) sin(pi Z) */
+  int mapping;      /* 0: identity, 1: x_i = X_i + a sin(pi X) sin(pi Y) sin(pi Z),
+                       2: affine, x_i = X_i + a X_{(i+1) mod 3} */
   double amplitude; /* a */
+  int cell_jacobian; /* 0: analytic J of the mapping; 1: variant G2 of Sec. 5, the
+                        cell term's J is the collocation derivative of the
+                        positions of the cell's Gauss points */
 } or_mesh;
 
 typedef struct {
@@ -182,7 +186,9 @@ static int64_t neighbour(const or_mesh *m, int64_t c, int d, int s) {
 
 /* Physical point x and Jacobian J = dx/dxi of cell c at reference point xi.
  * Cartesian point X_d = (i_d + xi_d)/n_d; mapping 1 shifts every coordinate
- * by a*s(X) with s = sin(pi X) sin(pi Y) sin(pi Z). */
+ * by a*s(X) with s = sin(pi X) sin(pi Y) sin(pi Z); mapping 2 is the linear
+ * shear x_i = X_i + a X_{(i+1) mod 3} (constant J per cell, det = (1 + a^3)
+ * / (n0 n1 n2)). */
 static void cell_map(const or_mesh *m, int64_t c, const double xi[3], double x[3], double J[3][3]) {
   int ijk[3];
   cell_ijk(m, c, ijk);
@@ -199,6 +205,15 @@ static void cell_map(const or_mesh *m, int64_t c, const double xi[3], double x[3
     gs[0] = OR_PI * cs[0] * sn[1] * sn[2];
     gs[1] = OR_PI * sn[0] * cs[1] * sn[2];
     gs[2] = OR_PI * sn[0] * sn[1] * cs[2];
+  }
+  if (m->mapping == 2) {
+    double a = m->amplitude;
+    for (int i = 0; i < 3; ++i) {
+      int i1 = (i + 1) % 3;
+      x[i] = X[i] + a * X[i1];
+      for (int j = 0; j < 3; ++j) J[i][j] = ((i == j ? 1.0 : 0.0) + (j == i1 ? a : 0.0)) * h[j];
+    }
+    return;
   }
   double a = (m->mapping == 1) ? m->amplitude : 0.0;
   for (int i = 0; i < 3; ++i) {
@@ -247,6 +262,31 @@ static int basis_init(basis1d *b, int degree) {
   if (or_gauss_lobatto(k, b->gl, wl)) return -1;
   if (or_gauss(k, b->gq, b->gw)) return -1;
   return 0;
+}
+
+/* Point x and the Jacobian used by the cell integral at the Gauss point
+ * (q0, q1, q2) of cell c.  Analytic (cell_map), or for variant G2 (Sec. 5:
+ * positions of the quadrature points stored, the Jacobian computed by a
+ * collocation derivative): column d of J is the derivative along xi_d of
+ * the polynomial interpolating the physical positions of the k Gauss points
+ * on the line through the point, J[i][d] = sum_j l_j'(g_{q_d}) x_i(.., g_j,
+ * ..), with l_j the Lagrange polynomials on the Gauss points. */
+static void cell_point(const or_mesh *m, const basis1d *b, int64_t c, const int q[3], double x[3], double J[3][3]) {
+  double xi[3] = {b->gq[q[0]], b->gq[q[1]], b->gq[q[2]]};
+  cell_map(m, c, xi, x, J);
+  if (m->cell_jacobian != 1) return;
+  int k = b->k;
+  for (int d = 0; d < 3; ++d) {
+    double col[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < k; ++j) {
+      double xj[3] = {xi[0], xi[1], xi[2]}, pj[3], Jj[3][3];
+      xj[d] = b->gq[j];
+      cell_map(m, c, xj, pj, Jj);
+      double dl = or_lagrange_deriv(k, b->gq, j, xi[d]);
+      for (int i = 0; i < 3; ++i) col[i] += dl * pj[i];
+    }
+    for (int i = 0; i < 3; ++i) J[i][d] = col[i];
+  }
 }
 
 /* Values and reference gradients of all k^3 tensor basis functions
@@ -369,7 +409,8 @@ static void apply_one_cell(const or_mesh *m, const basis1d *b, const or_form *f,
     for (int q1 = 0; q1 < k; ++q1)
       for (int q0 = 0; q0 < k; ++q0) {
         double xi[3] = {b->gq[q0], b->gq[q1], b->gq[q2]}, x[3], J[3][3], Ji[3][3];
-        cell_map(m, c, xi, x, J);
+        int q[3] = {q0, q1, q2};
+        cell_point(m, b, c, q, x, J);
         double detJ = det3(J);
         inv3(J, detJ, Ji);
         double jxw = detJ * b->gw[q0] * b->gw[q1] * b->gw[q2];
@@ -554,7 +595,8 @@ int64_t or_assemble(const or_mesh *m, int degree, const or_form *f, int64_t *row
         for (int q1 = 0; q1 < k; ++q1)
           for (int q0 = 0; q0 < k; ++q0) {
             double xi[3] = {b.gq[q0], b.gq[q1], b.gq[q2]}, x[3], J[3][3], Ji[3][3];
-            cell_map(m, c, xi, x, J);
+            int q[3] = {q0, q1, q2};
+            cell_point(m, &b, c, q, x, J);
             double detJ = det3(J);
             inv3(J, detJ, Ji);
             double jxw = detJ * b.gw[q0] * b.gw[q1] * b.gw[q2];

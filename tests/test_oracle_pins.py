@@ -15,6 +15,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
+import dg_inputs
 import oracle
 import ref1d
 
@@ -195,6 +196,31 @@ def test_advection_kills_constants_cartesian_periodic():
     assert np.abs(A @ np.ones(A.shape[0])).max() < 1e-14
 
 
+def test_advection_kills_constants_deformed_periodic_up_to_quadrature():
+    """On the sine-mapped periodic mesh a(v, 1) = -(grad v, c) + <v, c.n> is
+    zero in exact arithmetic (divergence theorem, div c = 0), but the k-point
+    Gauss rule integrates the mapped integrands only approximately, so A 1
+    is a quadrature error: small against |A| and decaying spectrally in the
+    degree (measured: 3.8e-3, 1.2e-4, 1.8e-5, 7.9e-7, 4.2e-8, 1.6e-9 of
+    max|A| for p = 1..6 on 2^3 cells) and with the mesh size.  A wrong sign
+    or normal in the face flux leaves an O(1) fraction of |A| instead."""
+    mesh = dict(n=(2, 2, 2), periodic=True, **DEFORMED)
+    prev = None
+    for p in range(1, 7):
+        A = oracle.assemble(mesh, p, dict(op="advection"))
+        r = np.abs(A @ np.ones(A.shape[0])).max() / abs(A).max()
+        assert r < 5e-3 * 10.0 ** (-(p - 1)), (p, r)
+        if prev is not None:
+            assert r < prev / 4, (p, r, prev)
+        prev = r
+    errs = []
+    for N in (2, 4):
+        m = dict(n=(N, N, N), periodic=True, **DEFORMED)
+        A = oracle.assemble(m, 2, dict(op="advection"))
+        errs.append(np.abs(A @ np.ones(A.shape[0])).max())
+    assert errs[1] < errs[0] / 32  # at least order p + 1 = 3 in h (measured 2^6.6)
+
+
 @pytest.mark.parametrize("periodic", [True, False])
 @pytest.mark.parametrize("coeff", [0, 1])
 def test_sipg_symmetric_deformed(periodic, coeff):
@@ -371,3 +397,82 @@ def test_assembled_equals_cellwise(mesh, p, form):
     k3 = (p + 1) ** 3
     for c in sub:
         np.testing.assert_array_equal(y3[c * k3:(c + 1) * k3], y2[c * k3:(c + 1) * k3])
+
+
+# ---- affine mapping (mapping 2) and geometry variant G2 (Sec. 5) ----------
+
+AFFINE = dict(mapping=2, amplitude=0.1)
+
+
+@pytest.mark.parametrize("N", [(1, 1, 1), (2, 3, 2)])
+def test_affine_map_volumes_closed_form(N):
+    """x_i = X_i + a X_{(i+1) mod 3}: J = (I + a P) diag(1/n) with P the cyclic
+    shift, det(I + a P) = 1 + a^3, so every cell has volume (1 + a^3) / (n0
+    n1 n2) and the mass matrix sums to 1 + a^3."""
+    mesh = dict(n=N, periodic=False, **AFFINE)
+    a = AFFINE["amplitude"]
+    nc = oracle.n_cells(mesh)
+    for p in (1, 3):
+        for c in range(nc):
+            assert abs(oracle.cell_volume(mesh, p, c) - (1 + a ** 3) / nc) < 1e-15
+        n = oracle.n_dofs(mesh, p)
+        assert abs(oracle.mass_apply(mesh, p, np.ones(n)).sum() - (1 + a ** 3)) < 1e-13
+
+
+def test_affine_map_invariants():
+    """On the affine mesh every integrand is a polynomial that the Gauss
+    rules integrate exactly: advection with constant c kills constants with
+    periodic boundaries to round-off (not only up to quadrature, as on the
+    sine map); SIPG kills constants, is symmetric, and is positive definite
+    with Dirichlet boundaries."""
+    per = dict(n=(2, 2, 3), periodic=True, **AFFINE)
+    for p in (1, 2, 4):
+        A = oracle.assemble(per, p, dict(op="advection"))
+        assert np.abs(A @ np.ones(A.shape[0])).max() < 1e-14 * max(1.0, abs(A).max())
+        S = oracle.assemble(per, p, dict(op="sipg", coeff=0))  # kappa is not periodic on the shear
+        assert np.abs(S @ np.ones(S.shape[0])).max() < 1e-12 * abs(S).max()
+        assert abs(S - S.T).max() < 1e-13 * abs(S).max()
+    D = oracle.assemble(dict(n=(2, 2, 2), periodic=False, **AFFINE), 3, dict(op="sipg", coeff=1))
+    x = np.random.default_rng(1).uniform(-1, 1, D.shape[0])
+    assert x @ (D @ x) > 0
+
+
+@pytest.mark.parametrize("mapping", [0, 2])
+@pytest.mark.parametrize("op", ["sipg", "advection"])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_g2_equals_analytic_jacobian_on_linear_maps(mapping, op, periodic):
+    """Variant G2 differentiates the polynomial through the Gauss points'
+    positions; for a linear map (identity, affine shear) that polynomial is
+    the map itself, so the G2 operator equals the analytic-J operator to
+    round-off.  The shear's J is not symmetric, so a transposed derivative
+    (J[d][i] for J[i][d]) fails here."""
+    mesh = dict(n=(2, 3, 2), periodic=periodic, mapping=mapping, amplitude=0.1)
+    # kappa(x) = 1 + 0.5 sin(2 pi x_0) is not periodic across the sheared
+    # mesh's y and z wrap (x_0 shifts by a there): periodic cases take kappa = 1
+    form = dict(op=op, coeff=1 if (op == "sipg" and not (periodic and mapping == 2)) else 0)
+    for p in (1, 2, 4):
+        A = oracle.assemble(mesh, p, form)
+        G = oracle.assemble(dict(mesh, cell_jacobian="g2"), p, form)
+        assert abs(A - G).max() < 1e-13 * abs(A).max(), p
+        u = dg_inputs.src_vector(A.shape[0], seed=9)
+        yg = oracle.apply(dict(mesh, cell_jacobian="g2"), p, form, u)
+        assert np.linalg.norm(yg - A @ u) < 1e-13 * np.linalg.norm(A @ u)
+
+
+def test_g2_converges_to_analytic_on_sine_map():
+    """On the sine-mapped mesh the interpolated positions approximate the map
+    to order p + 1, so the G2 operator approaches the analytic-J operator
+    spectrally in p (measured relative differences of A u on 2^3 cells:
+    9.0e-3, 1.2e-3, 1.7e-4, 1.5e-5, 1.4e-6, 7.2e-8 for p = 2..7)."""
+    mesh = dict(n=(2, 2, 2), periodic=False, **DEFORMED)
+    form = dict(op="sipg", coeff=1)
+    prev = None
+    for p in range(2, 8):
+        A = oracle.assemble(mesh, p, form)
+        u = dg_inputs.src_vector(A.shape[0], seed=3)
+        yg = oracle.apply(dict(mesh, cell_jacobian="g2"), p, form, u)
+        r = np.linalg.norm(yg - A @ u) / np.linalg.norm(A @ u)
+        assert r < 2e-2 * 5.0 ** (-(p - 2)), (p, r)
+        if prev is not None:
+            assert r < prev / 3, (p, r, prev)
+        prev = r
