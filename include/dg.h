@@ -141,7 +141,8 @@ typedef struct {
 dg_status dg_setup(const dg_mesh *mesh, int degree, int geom, const dg_opts *opts, void *stream,
                    dg_handle **out);
 
-/* Number of degrees of freedom n = n0 n1 n2 (p+1)^3.  Synchronous. */
+/* Number of degrees of freedom n = n0 n1 n2 (p+1)^3 (the dimension of the
+ * DG space of Sec. 2: (p+1)^3 Lagrange coefficients per cell).  Synchronous. */
 dg_status dg_n_dofs(const dg_handle *h, int64_t *n);
 
 /* Sizes of the operator's data (see dg_info_t).  Synchronous. */
@@ -207,7 +208,9 @@ dg_status dg_apply_host(dg_handle *h, const void *src_host, void *dst_host);
  * in FP64 regardless of the handle's precision.
  *   which_f 0: f = 3 pi^2 u (-Laplace u);  1: f = -div(kappa grad u) with
  *   kappa = 1 + 0.5 sin(2 pi x_0).
- * rhs: device pointer to n_dofs doubles.  Asynchronous. */
+ * rhs: device pointer to n_dofs doubles.  Asynchronous.
+ * No counterpart in the paper (it reports operator evaluations, not solves);
+ * the load vector is the right-hand side of the weak form of Sec. 2. */
 dg_status dg_rhs(dg_handle *h, int which_f, double *rhs);
 
 /* err = || u_h - u ||_{L2(Omega)} for the coefficient vector x (device, n_dofs
@@ -228,7 +231,9 @@ dg_status dg_l2_error(dg_handle *h, const double *x, double *err);
  * Stops when |r| <= rtol |rhs|.  Returns DG_ERR_NOT_CONVERGED after max_it
  * iterations and DG_ERR_BREAKDOWN on p.Ap <= 0 or non-finite scalars.
  * iters and final_rel_res (may be NULL) receive the count and |r|/|rhs|.
- * Synchronous. */
+ * Synchronous.  No counterpart in the paper: it evaluates the operator for
+ * iterative solvers (Sec. 1 and the conclusions) without giving one; this is
+ * textbook CG on the SPD operator of Eq. (poisson_sip). */
 dg_status dg_cg_solve(dg_handle *h, const double *rhs, double *x, double rtol, int max_it, int *iters,
                       double *final_rel_res);
 
@@ -330,14 +335,29 @@ const char *dg_server_last_error(void);
  *             reduced in a fixed order (bitwise reproducible).
  * Operators whose apply needs more than 65,536 CUDA blocks (see
  * dg_info_t.blocks) are rejected with DG_ERR_ARG.  No call allocates or
- * frees memory.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array: calls that
+ * frees memory: dg_setup, which allocates anyway, loads the library module
+ * that holds the array (with lazy module loading the array's memory is
+ * allocated at that load) and looks up its device address
+ * (cudaGetSymbolAddress) with the handle's device current, once per device.
+ * The first dg_setup on a device must therefore come before any stream
+ * capture that records this call.  All calls share the array: calls that
  * overlap on the GPU race on it and must be ordered by the caller.
  * Asynchronous on the handle's stream. */
 dg_status dg_apply_dot_noalloc(dg_handle *h, const void *src, void *dst, double *dot);
 
-/* Free everything the handle owns.  NULL is accepted. */
+/* Measurement aid, no counterpart in the paper: the FMA throughput of the
+ * current device, measured by a kernel of independent fused multiply-add
+ * chains (a whole number of resident blocks per SM; best of four timed
+ * launches after a warm-up, CUDA events; the best of a few shapes of chains
+ * per thread and threads per block).
+ *   kind    0: binary64 FMA (the FP64 pipe), 1: binary32 FMA.
+ *   tflops  receives 2 x FMAs per second / 1e12.
+ * Allocates and frees a small device buffer; synchronous (legacy default
+ * stream).  DG_ERR_ARG for another kind or a NULL tflops. */
+dg_status dg_peak_probe(int kind, double *tflops);
+
+/* Free everything the handle owns.  NULL is accepted.  No counterpart in the
+ * paper (resource management of this library). */
 dg_status dg_destroy(dg_handle *h);
 
 /* Message of the last error on this handle ("" if none); for errors before a

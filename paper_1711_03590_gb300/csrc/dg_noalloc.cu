@@ -16,6 +16,16 @@
 // overlap on the GPU (different streams or threads, no ordering between
 // them) race on it and must be serialized by the caller.  Each call writes
 // exactly the slots it reads back, so no slot needs clearing between calls.
+//
+// The array and reduce_dot sit in this translation unit, which the CUDA
+// runtime loads as a module of its own; with lazy module loading (the default
+// since CUDA 12.2) the array's device memory would be allocated when the
+// module is first touched.  dg_setup, which allocates anyway, therefore calls
+// dg_internal_noalloc_preload on its device: the module is loaded and the
+// array's device address looked up there, once per device, so that
+// dg_apply_dot_noalloc itself triggers neither a module load nor an
+// allocation.  The first dg_setup on a device must come before any stream
+// capture that records dg_apply_dot_noalloc.
 #include <mutex>
 #include <string>
 
@@ -65,6 +75,16 @@ __global__ void reduce_dot(const double* __restrict__ part, int n, double* __res
 }
 
 }  // namespace
+
+// Load this module on the current device (the array and reduce_dot) and
+// cache the array's device address.  Called by dg_setup.
+cudaError_t dg_internal_noalloc_preload() {
+  double* p = nullptr;
+  cudaError_t e = scratch_address(&p);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes attr;
+  return cudaFuncGetAttributes(&attr, reduce_dot);
+}
 
 // Defined in dg_api.cu: the apply launch with an optional per-block partial
 // buffer, and the handle's sizes and stream.

@@ -23,10 +23,18 @@ if not torch.cuda.is_available():
 import paper_1711_03590_gb300 as dgp  # noqa: E402
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_noalloc_apply_dot_matches_allocating_path(prec, tol):
+CASES = [("fp64", "element", 1e-12), ("fp32", "element", 1e-5), ("fp64", "loop", 1e-12),
+         ("fp64emu", "element", 1e-12), ("fp64emu", "loop", 1e-12)]
+
+
+@pytest.mark.parametrize("prec,mode,tol", CASES)
+def test_noalloc_apply_dot_matches_allocating_path(prec, mode, tol):
+    """Both face modes (the face loop writes the partials in its second
+    launch) and all three arithmetics, two calls in a row."""
     dgp.build()
     op = dgp.Operator((6, 5, 7), 3, geom="full", prec=prec, mapping=1, coeff=1)
+    if mode != "element":
+        op.set_face_mode(mode)
     dot = torch.zeros(1, dtype=torch.float64, device="cuda")
     for call, seed in enumerate((21, 22)):
         src = torch.tensor(dg_inputs.src_vector(op.n_dofs, seed), dtype=op.dtype, device="cuda")
@@ -39,6 +47,24 @@ def test_noalloc_apply_dot_matches_allocating_path(prec, tol):
         want = float(torch.dot(src.double(), ref.double()))
         got = float(dot.item())
         assert abs(got - want) <= tol * float(src.double().norm() * ref.double().norm()), (call, got, want)
+    op.close()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    """The defining property: once the operator is set up, calls change the
+    device's free memory by nothing (no allocation, no lazy module load)."""
+    dgp.build()
+    op = dgp.Operator((5, 6, 4), 2, geom="full", prec="fp64", mapping=1, coeff=1)
+    src = torch.tensor(dg_inputs.src_vector(op.n_dofs, 5), dtype=op.dtype, device="cuda")
+    dst = torch.empty_like(src)
+    dot = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dgp.dg_apply_dot_noalloc(op.handle, src.data_ptr(), dst.data_ptr(), dot.data_ptr())  # warm-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(4):
+        dgp.dg_apply_dot_noalloc(op.handle, src.data_ptr(), dst.data_ptr(), dot.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     op.close()
 
 
