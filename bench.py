@@ -113,19 +113,63 @@ def kernel_flops_per_cell_loop(k, op, geom, even_odd=False, folded=False):
     return sweeps + traces + qop + 6 * k2 * 8 + 12 * k3
 
 
+def eo_flops(k, anti):
+    """Flops of one 1D kernel on a line of k values in even-odd form (Sec.
+    4.1), each addition, subtraction or multiplication 1 and each FMA 2: the
+    k - (k mod 2) input sums and differences, per output pair an even and an
+    odd dot product (first term a multiplication) and their sum and
+    difference, and the middle output for odd k."""
+    h, h2 = k // 2, (k + 1) // 2
+    mid = (2 * h - 1 if anti else 2 * h2 - 1) if k % 2 else 0
+    return 2 * h + 2 * k * h + mid
+
+
+def algorithmic_flops_per_cell_loop(k, op, geom, even_odd, folded, boundary_fraction=0.0):
+    """Flops of one cell in the face-loop apply counted as the paper does
+    (Sec. 4.1: each FMA 2, each other addition or multiplication 1; the
+    first term of a dot product is a multiplication): the forward S and D^co
+    sweeps, the own traces (E_s extrapolation, 4 fields for SIPG) on six
+    faces, the q-point operation; the flux on six faces tested on this side
+    (boundary_fraction of the face sides on the domain boundary take the
+    boundary flux), the injection of the face test coefficients, the
+    D^co^T sweeps accumulated into the value field and the S^T sweeps."""
+    k2, k3 = k * k, k ** 3
+    direct = k * (2 * k - 1)                       # one line, direct form
+    s_line = eo_flops(k, False) if even_odd else direct
+    d_line = eo_flops(k, True) if even_odd else direct
+    bf = boundary_fraction
+    if op == "sipg":
+        fwd = 3 * k2 * s_line + 3 * k2 * d_line
+        traces = 6 * k2 * 4 * (2 * k - 1)
+        qop = {"full": 30 if folded else 33, "merged": 15, "cartesian": 13}[geom] * k3
+        flux_int = {"cartesian": 18}.get(geom, 19)
+        flux_bdy = {"cartesian": 12}.get(geom, 11)
+        flux = 6 * k2 * ((1 - bf) * flux_int + bf * flux_bdy)
+        inject = (4 * 11 + 3) * k3
+        bwd = 3 * k2 * (d_line + k) + 3 * k2 * s_line
+        return fwd + traces + qop + flux + inject + bwd
+    fwd = 3 * k2 * s_line
+    traces = 6 * k2 * (2 * k - 1)
+    qop = {"full": 21, "merged": 3, "cartesian": 12}[geom] * k3
+    flux = 6 * k2 * ((1 - bf) * 7 + bf * 1)
+    inject = 11 * k3
+    bwd = 3 * k2 * (d_line + k) + 3 * k2 * s_line
+    return fwd + traces + qop + flux + inject + bwd
+
+
 def bytes_per_dof(k, s, op, geom):
     """Algorithmic bytes per dof of one apply: src read and dst write, the
     cell geometry per point, the face geometry per face point (3 faces per
     cell, k^2 points each) and the penalty per face.  SIPG cell arrays with
     full Jacobians: sqrt(kappa JxW) J^{-1} (9 values) in binary64, J^{-1} and
-    kappa JxW (10) in binary32.  SIPG face arrays: both sides' J^{-T} n and
+    kappa JxW (10) in binary32; G2: the position and kappa (4 values).  SIPG face arrays: both sides' J^{-T} n and
     kappa da w (7 values) in binary64; in binary32 one J^{-T} e_d (the two
     sides' vectors differ only in sign) and kappa da w (4 values)."""
     vec = 2 * s
     if geom == "cartesian":
         return vec
     cell = {("sipg", "full"): 9 if s == 8 else 10, ("advection", "full"): 10, ("sipg", "merged"): 6,
-            ("advection", "merged"): 3}[(op, geom)] * s
+            ("advection", "merged"): 3, ("sipg", "positions"): 4, ("advection", "positions"): 3}[(op, geom)] * s
     nfa = (4 if s == 4 else 7) if op == "sipg" else 1
     face = nfa * s * 3 / k + (3 * s / k ** 3 if op == "sipg" else 0)
     return vec + cell + face
@@ -146,6 +190,21 @@ def measured_traffic(prec, face_mode, degree, cpb, workload):
     if workload != "deformed_dirichlet_32^3_p%d" % degree:
         return None
     return MEASURED_TRAFFIC.get((prec, face_mode, degree, cpb))
+
+
+def probe_alu_peaks(dgp):
+    """FP64 and FP32 FMA throughput measured on this GPU by the library's
+    FMA-chain kernel (dg_peak_probe); the derived unit-count figures are the
+    fallback if the probe fails."""
+    out = {}
+    for key, kind, derived in (("fp64_tflops", 0, FP64_PEAK_TFLOPS), ("fp32_tflops", 1, FP32_PEAK_TFLOPS)):
+        try:
+            out[key] = dgp.dg_peak_probe(kind)
+            out[key + "_source"] = "measured in this run: dg_peak_probe(%d), FMA chains, best of 4 launches" % kind
+        except Exception as e:  # noqa: BLE001
+            out[key] = derived
+            out[key + "_source"] = "derived from unit counts and the 2.07 GHz clock (probe failed: %s)" % e
+    return out
 
 
 def load_peaks():
@@ -304,17 +363,21 @@ def solve_metrics(torch, dgp, args, n=16, p=3, rtol=1e-10, repeats=20):
             "solves_per_s": 1.0 / float(np.mean(lat))}
 
 
-def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget_gb=120.0, seed=4):
+def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget_gb=120.0, seed=4, n_lo=8,
+                  n_hi=48):
     """Many independent operators in one graph launch: count deformed-cube
-    meshes with n^3 cells, n log-uniform in [8, 48], degrees uniform in 1..7
-    (G3 geometry, kappa variable, Dirichlet).  Compares one dg_batch_launch
-    (autotuned tile shapes, 8 graph branches) with the same applies issued one
-    by one on a stream; FP64 operators in the bench's face mode.  Meshes
-    beyond the device-memory budget are dropped (their count is reported)."""
+    meshes with n^3 cells, n log-uniform in [n_lo, n_hi], degrees uniform in
+    1..7 (G3 geometry, kappa variable, Dirichlet).  Compares one
+    dg_batch_launch (fused launches per kernel group, per-group autotuned
+    tile shapes, 8 graph branches) with the same applies issued one by one on
+    a stream, each operator at its own autotuned tile shape; FP64 operators
+    in the bench's face mode.  Meshes beyond the device-memory budget are
+    dropped (their count is reported)."""
     rng = np.random.default_rng(seed)
-    ns = np.round(np.exp(rng.uniform(np.log(8), np.log(48), count))).astype(int)
+    ns = np.round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count))).astype(int)
     ps = rng.integers(1, 8, count)
-    out = {"workload": "%d meshes, n^3 cells with n log-uniform in [8, 48], degree uniform in 1..7, G3" % count}
+    out = {"workload": "%d meshes, n^3 cells with n log-uniform in [%d, %d], degree uniform in 1..7, G3" % (
+        count, n_lo, n_hi)}
     for prec in prec_list:
         s = 4 if prec == "fp32" else 8
         ops, srcs, dsts, used = [], [], [], 0.0
@@ -337,20 +400,16 @@ def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget
                                      device="cuda"))
             dsts.append(torch.empty_like(srcs[-1]))
         total = sum(o.n_dofs for o in ops)
-        b = dgp.dg_batch_create([o.handle for o in ops], [x.data_ptr() for x in srcs], [x.data_ptr() for x in dsts],
-                                autotune=True, branches=8, stream=torch.cuda.current_stream().cuda_stream)
+        # the one-by-one reference: each operator at its own autotuned tile shape
+        for o in ops:
+            o.autotune()
         stream = torch.cuda.current_stream()
-        for _ in range(3):
-            dgp.dg_batch_launch(b)
+        for _ in range(2):
+            for o, x, y in zip(ops, srcs, dsts):
+                o.apply(x, y)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 5
         torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            dgp.dg_batch_launch(b)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_batch = e0.elapsed_time(e1) / reps
         e0.record(stream)
         for _ in range(reps):
             for o, x, y in zip(ops, srcs, dsts):
@@ -358,8 +417,22 @@ def batch_metrics(torch, dgp, args, count=64, prec_list=("fp64", "fp32"), budget
         e1.record(stream)
         torch.cuda.synchronize()
         t_seq = e0.elapsed_time(e1) / reps
+        b = dgp.dg_batch_create([o.handle for o in ops], [x.data_ptr() for x in srcs], [x.data_ptr() for x in dsts],
+                                autotune=True, branches=8, stream=torch.cuda.current_stream().cuda_stream)
+        groups, launches = dgp.dg_batch_info(b)
+        for _ in range(3):
+            dgp.dg_batch_launch(b)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            dgp.dg_batch_launch(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) / reps
         dgp.dg_batch_destroy(b)
         out[prec] = {"operators": len(ops), "skipped_for_memory": skipped, "dofs": total,
+                     "kernel_groups": groups, "launches_per_batch": launches,
+                     "launches_sequential": len(ops) * (2 if prec == "fp64" and args.face_mode == "loop" else 1),
                      "face_mode": "loop" if prec == "fp64" and args.face_mode == "loop" else "element",
                      "ms_per_batch_launch": t_batch, "dofs_per_s": total / (t_batch / 1e3),
                      "ms_sequential_applies": t_seq, "speedup_vs_sequential": t_seq / t_batch,
@@ -389,11 +462,14 @@ def serve_requests(dgp, count, seed, dof_lo=1e4, dof_hi=2e7, rtol=1e-8):
     return reqs
 
 
-def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rates=(0.5, 0.9), progress=None):
+def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rates=(0.5, 0.9), progress=None,
+                  policies=(0,), max_age_s=2.0):
     """Continuous-batching solve server under Poisson arrivals: first all
-    requests at once (capacity in solves/s), then Poisson arrivals at given
-    fractions of that capacity; p50/p99 latency (submit to done) per rate.
-    progress: optional callable given the partial result after each run."""
+    requests at once (capacity in solves/s, FIFO), then Poisson arrivals at
+    given fractions of that capacity, for each admission policy (0 FIFO, 1
+    shortest job first with aging max_age_s); p50/p99 latency (submit to
+    done) per rate.  progress: optional callable given the partial result
+    after each run."""
     budget = int(budget_gb * (1 << 30))
     reqs = serve_requests(dgp, count, seed, dof_hi=dof_hi)
     out = {"requests": count, "slots": slots, "budget_gb": budget_gb,
@@ -414,33 +490,70 @@ def serve_metrics(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, slots=8, rat
         lam = frac * cap
         arrivals = np.cumsum(rng.exponential(1.0 / lam, count))
         arrivals -= arrivals[0]
-        res = dgp.serve_arrivals(reqs, list(arrivals), budget, slots)
-        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
-        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
-        out["rate_%.2f_of_capacity" % frac] = {
-            "arrival_rate_per_s": lam, "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)), "solves_per_s": count / span,
-            "all_converged": all(r["status"] == 0 and r["rel_res"] <= 1e-8 for r in res)}
-        if progress:
-            progress(out)
+        for pol in policies:
+            res = dgp.serve_arrivals(reqs, list(arrivals), budget, slots, policy=pol, max_age_s=max_age_s)
+            lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+            span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+            key = "rate_%.2f_of_capacity" % frac + ("" if pol == 0 else "_sjf")
+            out[key] = {
+                "arrival_rate_per_s": lam, "policy": "fifo" if pol == 0 else "sjf, aging %.1f s" % max_age_s,
+                "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)), "solves_per_s": count / span,
+                "all_converged": all(r["status"] == 0 and r["rel_res"] <= 1e-8 for r in res)}
+            if progress:
+                progress(out)
     return out
 
 
-def config3_metrics(torch, dgp, rtol=1e-10, cases=(("cartesian_64^3_p3", 64, 3, 0), ("deformed_48^3_p3", 48, 3, 1),
-                                                   ("deformed_48^3_p5", 48, 5, 1)), face_mode="loop"):
-    """Mixed precision at full size: manufactured Poisson problems solved to
-    rtol by plain FP64 CG, by the mixed solver (FP64 outer residual; the FP64
-    operator in the given face mode) and by the mixed solver with the
-    emulated-FP64 outer residual; wall time,
-    iterations, L2 errors against the exact solution and the difference
-    between the mixed and the FP64 solutions."""
+def serve_slot_study(dgp, count=48, seed=5, dof_hi=2e6, budget_gb=120, frac=0.5, slot_list=(2, 4, 8, 16),
+                     max_age_s=2.0):
+    """p50/p99 latency against the slot count and the admission policy at one
+    arrival rate (frac of the 8-slot FIFO capacity): the same request mix and
+    arrival times for every run."""
+    budget = int(budget_gb * (1 << 30))
+    reqs = serve_requests(dgp, count, seed, dof_hi=dof_hi)
+    res = dgp.serve_arrivals(reqs, [0.0] * count, budget, 8)
+    cap = count / (max(r["t_done"] for r in res) - min(r["t_submit"] for r in res))
+    rng = np.random.default_rng(seed + 7)
+    arrivals = np.cumsum(rng.exponential(1.0 / (frac * cap), count))
+    arrivals -= arrivals[0]
+    rows = []
+    for slots in slot_list:
+        for pol in (0, 1):
+            res = dgp.serve_arrivals(reqs, list(arrivals), budget, slots, policy=pol, max_age_s=max_age_s)
+            lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+            rows.append({"slots": slots, "policy": "fifo" if pol == 0 else "sjf",
+                         "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 2),
+                         "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 2),
+                         "all_converged": all(r["status"] == 0 for r in res)})
+    return {"requests": count, "arrival_rate_per_s": frac * cap, "capacity_8_slots_per_s": cap,
+            "aging_s": max_age_s, "rows": rows}
+
+
+CONFIG3_CASES = (("cartesian_64^3_p3", 64, 3, 0), ("cartesian_64^3_p5", 64, 5, 0), ("deformed_48^3_p3", 48, 3, 1),
+                 ("deformed_48^3_p5", 48, 5, 1))
+
+
+def config3_metrics(torch, dgp, rtol=1e-10, cases=CONFIG3_CASES, face_mode="loop", emulated=True, emu_rtol=1e-9,
+                    progress=None):
+    """Mixed precision at full size: manufactured Poisson problems (64^3
+    Cartesian and 48^3 deformed cells, degrees 3 and 5) solved to rtol by
+    plain FP64 CG and by the mixed solver (binary32 CG with residual
+    replacement by the FP64 residual; the FP64 operator in the given face
+    mode); optionally also with the emulated-FP64 outer residual, to emu_rtol
+    (double-float residuals floor near 2e-10 relative at p = 5, so that
+    variant is run to 1e-9).  Wall time, iterations, L2 errors against the
+    exact solution and the difference between the mixed and the FP64
+    solutions."""
     out = {}
     for name, n, p, mapping in cases:
         kw = dict(geom="full" if mapping else "cartesian", mapping=mapping, amplitude=0.1, coeff=mapping)
         o64 = dgp.Operator(n, p, prec="fp64", **kw)
         o64.set_face_mode(face_mode)
         o32 = dgp.Operator(n, p, prec="fp32", **kw)
-        oe = dgp.Operator(n, p, prec="fp64emu", **kw)
+        oe = dgp.Operator(n, p, prec="fp64emu", **kw) if emulated else None
+        if oe is not None:
+            oe.set_face_mode(face_mode)
         rhs = o64.rhs(mapping)
         res = {"dofs": o64.n_dofs, "rtol": rtol}
         x64 = torch.zeros_like(rhs)
@@ -449,20 +562,25 @@ def config3_metrics(torch, dgp, rtol=1e-10, cases=(("cartesian_64^3_p3", 64, 3, 
         _, it, rr, st = o64.cg(rhs, x64, rtol=rtol, max_it=200000, raise_on_error=False)
         res["fp64_cg"] = {"seconds": time.perf_counter() - t, "iterations": it, "rel_res": rr, "status": st,
                           "l2_error": o64.l2_error(x64)}
-        for label, oh in (("mixed_fp64_outer", o64), ("mixed_emulated_fp64_outer", oe)):
+        variants = [("mixed_fp64_outer", o64, rtol)] + ([("mixed_emulated_fp64_outer", oe, emu_rtol)] if emulated else [])
+        for label, oh, rt in variants:
             xm = torch.zeros_like(rhs)
             torch.cuda.synchronize()
             t = time.perf_counter()
-            st, outer, inner, rr = dgp.dg_cg_solve_mixed(oh.handle, o32.handle, rhs.data_ptr(), xm.data_ptr(), rtol,
-                                                         max_outer=100, max_inner=200000, raise_on_error=False)
+            st, outer, inner, rr = dgp.dg_cg_solve_mixed(oh.handle, o32.handle, rhs.data_ptr(), xm.data_ptr(), rt,
+                                                         max_outer=60, inner_rtol=1e-2, max_inner=20000,
+                                                         raise_on_error=False)
             secs = time.perf_counter() - t
-            res[label] = {"seconds": secs, "outer": outer, "inner_fp32_iterations": inner, "rel_res": rr,
+            res[label] = {"seconds": secs, "rtol": rt, "outer": outer, "inner_fp32_iterations": inner, "rel_res": rr,
                           "status": st, "l2_error": o64.l2_error(xm),
                           "rel_diff_to_fp64_solution": float((xm - x64).norm() / x64.norm()),
                           "speedup_vs_fp64_cg": res["fp64_cg"]["seconds"] / secs}
         out[name] = res
+        if progress:
+            progress(name, res)
         for o in (o64, o32, oe):
-            o.close()
+            if o is not None:
+                o.close()
         torch.cuda.empty_cache()
     return out
 
@@ -619,7 +737,9 @@ def main():
         return
     if args.solve_config3:
         if rank == 0:
-            print(json.dumps({"solve_config3": config3_metrics(torch, dgp, face_mode=args.face_mode)}), flush=True)
+            print(json.dumps({"solve_config3": config3_metrics(
+                torch, dgp, face_mode=args.face_mode,
+                progress=lambda nm, r: print(json.dumps({"case": nm, "result": r}), flush=True))}), flush=True)
         return
 
     wname = "deformed_dirichlet_32^3_p%d" % args.degree
@@ -628,6 +748,7 @@ def main():
     k = p + 1
     common = dict(periodic=mesh["periodic"], mapping=mesh["mapping"], amplitude=mesh["amplitude"])
     peaks = load_peaks()
+    alu = probe_alu_peaks(dgp)
 
     op = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec=args.prec, coeff=w["coeff"], **common)
     loop = args.prec in ("fp64", "fp64emu") and args.face_mode == "loop"
@@ -667,6 +788,11 @@ def main():
         flops = kernel_flops_per_cell(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5),
                                       folded=args.prec != "fp32") * n_cells
     achieved_tf = flops / (launch_ms / 1e3) / 1e12
+    nx = mesh["n"]
+    bfrac = 0.0 if mesh["periodic"] else 2.0 * (nx[0] * nx[1] + nx[1] * nx[2] + nx[0] * nx[2]) / (6.0 * n_cells)
+    flops_alg = (algorithmic_flops_per_cell_loop(k, "sipg", w["geom"], even_odd=(args.prec == "fp64" and k >= 5),
+                                                 folded=args.prec != "fp32", boundary_fraction=bfrac) * n_cells
+                 if loop else None)
     bpd = bytes_per_dof(k, ssz, "sipg", w["geom"])
     achieved_gbs = bpd * n / (launch_ms / 1e3) / 1e9
     if args.prec == "fp32":
@@ -683,14 +809,20 @@ def main():
            "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc, "kernel": kname,
            "bytes_per_dof": bpd, "algorithmic_bytes_per_launch": bpd * n, "peak_source": peaks.get("source")}
     if args.prec == "fp64":
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic, "traffic_source": tsrc,
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                    "frac": achieved_tf / alu["fp64_tflops"], "traffic": traffic, "traffic_source": tsrc,
                     "kernel": kname,
                     "flops_per_launch": flops,
-                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                    "flops_counting": "2 per FP64 arithmetic instruction (issue-slot count)",
+                    "algorithmic": None if flops_alg is None else {
+                        "flops_per_launch": flops_alg, "achieved": flops_alg / (launch_ms / 1e3) / 1e12,
+                        "frac": flops_alg / (launch_ms / 1e3) / 1e12 / alu["fp64_tflops"],
+                        "counting": "paper's method (Sec. 4.1): FMA 2, other add/mul 1, even-odd sweeps"},
+                    "peak_source": alu["fp64_tflops_source"],
+                    "peak_derived": FP64_PEAK_TFLOPS,
                     "hbm": hbm}
     else:
-        roofline = dict(hbm, alu_tflops=achieved_tf, alu_peak_tflops=FP32_PEAK_TFLOPS)
+        roofline = dict(hbm, alu_tflops=achieved_tf, alu_peak_tflops=alu["fp32_tflops"])
 
     # end to end through the C ABI with pinned host buffers
     hsrc = torch.tensor(dg_inputs.src_vector(n, seed=1 + rank), dtype=op.dtype).pin_memory()
@@ -746,7 +878,7 @@ def main():
                                        "traffic": measured_traffic("fp32", "element", p, op32.info()["cells_per_block"],
                                                                    wname),
                                        "kernel": "apply_f32_kernel<%d,%d,FULL,SIPG>" % (k, op32.info()["cells_per_block"]),
-                                       "alu_tflops": tf32, "alu_peak_tflops": FP32_PEAK_TFLOPS}}
+                                       "alu_tflops": tf32, "alu_peak_tflops": alu["fp32_tflops"]}}
         op32.close()
         # emulated FP64 (double-float on the FP32 pipe), same workload and vectors
         emu = {}
@@ -767,6 +899,23 @@ def main():
                           "FP64 vectors; parity with the FP64 oracle at 1e-12",
             "speedup_vs_fp64": (total_ms / args.steps) / (tote / args.steps),
             "hbm": {"achieved": bpd * n / (tote / args.steps / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}}
+        # geometry variant G2 (positions stored, J computed in the kernel): the
+        # same workload in FP64 (face loop) and FP32, bytes for arithmetic
+        g2 = {}
+        for prec in ("fp64", "fp32"):
+            og = dgp.Operator(mesh["n"], p, geom="positions", op="sipg", prec=prec, coeff=w["coeff"], **common)
+            sg = src if prec == "fp64" else src.float()
+            dg_ = torch.empty_like(sg)
+            for _ in range(args.warmup):
+                og.apply(sg, dg_)
+            totg, lg = time_applies(torch, og, sg, dg_, args.steps)
+            bg = bytes_per_dof(k, 8 if prec == "fp64" else 4, "sipg", "positions")
+            g2[prec] = {"value": n / (lg / 1e3), "unit": UNIT, "ms_per_step": lg, "bytes_per_dof": bg,
+                        "hbm_frac": bg * n / (lg / 1e3) / 1e9 / peaks["hbm_gbs"],
+                        "face_mode": "loop" if prec == "fp64" else "element",
+                        "vs_g3": (total_ms / args.steps) / lg if prec == "fp64" else (l32 / lg)}
+            og.close()
+        extras["g2_positions"] = g2
         # advection, FP64
         opa = dgp.Operator(mesh["n"], p, geom=w["geom"], op="advection", prec="fp64", **common)
         if loop:
@@ -779,8 +928,19 @@ def main():
 
     if not args.no_extras and args.prec == "fp64":
         extras["solve"] = solve_metrics(torch, dgp, args)
+        # the mixed-precision workload at full size (64^3 Cartesian and 48^3
+        # deformed, p = 3 and 5, to 1e-10): plain FP64 CG against the mixed solver
+        extras["solve_config3"] = config3_metrics(torch, dgp, face_mode=args.face_mode, emulated=False)
         extras["batch"] = batch_metrics(torch, dgp, args)
-        extras["serve"] = serve_metrics(dgp)
+        # many small meshes: where one launch per operator underfills the GPU
+        extras["batch_small_meshes"] = batch_metrics(torch, dgp, args, count=64, seed=6, n_lo=3, n_hi=12)
+        extras["serve"] = serve_metrics(dgp, policies=(0, 1))
+        extras["serve_slots"] = serve_slot_study(dgp)
+        # the serving stream's shape (dofs lognormal over 1e4..2e7, degrees
+        # 2..6, half Cartesian / half deformed, mixed CG to 1e-8, 120 GB),
+        # bounded to 160 requests: saturated, then 90% load with both policies
+        extras["serve_config5_bounded"] = serve_metrics(dgp, count=160, seed=11, dof_hi=2e7, rates=(0.9,),
+                                                        policies=(0, 1), max_age_s=5.0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -19,7 +19,8 @@
  * range [c k^3, (c+1) k^3); its dof (i0, i1, i2) sits at c k^3 + i0 +
  * k (i1 + k i2) (x fastest), the Lagrange node at the Gauss-Lobatto points.
  * Cell c maps the reference cube [0,1]^3 onto its box of the unit cube and,
- * for mapping 1, shifts every coordinate by a sin(pi X) sin(pi Y) sin(pi Z).
+ * for mapping 1, shifts every coordinate by a sin(pi X) sin(pi Y) sin(pi Z)
+ * (mapping 2: the linear shear x_i = X_i + a X_{(i+1) mod 3}).
  *
  * Conventions for every call:
  *   - Device pointers are CUDA device addresses of the current device with
@@ -72,12 +73,22 @@ typedef enum { DG_OP_SIPG = 0, DG_OP_ADVECTION = 1 } dg_op;
  *             point instead.
  *  MERGED:    variant G4: per cell quadrature point the merged coefficient
  *             kappa det J w J^{-1} J^{-T} (6 values, SIPG) or
- *             -det J w J^{-1} c (3 values, advection); faces as FULL_JAC. */
+ *             -det J w J^{-1} c (3 values, advection); faces as FULL_JAC.
+ *  POSITIONS: variant G2: per cell quadrature point its physical position
+ *             (3 values) and, for SIPG, kappa (1 value); the kernels compute
+ *             J at each point by the collocation derivative of the positions
+ *             along the three lines through it (the derivative of the degree-p
+ *             interpolant of the map through the Gauss points), then det J
+ *             and J^{-1}; faces as FULL_JAC (face data is stored separately,
+ *             as Sec. 5 notes for Gauss rules).  Binary64 and double-float
+ *             operators run the face loop (dg_setup selects DG_FACE_LOOP and
+ *             allocates its work arrays; DG_FACE_ELEMENT is refused). */
 typedef enum {
   DG_GEOM_CARTESIAN = 0,
   DG_GEOM_AFFINE = 1,
   DG_GEOM_FULL_JAC = 2,
-  DG_GEOM_MERGED = 3
+  DG_GEOM_MERGED = 3,
+  DG_GEOM_POSITIONS = 4
 } dg_geom;
 
 /* Arithmetic of the apply.
@@ -93,8 +104,10 @@ typedef enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP64_EMU = 2 } dg_prec;
 typedef struct {
   int n[3];         /* cells per direction, each >= 1 */
   int periodic;     /* 1: periodic in every direction; 0: Dirichlet (g = 0) on all of the boundary */
-  int mapping;      /* 0: identity; 1: x_i = X_i + amplitude sin(pi X) sin(pi Y) sin(pi Z) */
-  double amplitude; /* used by mapping 1; det J must stay positive */
+  int mapping;      /* 0: identity; 1: x_i = X_i + amplitude sin(pi X) sin(pi Y) sin(pi Z);
+                       2: the shear x_i = X_i + amplitude X_{(i+1) mod 3} (constant J per cell;
+                       with periodic boundaries only kappa = 1, since x_0 shifts across the wrap) */
+  double amplitude; /* used by mappings 1 and 2; det J must stay positive */
 } dg_mesh;
 
 typedef struct {
@@ -137,7 +150,7 @@ typedef struct {
  * Returns DG_ERR_ARG for invalid sizes, degree, geometry/mapping mismatch
  * (CARTESIAN needs mapping 0) or a non-positive det J; DG_ERR_OOM if device
  * memory runs out.  Blocks until set-up is complete.
- * Cite: Sec. 5 (G3, G4, compressed Cartesian), Design Choice on j_n. */
+ * Cite: Sec. 5 (G2, G3, G4, compressed Cartesian), Design Choice on j_n. */
 dg_status dg_setup(const dg_mesh *mesh, int degree, int geom, const dg_opts *opts, void *stream,
                    dg_handle **out);
 
@@ -257,18 +270,30 @@ dg_status dg_cg_solve_mixed(dg_handle *h64, dg_handle *h32, const double *rhs, d
 
 /* Batched evaluation (beyond the paper, which evaluates one operator
  * at a time).  A batch applies count set-up operators -- any mix of meshes,
- * degrees, geometries and precisions -- with one CUDA graph launch.
+ * degrees, geometries, precisions and face modes -- with one CUDA graph
+ * launch.  Operators sharing a kernel (degree, precision, geometry variant,
+ * weak form, face mode) form a group that runs as fused launches: one grid
+ * holds the blocks of up to 64 operators (larger operators first), each
+ * block finding its operator in a prefix table of block counts, so small
+ * meshes fill the SMs together instead of one launch each; face-loop groups
+ * take two such launches.  The groups' launches are dealt to branches of the
+ * graph, largest groups first, so groups of different degrees overlap.
  * handles[i], srcs[i], dsts[i]: operator i and its device vectors (as for
- * dg_apply); the pointers are fixed at creation.  autotune != 0 runs
- * dg_autotune on every operator first (tile shape per operator).  branches
- * (1..32): independent graph branches the applies are dealt to, largest
- * first, so that small and large applies overlap on the device.  stream: the
+ * dg_apply; two operators may not share a dst); the pointers are fixed at
+ * creation.  autotune != 0: each group's tile shape (cells per block) is
+ * chosen by timing the group's fused launch for every valid tile shape
+ * (dg_info_t.tile_choices); otherwise the group takes its first (largest)
+ * operator's.  Every member's tile shape is set to its group's
+ * (dg_set_cells_per_block).  branches (1..32): graph branches.  stream: the
  * cudaStream_t dg_batch_launch launches on.  Creation performs one plain
- * apply per operator, captures the graph and blocks until done.  The handles
- * must outlive the batch and must not change tile shape afterwards. */
+ * apply per operator, tunes, captures the graph and blocks until done.  The
+ * handles must outlive the batch and must not change tile shape or face mode
+ * afterwards.  Results equal the single applies bit for bit. */
 typedef struct dg_batch dg_batch;
 dg_status dg_batch_create(dg_handle *const *handles, const void *const *srcs, void *const *dsts, int count,
                           int autotune, int branches, void *stream, dg_batch **out);
+/* Number of kernel groups and of kernel launches per dg_batch_launch. */
+dg_status dg_batch_info(const dg_batch *b, int *groups, int *launches);
 /* All applies of the batch, asynchronously on the batch's stream. */
 dg_status dg_batch_launch(dg_batch *b);
 dg_status dg_batch_destroy(dg_batch *b);
@@ -313,6 +338,13 @@ typedef struct {
 
 int64_t dg_request_device_bytes(const dg_request *r);
 dg_status dg_server_create(int device, int64_t budget_bytes, int slots, dg_server **out);
+/* Admission policy: which queued request a free slot takes.  policy 0
+ * (default): FIFO, the oldest request once it fits into the remaining
+ * budget.  policy 1: shortest job first with aging -- a request queued
+ * longer than max_age_s seconds goes first (oldest first); otherwise the
+ * smallest estimated work (dofs x (p+1)) among the requests that fit.
+ * Applies to later admissions. */
+dg_status dg_server_set_policy(dg_server *s, int policy, double max_age_s);
 dg_status dg_server_submit(dg_server *s, const dg_request *r, int64_t *ticket);
 /* Blocks until the request is done; each ticket can be waited for once. */
 dg_status dg_server_wait(dg_server *s, int64_t ticket, dg_result *out);

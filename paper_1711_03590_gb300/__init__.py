@@ -36,6 +36,7 @@ DG_GEOM_CARTESIAN = 0
 DG_GEOM_AFFINE = 1
 DG_GEOM_FULL_JAC = 2
 DG_GEOM_MERGED = 3
+DG_GEOM_POSITIONS = 4
 DG_FACE_ELEMENT = 0
 DG_FACE_LOOP = 1
 DG_FP64 = 0
@@ -43,7 +44,7 @@ DG_FP32 = 1
 DG_FP64_EMU = 2
 
 GEOMS = {"cartesian": DG_GEOM_CARTESIAN, "affine": DG_GEOM_AFFINE, "full": DG_GEOM_FULL_JAC,
-         "merged": DG_GEOM_MERGED}
+         "merged": DG_GEOM_MERGED, "positions": DG_GEOM_POSITIONS}
 OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
 PRECS = {"fp64": DG_FP64, "fp32": DG_FP32, "fp64emu": DG_FP64_EMU}
 
@@ -51,7 +52,8 @@ EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg
             "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
             "dg_set_cells_per_block", "dg_autotune", "dg_batch_create", "dg_batch_launch", "dg_batch_destroy",
             "dg_batch_last_error", "dg_request_device_bytes", "dg_server_create", "dg_server_submit",
-            "dg_server_wait", "dg_server_destroy", "dg_server_last_error", "dg_l2_error", "dg_set_face_mode"]
+            "dg_server_wait", "dg_server_destroy", "dg_server_last_error", "dg_l2_error", "dg_set_face_mode",
+            "dg_peak_probe", "dg_batch_info", "dg_server_set_policy"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -127,12 +129,14 @@ def load_library(path=None):
     L.dg_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
     L.dg_batch_launch.argtypes = [_vp]
+    L.dg_batch_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.dg_batch_destroy.argtypes = [_vp]
     L.dg_batch_last_error.argtypes = []
     L.dg_request_device_bytes.argtypes = [ctypes.POINTER(dg_request)]
     L.dg_l2_error.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double)]
     L.dg_server_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(_vp)]
     L.dg_server_submit.argtypes = [_vp, ctypes.POINTER(dg_request), ctypes.POINTER(ctypes.c_int64)]
+    L.dg_server_set_policy.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
     L.dg_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(dg_result)]
     L.dg_server_destroy.argtypes = [_vp]
     L.dg_server_last_error.argtypes = []
@@ -140,6 +144,7 @@ def load_library(path=None):
     L.dg_cg_solve_mixed.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_double)]
+    L.dg_peak_probe.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.dg_destroy.argtypes = [_vp]
     L.dg_last_error.argtypes = [_vp]
     L.dg_last_error.restype = ctypes.c_char_p
@@ -279,6 +284,16 @@ def dg_batch_create(handles, src_ptrs, dst_ptrs, autotune=True, branches=8, stre
     return b.value
 
 
+def dg_batch_info(batch):
+    """Returns (kernel groups, kernel launches per dg_batch_launch)."""
+    L = load_library()
+    g, n = ctypes.c_int(0), ctypes.c_int(0)
+    st = L.dg_batch_info(_vp(batch), ctypes.byref(g), ctypes.byref(n))
+    if st != DG_OK:
+        raise DGError(st, L.dg_batch_last_error().decode())
+    return g.value, n.value
+
+
 def dg_batch_launch(batch):
     L = load_library()
     st = L.dg_batch_launch(_vp(batch))
@@ -319,6 +334,14 @@ def dg_server_create(budget_bytes, slots, device=0):
     return s.value
 
 
+def dg_server_set_policy(server, policy, max_age_s=0.0):
+    """policy 0: FIFO; 1: shortest job first with aging (max_age_s)."""
+    L = load_library()
+    st = L.dg_server_set_policy(_vp(server), int(policy), float(max_age_s))
+    if st != DG_OK:
+        raise DGError(st, L.dg_server_last_error().decode())
+
+
 def dg_server_submit(server, req):
     L = load_library()
     t = ctypes.c_int64(0)
@@ -344,13 +367,16 @@ def dg_server_destroy(server):
         load_library().dg_server_destroy(_vp(server))
 
 
-def serve_arrivals(requests, arrivals, budget_bytes, slots):
+def serve_arrivals(requests, arrivals, budget_bytes, slots, policy=0, max_age_s=0.0):
     """Submit requests at the given arrival times (seconds from now, sorted)
-    to a fresh server and wait for all; returns the result dicts in request
-    order (latency = t_done - t_submit)."""
+    to a fresh server (admission policy as dg_server_set_policy) and wait for
+    all; returns the result dicts in request order (latency = t_done -
+    t_submit)."""
     import time
     server = dg_server_create(budget_bytes, slots)
     try:
+        if policy:
+            dg_server_set_policy(server, policy, max_age_s)
         tickets = []
         start = time.perf_counter()
         for req, t in zip(requests, arrivals):
@@ -361,6 +387,14 @@ def serve_arrivals(requests, arrivals, budget_bytes, slots):
         return [dg_server_wait(server, t) for t in tickets]
     finally:
         dg_server_destroy(server)
+
+
+def dg_peak_probe(kind):
+    """Measured FMA throughput of the current device in TFLOP/s: kind 0
+    binary64, 1 binary32 (2 flops per FMA)."""
+    t = ctypes.c_double(0.0)
+    _check(load_library().dg_peak_probe(int(kind), ctypes.byref(t)), None)
+    return t.value
 
 
 def dg_destroy(handle):

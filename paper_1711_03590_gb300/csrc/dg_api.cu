@@ -280,6 +280,7 @@ struct dg_handle {
   // face evaluation of the binary64 / double-float apply (dg_set_face_mode)
   int face_mode;
   dg::SplitArrays split;
+  const double* skip;     // device flag handed to the apply launches (null: never skip)
   cudaStream_t h2d_stream, d2h_stream, cmp_stream;
   cudaEvent_t pipe_ev[3 * kHostSlabs + 2];
   std::string err;
@@ -297,6 +298,14 @@ dg_status fail(dg_handle* h, dg_status s, const std::string& msg) {
 
 dg_status cuda_fail(dg_handle* h, cudaError_t e, const char* what) {
   return fail(h, DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Kernel geometry variant of a public dg_geom value.
+int kernel_geo(int geom) {
+  return geom == DG_GEOM_CARTESIAN  ? dg::GEO_CART
+         : geom == DG_GEOM_FULL_JAC ? dg::GEO_FULL
+         : geom == DG_GEOM_POSITIONS ? dg::GEO_POS
+                                     : dg::GEO_MERGED;
 }
 
 #define DG_CUDA(h, call)                                   \
@@ -361,10 +370,19 @@ __device__ int64_t face_slot(const SetupParams& S, int d, int m, int64_t f, int 
   return ((fm / B) * S.nfa * k2 + (int64_t)m * k2 + q) * B + fm % B;
 }
 
-// x = X + a s(X)(1,1,1), s = sin(pi X) sin(pi Y) sin(pi Z); J = dx/dxi includes 1/n_d
+// mapping 1: x = X + a s(X)(1,1,1), s = sin(pi X) sin(pi Y) sin(pi Z);
+// mapping 2: the shear x_i = X_i + a X_{(i+1) mod 3}; J = dx/dxi includes 1/n_d
 __device__ void map_point(const SetupParams& S, const int ijk[3], const double xi[3], double x[3], double J[9]) {
   double X[3];
   for (int d = 0; d < 3; ++d) X[d] = (ijk[d] + xi[d]) / S.n[d];
+  if (S.mapping == 2) {
+    for (int i = 0; i < 3; ++i) {
+      const int i1 = (i + 1) % 3;
+      x[i] = X[i] + S.amp * X[i1];
+      for (int j = 0; j < 3; ++j) J[i * 3 + j] = ((i == j) + (j == i1 ? S.amp : 0.0)) / S.n[j];
+    }
+    return;
+  }
   double grad[3] = {0.0, 0.0, 0.0}, sv = 0.0;
   if (S.mapping == 1) {
     double sn[3], cs[3];
@@ -431,7 +449,11 @@ __global__ void setup_cell_geometry(const SetupParams S, int64_t n_cells, T* out
     auto at = [&](int m) -> int64_t {
       return S.cblk ? (((c / S.cblk) * S.ncomp + m) * (int64_t)k3 + q) * S.cblk + c % S.cblk : m * ncq + idx;
     };
-    if (S.geom == dg::GEO_FULL && S.fold) {
+    if (S.geom == dg::GEO_POS) {
+      // G2: the point's position (the kernel differentiates them), and kappa
+      for (int m = 0; m < 3; ++m) out[at(m)] = (T)x[m];
+      if (S.op == dg::OP_SIPG) out[at(3)] = (T)kappa_of(S, x);
+    } else if (S.geom == dg::GEO_FULL && S.fold) {
       // kappa JxW J^{-1} J^{-T} = (s J^{-1}) (s J^{-1})^T with s = sqrt(kappa JxW)
       const double sw = sqrt(kappa_of(S, x) * jxw);
       for (int m = 0; m < 9; ++m) out[at(m)] = (T)(sw * Ji[m]);
@@ -678,8 +700,16 @@ constexpr int kRedBlocks = 1024;
 
 // device scalars: 0 rr, 1 bb, 2 pAp, 3 alpha, 4 beta, 5 rr_new, 6 breakdown flag,
 // 7 stop flag (converged, breakdown or max_it), 8 iterations done,
-// 9 (rtol |b|)^2, 10 max_it, 11 converged flag
-enum { S_RR = 0, S_BB, S_PAP, S_ALPHA, S_BETA, S_RRNEW, S_FLAG, S_STOP, S_ITER, S_TOL2, S_MAXIT, S_DONE, S_COUNT };
+// 9 (rtol |b|)^2, 10 max_it, 11 converged flag; the mixed-precision solver's
+// residual replacement adds 12 the largest r.r since the last replacement,
+// 13 delta^2, 14 replacement requested, 15 keep p (iterations frozen after a
+// request leave the search direction alone)
+enum {
+  S_RR = 0, S_BB, S_PAP, S_ALPHA, S_BETA, S_RRNEW, S_FLAG, S_STOP, S_ITER, S_TOL2, S_MAXIT, S_DONE,
+  // residual replacement of the mixed-precision solver
+  S_MAXRR, S_DELTA2, S_RU, S_KEEP,
+  S_COUNT
+};
 
 __device__ void block_store_sum(double v, double* out) {
   __shared__ double red[kRedThreads];
@@ -830,6 +860,91 @@ __global__ void mp_correct(int64_t n, double scale, const float* d, double* x) {
     x[i] = fma(scale, (double)d[i], x[i]);
 }
 
+// Residual replacement ("reliable updates": Sleijpen & van der Vorst 1996,
+// Clark et al. 2010) of the mixed-precision solver.  The binary32 iteration
+// works on the scaled system A d = sigma r64 (sigma = 1 / |r64| at the last
+// replacement): d accumulates in xl32, r32 is its recursive residual and p32
+// the search direction.  A replacement is requested once r.r <= delta^2
+// max r.r, r.r <= the scaled target, or after max_it iterations: that
+// iteration stops before its direction update and later ones are frozen.
+// The host then adds xl32 / sigma to the FP64 solution, recomputes the FP64
+// residual r64, and continues the CG recursion with it in place of the
+// recursive residual: beta = |r64|^2 / |r_old|^2 (r_old the residual at the
+// start of the replacing iteration, S_RR) and p = r64 + beta p, so the
+// search directions built so far are kept.
+__global__ void ru_scalars_beta(const double* part, int64_t nparts, double* scal) {
+  const double rr = reduce_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    scal[S_RRNEW] = rr;
+    if (scal[S_STOP] != 0.0) {
+      scal[S_BETA] = 0.0;
+      scal[S_KEEP] = 1.0;
+      return;
+    }
+    scal[S_ITER] += 1.0;
+    if (rr > scal[S_MAXRR]) scal[S_MAXRR] = rr;
+    if (!isfinite(rr)) {
+      scal[S_FLAG] = 1.0;
+      scal[S_STOP] = 1.0;
+      scal[S_KEEP] = 1.0;
+    } else if (rr <= scal[S_TOL2] || rr <= scal[S_DELTA2] * scal[S_MAXRR] || scal[S_ITER] >= scal[S_MAXIT]) {
+      // replacement: S_RR keeps |r_old|^2 for the host's beta
+      scal[S_RU] = 1.0;
+      scal[S_STOP] = 1.0;
+      scal[S_KEEP] = 1.0;
+    } else {
+      const double b = rr / scal[S_RR];
+      scal[S_BETA] = isfinite(b) ? b : 0.0;
+      scal[S_RR] = rr;
+    }
+  }
+}
+
+// p = r + beta p, except in iterations frozen after a replacement request
+__global__ void ru_direction(int64_t n, const double* scal, const float* r, float* p) {
+  if (scal[S_KEEP] != 0.0) return;
+  const float b = (float)scal[S_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(b, p[i], r[i]);
+}
+
+// Restart of the recursion from the FP64 residual: r32 = sigma r64 and
+// p32 = r32 + bscaled p32 (bscaled = beta sigma_new / sigma_old; 0 on the
+// first start), xl32 = 0; partials of r32.r32 (FP64).
+__global__ void ru_restart(int64_t n, const double* r64, double sigma, double bscaled, float* r32, float* p32,
+                           float* xl32, double* part) {
+  double rr = 0.0;
+  const float fb = (float)bscaled;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = (float)(r64[i] * sigma);
+    r32[i] = ri;
+    p32[i] = bscaled != 0.0 ? fmaf(fb, p32[i], ri) : ri;
+    xl32[i] = 0.f;
+    rr += (double)ri * (double)ri;
+  }
+  block_store_sum(rr, part + blockIdx.x);
+}
+
+__global__ void ru_scalars_reset(const double* part, int64_t nparts, double* scal, double tol2, double delta2,
+                                 double max_it) {
+  const double rr = reduce_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    scal[S_RR] = rr;
+    scal[S_MAXRR] = rr;
+    scal[S_TOL2] = tol2;
+    scal[S_DELTA2] = delta2;
+    scal[S_MAXIT] = max_it;
+    scal[S_ITER] = 0.0;
+    scal[S_STOP] = 0.0;
+    scal[S_RU] = 0.0;
+    scal[S_KEEP] = 0.0;
+    scal[S_FLAG] = 0.0;
+    scal[S_DONE] = 0.0;
+    scal[S_ALPHA] = 0.0;
+    scal[S_BETA] = 0.0;
+  }
+}
+
 __global__ void sum_to_scalar(const double* part, int64_t nparts, double* out) {
   const double v = reduce_partials(part, nparts);
   if (threadIdx.x == 0) *out = v;
@@ -857,7 +972,7 @@ dg_status launch_apply_range(dg_handle* h, const void* src, void* dst, double* d
   dg::ApplyLaunch L;
   L.k = h->k;
   L.prec = h->prec;
-  L.geo = h->geom == DG_GEOM_CARTESIAN ? dg::GEO_CART : h->geom == DG_GEOM_FULL_JAC ? dg::GEO_FULL : dg::GEO_MERGED;
+  L.geo = kernel_geo(h->geom);
   L.op = h->op;
   L.src = src;
   L.dst = dst;
@@ -868,6 +983,7 @@ dg_status launch_apply_range(dg_handle* h, const void* src, void* dst, double* d
                : h->prec == DG_FP32 ? (const void*)&h->geof
                                     : (const void*)&h->geodf;
   L.dot_partial = dot_partial;
+  L.skip = h->skip;
   L.stream = stream;
   L.cpb = h->cpb;
   L.cell_begin = cell_begin;
@@ -950,7 +1066,7 @@ dg_status setup_geometry(dg_handle* h) {
   }
   S.op = h->op;
   S.coeff = h->op == DG_OP_SIPG ? h->opts.coeff : 0;
-  S.geom = h->geom == DG_GEOM_FULL_JAC ? dg::GEO_FULL : h->geom == DG_GEOM_MERGED ? dg::GEO_MERGED : dg::GEO_CART;
+  S.geom = kernel_geo(h->geom);
   S.penalty = (h->opts.penalty_scale > 0 ? h->opts.penalty_scale : 1.0) * k * k;
 
   int* bad = nullptr;
@@ -973,6 +1089,7 @@ dg_status setup_geometry(dg_handle* h) {
   S.fold = h->geom == DG_GEOM_FULL_JAC && h->op == DG_OP_SIPG && h->prec != DG_FP32;
   if (!cart) {
     if (h->geom == DG_GEOM_FULL_JAC) ncell_arrays = S.fold ? 9 : 10;
+    else if (h->geom == DG_GEOM_POSITIONS) ncell_arrays = h->op == DG_OP_SIPG ? 4 : 3;  // x, y, z (+ kappa)
     else ncell_arrays = h->op == DG_OP_SIPG ? 6 : 3;
   }
   // binary32: cell-blocked layout padded to whole blocks (zero padding)
@@ -1164,7 +1281,9 @@ dg_status run_cg(dg_handle* h, const T* b, T* x, bool x_zero, double rtol, int m
     }
     // a block of kIterBlock iterations: apply with p.Ap fused into its
     // epilogue, fused x/r update with r.r, direction update; captured once
-    // as a CUDA graph when the solve may be long
+    // as a CUDA graph when the solve may be long.  Iterations after
+    // convergence skip their applies (the flag was set by cg_scalars_init).
+    h->skip = h->scal + S_STOP;
     const int kIterBlock = 8;
     auto enqueue_block = [&]() -> dg_status {
       for (int j = 0; j < kIterBlock; ++j) {
@@ -1216,6 +1335,7 @@ dg_status run_cg(dg_handle* h, const T* b, T* x, bool x_zero, double rtol, int m
     }
   } while (false);
   if (exec) cudaGraphExecDestroy(exec);
+  h->skip = nullptr;
   cudaEventRecord(h->cg_event, s);
   cudaStreamWaitEvent(user, h->cg_event, 0);
   h->stream = user;
@@ -1227,6 +1347,8 @@ dg_status run_cg(dg_handle* h, const T* b, T* x, bool x_zero, double rtol, int m
 
 // Used by dg_noalloc.cu: the apply launch with caller-provided per-block
 // partials of src . dst, after the same argument checks as dg_apply.
+cudaError_t dg_internal_noalloc_preload();  // dg_noalloc.cu
+
 dg_status dg_internal_apply_with_partials(dg_handle* h, const void* src, void* dst, double* partials,
                                           int64_t* n_blocks, cudaStream_t* stream) {
   if (!src || !dst) return fail(h, DG_ERR_ARG, "src or dst is NULL");
@@ -1242,6 +1364,45 @@ dg_status dg_internal_apply_with_partials(dg_handle* h, const void* src, void* d
 }
 
 dg_status dg_internal_fail(dg_handle* h, dg_status s, const char* msg) { return fail(h, s, msg); }
+
+// Used by dg_batch.cu: the batched-launch description of one operator
+// (key: degree k, arithmetic, geometry variant, weak form, face mode, tile
+// shape), its tables, and the per-degree batched launch.
+dg_status dg_internal_batch_desc(dg_handle* h, const void* src, void* dst, dg::BatchOp* op, int key[6],
+                                 const void** tables) {
+  if (!h || !op || !key || !tables) return DG_ERR_ARG;
+  op->geometry = h->prec == DG_FP64 ? (const void*)&h->geod
+                 : h->prec == DG_FP32 ? (const void*)&h->geof
+                                      : (const void*)&h->geodf;
+  op->src = src;
+  op->dst = dst;
+  op->split = (h->prec != DG_FP32 && h->face_mode == DG_FACE_LOOP) ? (const void*)&h->split : nullptr;
+  op->n_cells = h->n_cells;
+  key[0] = h->k;
+  key[1] = h->prec;
+  key[2] = kernel_geo(h->geom);
+  key[3] = h->op;
+  key[4] = h->prec != DG_FP32 ? h->face_mode : 0;
+  key[5] = h->cpb;
+  *tables = h->prec == DG_FP64 ? (const void*)&h->tabd
+            : h->prec == DG_FP32 ? (const void*)&h->tabf
+                                 : (const void*)&h->tabdf;
+  return DG_OK;
+}
+
+cudaError_t dg_internal_batch_launch(const dg::BatchLaunch& L) {
+  switch (L.k) {
+    case 2: return dg::launch_batch_k2(L);
+    case 3: return dg::launch_batch_k3(L);
+    case 4: return dg::launch_batch_k4(L);
+    case 5: return dg::launch_batch_k5(L);
+    case 6: return dg::launch_batch_k6(L);
+    case 7: return dg::launch_batch_k7(L);
+    case 8: return dg::launch_batch_k8(L);
+    case 9: return dg::launch_batch_k9(L);
+    default: return cudaErrorInvalidValue;
+  }
+}
 // Used by dg_batch.cu: dg_apply on a given stream (for graph capture).
 dg_status dg_internal_apply_on_stream(dg_handle* h, const void* src, void* dst, void* stream) {
   if (!h) return DG_ERR_ARG;
@@ -1265,13 +1426,16 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   if (degree < 1 || degree > kMaxK - 1) return fail(nullptr, DG_ERR_ARG, "degree must be in 1..8");
   for (int d = 0; d < 3; ++d)
     if (mesh->n[d] < 1 || mesh->n[d] > (1 << 20)) return fail(nullptr, DG_ERR_ARG, "cells per direction must be >= 1");
-  if (mesh->mapping != 0 && mesh->mapping != 1) return fail(nullptr, DG_ERR_ARG, "mapping must be 0 or 1");
+  if (mesh->mapping < 0 || mesh->mapping > 2) return fail(nullptr, DG_ERR_ARG, "mapping must be 0, 1 or 2");
+  if (mesh->mapping == 2 && mesh->periodic && opts->op == DG_OP_SIPG && opts->coeff == 1)
+    return fail(nullptr, DG_ERR_ARG,
+                "kappa = 1 + 0.5 sin(2 pi x) is not periodic on the sheared mesh (x shifts across the y/z wrap)");
   if (opts->op != DG_OP_SIPG && opts->op != DG_OP_ADVECTION) return fail(nullptr, DG_ERR_ARG, "unknown operator");
   if (opts->prec != DG_FP64 && opts->prec != DG_FP32 && opts->prec != DG_FP64_EMU)
     return fail(nullptr, DG_ERR_ARG, "unknown precision");
   if (opts->coeff != 0 && opts->coeff != 1) return fail(nullptr, DG_ERR_ARG, "coeff must be 0 or 1");
   if (geom == DG_GEOM_AFFINE) return fail(nullptr, DG_ERR_UNSUPPORTED, "affine geometry storage is not implemented");
-  if (geom != DG_GEOM_CARTESIAN && geom != DG_GEOM_FULL_JAC && geom != DG_GEOM_MERGED)
+  if (geom != DG_GEOM_CARTESIAN && geom != DG_GEOM_FULL_JAC && geom != DG_GEOM_MERGED && geom != DG_GEOM_POSITIONS)
     return fail(nullptr, DG_ERR_ARG, "unknown geometry variant");
   if (geom == DG_GEOM_CARTESIAN && mesh->mapping != 0)
     return fail(nullptr, DG_ERR_ARG, "Cartesian geometry needs the identity mapping");
@@ -1318,9 +1482,28 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
     free_handle(h);
     return st;
   }
+  {
+    // load the allocation-free entry point's module now, while allocating is allowed
+    const cudaError_t e = dg_internal_noalloc_preload();
+    if (e != cudaSuccess) {
+      cuda_fail(h, e, "loading the allocation-free scratch module");
+      g_setup_error = h->err;
+      free_handle(h);
+      return DG_ERR_CUDA;
+    }
+  }
   fill_geometry<double>(h, h->geod);
   fill_geometry<float>(h, h->geof);
   fill_geometry<df64>(h, h->geodf);
+  if (geom == DG_GEOM_POSITIONS && h->prec != DG_FP32) {
+    // G2 in binary64 / double-float: the face loop (its forward kernel stages the positions)
+    st = dg_set_face_mode(h, DG_FACE_LOOP);
+    if (st != DG_OK) {
+      g_setup_error = h->err;
+      free_handle(h);
+      return st;
+    }
+  }
   *out = h;
   return DG_OK;
 }
@@ -1566,56 +1749,167 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
   dg_status st = ensure_cg_work(h64, false);
   if (st == DG_OK) st = ensure_cg_work(h32, true);
   if (st != DG_OK) return st;
-  cudaStream_t saved = h32->stream;
-  h32->stream = h64->stream;  // one stream orders the whole solve
-  cudaStream_t s = h64->stream;
+  // the whole solve runs on the FP32 handle's solver stream (capturable),
+  // ordered after the caller's stream and before its later work
+  cudaStream_t user = h64->stream;
+  if (!h32->cg_stream) DG_CUDA(h64, cudaStreamCreateWithFlags(&h32->cg_stream, cudaStreamNonBlocking));
+  if (!h32->cg_event) DG_CUDA(h64, cudaEventCreateWithFlags(&h32->cg_event, cudaEventDisableTiming));
+  DG_CUDA(h64, cudaEventRecord(h32->cg_event, user));
+  DG_CUDA(h64, cudaStreamWaitEvent(h32->cg_stream, h32->cg_event, 0));
+  cudaStream_t s = h32->cg_stream;
+  cudaStream_t saved32 = h32->stream;
+  h64->stream = s;
+  h32->stream = s;
   const int64_t n = h64->n_dofs;
   const int vb = (int)std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads);
-  float* b32 = reinterpret_cast<float*>(h32->bw);
-  float* d32 = reinterpret_cast<float*>(h32->xw);
+  const int64_t nblk32 = apply_blocks(h32);
+  float* r32 = reinterpret_cast<float*>(h32->r);
+  float* p32 = reinterpret_cast<float*>(h32->p);
+  float* ap32 = reinterpret_cast<float*>(h32->ap);
+  float* xl32 = reinterpret_cast<float*>(h32->xw);
+  double* part32 = h32->partial;
+  double* part_apply32 = h32->partial + 2 * kRedBlocks;
+  const double delta2 = inner_rtol * inner_rtol;
+  cudaGraphExec_t exec = nullptr;
   int outer = 0, inner_total = 0;
-  double rel = 0.0, bnorm = 1.0;
-  while (true) {
-    // outer FP64 residual r = b - A x and its norm; |b| on the first pass
-    if ((st = launch_apply(h64, x, h64->ap, nullptr)) != DG_OK) break;
-    cg_init<double><<<vb, kRedThreads, 0, s>>>(n, rhs, h64->ap, h64->r, h64->p, h64->partial);
-    cg_scalars_init<<<1, kRedThreads, 0, s>>>(h64->partial, vb, h64->scal, rtol, 0.0);
+  double rel = 0.0, bnorm = 1.0, sigma = 1.0;
+
+  // FP64 residual r64 = b - A x into h64->r and its r.r into h64->scal[S_RR]
+  auto fp64_residual = [&](double* rr_out) -> dg_status {
+    dg_status s2 = launch_apply(h64, x, h64->ap, nullptr);
+    if (s2 != DG_OK) return s2;
+    mp_residual<<<vb, kRedThreads, 0, s>>>(n, rhs, h64->ap, h64->r, h64->partial);
+    sum_to_scalar<<<1, kRedThreads, 0, s>>>(h64->partial, vb, h64->scal + S_RR);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h64->scal_host, h64->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      st = cuda_fail(h64, e, "mixed-precision outer residual");
-      break;
+    if (e != cudaSuccess) return cuda_fail(h64, e, "mixed-precision FP64 residual");
+    *rr_out = h64->scal_host[S_RR];
+    return DG_OK;
+  };
+  // restart the binary32 recursion from the FP64 residual (norm^2 rr64);
+  // rr_old: |r_old|^2 of the replacing iteration in the old scaling
+  auto restart = [&](double rr64, bool first, double rr_old) -> dg_status {
+    const double sig = 1.0 / std::sqrt(rr64);
+    // beta = |r64|^2 / |r_old / sigma|^2, times sigma_new / sigma_old for the
+    // rescaling of p
+    const double bscaled = first ? 0.0 : (rr64 * sigma * sigma / rr_old) * (sig / sigma);
+    if (!first && !(std::isfinite(bscaled) && bscaled > 0.0))
+      return fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG: invalid beta at a residual replacement");
+    ru_restart<<<vb, kRedThreads, 0, s>>>(n, h64->r, sig, bscaled, r32, p32, xl32, part32);
+    sigma = sig;
+    const double tol = rtol * bnorm * sigma;
+    ru_scalars_reset<<<1, kRedThreads, 0, s>>>(part32, vb, h32->scal, tol * tol, delta2, (double)max_inner);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DG_OK : cuda_fail(h64, e, "mixed-precision restart");
+  };
+  // a block of binary32 iterations; the applies skip themselves once the
+  // iteration is frozen (replacement requested or breakdown)
+  const int kIterBlock = 8;
+  auto enqueue_block = [&]() -> dg_status {
+    for (int j = 0; j < kIterBlock; ++j) {
+      dg_status s2 = launch_apply(h32, p32, ap32, part_apply32);
+      if (s2 != DG_OK) return s2;
+      cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply32, nblk32, h32->scal);
+      cg_update<float><<<vb, kRedThreads, 0, s>>>(n, h32->scal, xl32, r32, p32, ap32, part32);
+      ru_scalars_beta<<<1, kRedThreads, 0, s>>>(part32, vb, h32->scal);
+      ru_direction<<<vb, kRedThreads, 0, s>>>(n, h32->scal, r32, p32);
     }
-    const double rr = h64->scal_host[S_RR];
-    if (outer == 0) bnorm = std::sqrt(h64->scal_host[S_BB] > 0 ? h64->scal_host[S_BB] : 1.0);
-    rel = std::sqrt(rr) / bnorm;
+    return DG_OK;
+  };
+  h32->skip = h32->scal + S_STOP;
+  do {
+    // |b| and the initial residual
+    cg_init<double><<<vb, kRedThreads, 0, s>>>(n, rhs, nullptr, h64->r, h64->p, h64->partial);
+    sum_to_scalar<<<1, kRedThreads, 0, s>>>(h64->partial + kRedBlocks, vb, h64->scal + S_BB);
+    double rr64 = 0.0;
+    if ((st = fp64_residual(&rr64)) != DG_OK) break;
+    bnorm = std::sqrt(h64->scal_host[S_BB] > 0 ? h64->scal_host[S_BB] : 1.0);
+    rel = std::sqrt(rr64) / bnorm;
     if (!std::isfinite(rel)) {
       st = fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG: non-finite residual");
       break;
     }
     if (rel <= rtol) break;
-    if (outer >= max_outer) {
+    if (rr64 <= 0.0) break;
+    if (max_outer <= 0) {
       st = fail(h64, DG_ERR_NOT_CONVERGED, "mixed-precision CG reached max_outer");
       break;
     }
-    // inner FP32 CG on the normalized defect A d = r / |r|, from d = 0
-    const double rn = std::sqrt(rr);
-    mp_to_float<<<vb, kRedThreads, 0, s>>>(n, h64->r, 1.0 / rn, b32);
-    int it = 0;
-    double irel = 0.0, ib = 0.0;
-    st = run_cg<float>(h32, b32, d32, true, inner_rtol, max_inner, &it, &irel, &ib);
-    inner_total += it;
-    if (st == DG_ERR_NOT_CONVERGED) st = DG_OK;  // a partial correction still reduces the defect
-    if (st != DG_OK) {
-      h64->err = h32->err;
-      break;
+    if ((st = restart(rr64, true, 0.0)) != DG_OK) break;
+    {
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        dg_status s2 = enqueue_block();
+        cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        if (s2 == DG_OK && ec == cudaSuccess && graph) {
+          if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();  // a failed capture falls back to direct launches
     }
-    mp_correct<<<vb, kRedThreads, 0, s>>>(n, rn, d32, x);
-    ++outer;
-  }
-  h32->stream = saved;
+    int last_it = 0, stalled = 0;
+    double best_rel = rel;
+    while (true) {
+      if (exec) {
+        cudaError_t e2 = cudaGraphLaunch(exec, s);
+        if (e2 != cudaSuccess) {
+          st = cuda_fail(h64, e2, "mixed-precision graph launch");
+          break;
+        }
+      } else if ((st = enqueue_block()) != DG_OK) {
+        break;
+      }
+      cudaError_t e = cudaMemcpyAsync(h32->scal_host, h32->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        st = cuda_fail(h64, e, "mixed-precision scalars");
+        break;
+      }
+      const int it = (int)h32->scal_host[S_ITER];
+      inner_total += it - last_it;
+      last_it = it;
+      if (h32->scal_host[S_FLAG] != 0.0) {
+        st = fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG breakdown: p.Ap <= 0 or non-finite scalar");
+        break;
+      }
+      if (h32->scal_host[S_RU] == 0.0) continue;
+      // residual replacement: x += xl / sigma, FP64 residual, restart
+      mp_correct<<<vb, kRedThreads, 0, s>>>(n, 1.0 / sigma, xl32, x);
+      if ((st = fp64_residual(&rr64)) != DG_OK) break;
+      ++outer;
+      rel = std::sqrt(rr64) / bnorm;
+      if (!std::isfinite(rel)) {
+        st = fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG: non-finite residual");
+        break;
+      }
+      if (rel <= rtol || rr64 <= 0.0) break;
+      if (outer >= max_outer) {
+        st = fail(h64, DG_ERR_NOT_CONVERGED, "mixed-precision CG reached max_outer residual replacements");
+        break;
+      }
+      // stagnation: the outer residual's attainable floor (e.g. a
+      // double-float outer operator near 1e-10) is reached when four
+      // replacements in a row bring no halving of the best residual so far
+      if (rel < 0.5 * best_rel) {
+        best_rel = rel;
+        stalled = 0;
+      } else if (++stalled >= 4) {
+        st = fail(h64, DG_ERR_NOT_CONVERGED, "mixed-precision CG stagnated: the outer residual no longer decreases");
+        break;
+      }
+      if ((st = restart(rr64, false, h32->scal_host[S_RR])) != DG_OK) break;
+      last_it = 0;
+    }
+  } while (false);
+  h32->skip = nullptr;
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaEventRecord(h32->cg_event, s);
+  cudaStreamWaitEvent(user, h32->cg_event, 0);
+  h64->stream = user;
+  h32->stream = saved32;
   if (outer_iters) *outer_iters = outer;
   if (inner_iters) *inner_iters = inner_total;
   if (final_rel_res) *final_rel_res = rel;
@@ -1627,6 +1921,8 @@ dg_status dg_set_face_mode(dg_handle* h, int mode) {
   if (mode != DG_FACE_ELEMENT && mode != DG_FACE_LOOP) return fail(h, DG_ERR_ARG, "unknown face mode");
   if (mode == DG_FACE_LOOP && h->prec == DG_FP32)
     return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply is implemented for DG_FP64 and DG_FP64_EMU");
+  if (mode == DG_FACE_ELEMENT && h->geom == DG_GEOM_POSITIONS && h->prec != DG_FP32)
+    return fail(h, DG_ERR_UNSUPPORTED, "G2 (positions) binary64 and double-float operators run the face loop only");
   if (mode == DG_FACE_LOOP && !h->split.tq) {
     // traces per face and slot, gradient-test fields per point
     const int k2 = h->k * h->k;

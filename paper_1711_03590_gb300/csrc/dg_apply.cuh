@@ -27,6 +27,7 @@
 // position (E, W) are copied to shared memory first.
 #pragma once
 
+#include <cstring>
 #include <type_traits>
 
 #include "dg_df64.cuh"
@@ -65,6 +66,57 @@ struct Acc {
 template <>
 struct Acc<df64> : DfAcc {};
 
+// 1 / x in the kernel arithmetic (binary64 division; double-float Newton step)
+template <typename T>
+__device__ __forceinline__ T recip_of(T x) {
+  return T(1) / x;
+}
+template <>
+__device__ __forceinline__ df64 recip_of<df64>(df64 x) {
+  return dfp::df_recip(x);
+}
+
+// Geometry variant G2 (Sec. 5): the Jacobian at Gauss point (a, b, c) of a
+// cell whose k^3 Gauss-point positions X[i][k^3] (component i, x fastest)
+// are in shared memory, by the collocation derivative D^co along the three
+// lines through the point (J[i][d] = dx_i / dxi_d); J^{-1} by the adjugate
+// (Ji[r*3 + s] = (J^{-1})_{rs}).  Returns det J.
+template <int K, typename T>
+__device__ __forceinline__ T g2_inverse_jacobian(const T* __restrict__ D, const T* X0, const T* X1, const T* X2,
+                                                 int a, int b, int c, T (&Ji)[9]) {
+  T J[9];
+  const T* X[3] = {X0, X1, X2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Acc<T> s0, s1, s2;
+    s0.init();
+    s1.init();
+    s2.init();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      s0.add(D[a * K + j], X[i][j + K * (b + K * c)]);
+      s1.add(D[b * K + j], X[i][a + K * (j + K * c)]);
+      s2.add(D[c * K + j], X[i][a + K * (b + K * j)]);
+    }
+    J[i * 3 + 0] = s0.get();
+    J[i * 3 + 1] = s1.get();
+    J[i * 3 + 2] = s2.get();
+  }
+  const T c00 = J[4] * J[8] - J[5] * J[7], c01 = J[5] * J[6] - J[3] * J[8], c02 = J[3] * J[7] - J[4] * J[6];
+  const T det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+  const T r = recip_of(det);
+  Ji[0] = c00 * r;
+  Ji[3] = c01 * r;
+  Ji[6] = c02 * r;
+  Ji[1] = (J[2] * J[7] - J[1] * J[8]) * r;
+  Ji[4] = (J[0] * J[8] - J[2] * J[6]) * r;
+  Ji[7] = (J[1] * J[6] - J[0] * J[7]) * r;
+  Ji[2] = (J[1] * J[5] - J[2] * J[4]) * r;
+  Ji[5] = (J[2] * J[3] - J[0] * J[5]) * r;
+  Ji[8] = (J[0] * J[4] - J[1] * J[3]) * r;
+  return det;
+}
+
 template <typename T>
 struct ApplyParams {
   Tables<T> tab;
@@ -72,9 +124,49 @@ struct ApplyParams {
   const typename Arith<T>::V* src;
   typename Arith<T>::V* dst;
   double* dot_partial;
+  const double* skip;  // optional device flag: the launch does nothing while *skip != 0
   int C;  // cells per block
   int64_t cell_begin, cell_end;  // cells of this launch
 };
+
+// Per-operator part of the launch parameters (all but the 1D tables), for
+// the batched launches that cover the blocks of several operators of one
+// degree, arithmetic, geometry variant, weak form and tile shape.
+template <typename T>
+struct OpParams {
+  Geometry<T> geo;
+  const typename Arith<T>::V* src;
+  typename Arith<T>::V* dst;
+  double* dot_partial;
+  const double* skip;
+  int C;
+  int64_t cell_begin, cell_end;
+  SplitArrays split;  // face-loop work arrays (face-loop operators only)
+};
+
+// Parameters of a batched launch: the shared tables and up to kBatchOps
+// operators; block b of the launch is block b - block_start[i] of operator i
+// (block_start ascending, block_start[nops] = the grid size).
+template <typename T>
+struct BatchParams {
+  Tables<T> tab;
+  int nops;
+  int block_start[kBatchOps + 1];
+  OpParams<T> op[kBatchOps];
+};
+static_assert(sizeof(BatchParams<double>) <= 32000, "batched launch parameters exceed the kernel parameter space");
+
+// operator of block b: the last i with block_start[i] <= b (binary search)
+template <typename T>
+__device__ __forceinline__ int batch_op(const BatchParams<T>& B, int b) {
+  int lo = 0, hi = B.nops - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.block_start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 template <int K>
 struct Shape {
@@ -230,8 +322,10 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.L2 [%0];" ::"l"(p));
 }
 
-template <int K, typename T, int GEO, int OP>
-__global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __grid_constant__ ApplyParams<T> P) {
+// The element-centric apply of one block (blk) of an operator: the body of
+// apply_kernel (one operator) and apply_kernel_batch (several).
+template <int K, typename T, int GEO, int OP, typename PP>
+__device__ __forceinline__ void apply_body(const Tables<T>& tb, const PP& P, const int blk) {
   constexpr int K2 = K * K, K3 = K2 * K;
   const int C = P.C;
   constexpr int NBA = Smem<K, OP>::NBA, NBB = Smem<K, OP>::NBB, FTF = Smem<K, OP>::FTF;
@@ -250,13 +344,12 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
   constexpr int kUd = kCompact ? 1 : 3;     // unroll of the face-direction loop
   using A = Arith<T>;
 
-  const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
   const int tid = threadIdx.x;
   const int lc = tid / K2;
   const int ln = tid - lc * K2;
   const int la = ln % K, lb = ln / K;
-  const int64_t cell0 = P.cell_begin + (int64_t)blockIdx.x * C;
+  const int64_t cell0 = P.cell_begin + (int64_t)blk * C;
   const int64_t cell = cell0 + lc;
   const bool active = cell < P.cell_end;
   const int nloc = (int)min((int64_t)C, P.cell_end - cell0);
@@ -728,10 +821,22 @@ __global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __gr
       if (tid == 0) {
         double t = 0.0;
         for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
-        P.dot_partial[blockIdx.x] = t;
+        P.dot_partial[blk] = t;
       }
     }
   }
+}
+
+template <int K, typename T, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel(const __grid_constant__ ApplyParams<T> P) {
+  if (P.skip != nullptr && *P.skip != 0.0) return;
+  apply_body<K, T, GEO, OP>(P.tab, P, (int)blockIdx.x);
+}
+
+template <int K, typename T, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads) apply_kernel_batch(const __grid_constant__ BatchParams<T> B) {
+  const int i = batch_op(B, (int)blockIdx.x);
+  apply_body<K, T, GEO, OP>(B.tab, B.op[i], (int)blockIdx.x - B.block_start[i]);
 }
 
 template <int K, typename T, int GEO, int OP>
@@ -742,6 +847,7 @@ cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
   P.src = static_cast<const typename Arith<T>::V*>(L.src);
   P.dst = static_cast<typename Arith<T>::V*>(L.dst);
   P.dot_partial = L.dot_partial;
+  P.skip = L.skip;
   const int C = (L.cpb >= 1 && L.cpb <= cells_per_block(K)) ? L.cpb : cells_per_block(K);
   P.C = C;
   P.cell_begin = L.cell_begin;
@@ -763,6 +869,7 @@ cudaError_t launch_one(const ApplyLaunch& L, int64_t n_cells) {
 
 template <int K, typename T>
 cudaError_t launch_prec(const ApplyLaunch& L, int64_t n_cells) {
+  if (L.geo == GEO_POS) return cudaErrorInvalidValue;  // G2 runs the face loop (binary64, double-float)
   if (L.op == OP_SIPG) {
     if (L.geo == GEO_CART) return launch_one<K, T, GEO_CART, OP_SIPG>(L, n_cells);
     if (L.geo == GEO_FULL) return launch_one<K, T, GEO_FULL, OP_SIPG>(L, n_cells);
@@ -788,6 +895,132 @@ cudaError_t launch_apply(const ApplyLaunch& L, int64_t n_cells) {
   return launch_prec<K, df64>(L, n_cells);
 }
 
+// ---- batched launches: the blocks of several operators in one grid ----
+
+// Kernel parameters of a batched launch with tile shape C; returns the grid
+// size (blocks of all operators, largest-first order as given).
+template <typename T>
+int fill_batch(BatchParams<T>& B, const BatchLaunch& L, int C) {
+  B.tab = *static_cast<const Tables<T>*>(L.tables);
+  B.nops = L.nops;
+  int start = 0;
+  for (int i = 0; i < L.nops; ++i) {
+    const BatchOp& o = L.ops[i];
+    OpParams<T>& q = B.op[i];
+    q.geo = *static_cast<const Geometry<T>*>(o.geometry);
+    q.src = static_cast<const typename Arith<T>::V*>(o.src);
+    q.dst = static_cast<typename Arith<T>::V*>(o.dst);
+    q.dot_partial = nullptr;
+    q.skip = nullptr;
+    q.C = C;
+    q.cell_begin = 0;
+    q.cell_end = o.n_cells;
+    if (o.split) q.split = *static_cast<const SplitArrays*>(o.split);
+    else memset(&q.split, 0, sizeof(q.split));
+    B.block_start[i] = start;
+    start += (int)((o.n_cells + C - 1) / C);
+  }
+  B.block_start[L.nops] = start;
+  return start;
+}
+
+template <int K, typename T, int GEO, int OP>
+cudaError_t launch_batch_one(const BatchLaunch& L) {
+  const int C = (L.cpb >= 1 && L.cpb <= cells_per_block(K)) ? L.cpb : cells_per_block(K);
+  static thread_local BatchParams<T> B;  // large (kernel parameter space): not on the stack
+  const int grid = fill_batch<T>(B, L, C);
+  if (grid <= 0) return cudaSuccess;
+  if (L.face_mode != 0) {
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(split_forward_batch<K, T, GEO, OP>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           split_smem_forward(K, cells_per_block(K), GEO));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(split_backward_batch<K, T, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 split_smem_backward(K, OP, cells_per_block(K)));
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    split_forward_batch<K, T, GEO, OP><<<grid, C * K * K, split_smem_forward(K, C, GEO), L.stream>>>(B);
+    split_backward_batch<K, T, GEO, OP><<<grid, C * K * K, split_smem_backward(K, OP, C), L.stream>>>(B);
+    return cudaGetLastError();
+  }
+  if constexpr (GEO == GEO_POS) {
+    return cudaErrorInvalidValue;  // G2 binary64 / double-float operators run the face loop only
+  } else {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel_batch<K, T, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes_per_block(K, OP, (int)sizeof(T), cells_per_block(K)));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  apply_kernel_batch<K, T, GEO, OP>
+      <<<grid, C * K * K, smem_bytes_per_block(K, OP, (int)sizeof(T), C), L.stream>>>(B);
+  return cudaGetLastError();
+  }
+}
+
+template <int K, int C, int GEO, int OP>
+cudaError_t launch_batch_f32_one(const BatchLaunch& L) {
+  static thread_local BatchParams<float> B;
+  const int grid = fill_batch<float>(B, L, C);
+  if (grid <= 0) return cudaSuccess;
+  const int smem = f32_smem_bytes(K, OP, C, GEO);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(apply_f32_batch<K, C, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int want = f32_min_blocks(K, C, OP) * (smem + 1024);
+    const int pct = want >= 228 * 1024 ? 100 : (want * 100 + 228 * 1024 - 1) / (228 * 1024);
+    e = cudaFuncSetAttribute(apply_f32_batch<K, C, GEO, OP>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  apply_f32_batch<K, C, GEO, OP><<<grid, C * K * K, smem, L.stream>>>(B);
+  return cudaGetLastError();
+}
+
+template <int K, int C>
+cudaError_t launch_batch_f32_tile(const BatchLaunch& L) {
+  if (L.op == OP_SIPG) {
+    if (L.geo == GEO_CART) return launch_batch_f32_one<K, C, GEO_CART, OP_SIPG>(L);
+    if (L.geo == GEO_FULL) return launch_batch_f32_one<K, C, GEO_FULL, OP_SIPG>(L);
+    if (L.geo == GEO_POS) return launch_batch_f32_one<K, C, GEO_POS, OP_SIPG>(L);
+    return launch_batch_f32_one<K, C, GEO_MERGED, OP_SIPG>(L);
+  }
+  if (L.geo == GEO_CART) return launch_batch_f32_one<K, C, GEO_CART, OP_ADV>(L);
+  if (L.geo == GEO_FULL) return launch_batch_f32_one<K, C, GEO_FULL, OP_ADV>(L);
+  if (L.geo == GEO_POS) return launch_batch_f32_one<K, C, GEO_POS, OP_ADV>(L);
+  return launch_batch_f32_one<K, C, GEO_MERGED, OP_ADV>(L);
+}
+
+template <int K, typename T>
+cudaError_t launch_batch_prec(const BatchLaunch& L) {
+  if (L.op == OP_SIPG) {
+    if (L.geo == GEO_CART) return launch_batch_one<K, T, GEO_CART, OP_SIPG>(L);
+    if (L.geo == GEO_FULL) return launch_batch_one<K, T, GEO_FULL, OP_SIPG>(L);
+    if (L.geo == GEO_POS) return launch_batch_one<K, T, GEO_POS, OP_SIPG>(L);
+    return launch_batch_one<K, T, GEO_MERGED, OP_SIPG>(L);
+  }
+  if (L.geo == GEO_CART) return launch_batch_one<K, T, GEO_CART, OP_ADV>(L);
+  if (L.geo == GEO_FULL) return launch_batch_one<K, T, GEO_FULL, OP_ADV>(L);
+  if (L.geo == GEO_POS) return launch_batch_one<K, T, GEO_POS, OP_ADV>(L);
+  return launch_batch_one<K, T, GEO_MERGED, OP_ADV>(L);
+}
+
+template <int K>
+cudaError_t launch_batch(const BatchLaunch& L) {
+  if (L.nops < 1 || L.nops > kBatchOps) return cudaErrorInvalidValue;
+  if (L.prec == 0) return launch_batch_prec<K, double>(L);
+  if (L.prec == 2) return launch_batch_prec<K, df64>(L);
+  if (L.cpb == F32Tiles<K>::large) return launch_batch_f32_tile<K, F32Tiles<K>::large>(L);
+  if (L.cpb == F32Tiles<K>::small) return launch_batch_f32_tile<K, F32Tiles<K>::small>(L);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace dg
 
 #define DG_DEFINE_APPLY_LAUNCHER(KK)                                              \
@@ -795,4 +1028,5 @@ cudaError_t launch_apply(const ApplyLaunch& L, int64_t n_cells) {
   cudaError_t launch_apply_k##KK(const ApplyLaunch& L, int64_t n_cells) {         \
     return launch_apply<KK>(L, n_cells);                                          \
   }                                                                               \
+  cudaError_t launch_batch_k##KK(const BatchLaunch& L) { return launch_batch<KK>(L); } \
   }

@@ -90,9 +90,10 @@ __host__ __device__ constexpr int f32_min_blocks(int k, int C, int op) {
              : 1;
 }
 
-template <int K, int C, int GEO, int OP>
-__global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
-    apply_f32_kernel(const __grid_constant__ ApplyParams<float> P) {
+// One block (blk) of the binary32 apply: the body of apply_f32_kernel (one
+// operator) and apply_f32_batch (several).
+template <int K, int C, int GEO, int OP, typename PP>
+__device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, const int blk) {
   using Sh = F32Shape<K, C>;
   constexpr int K2 = Sh::K2, K3 = Sh::K3, XS = Sh::XS, YS = Sh::YS, NP = Sh::NP, NT = Sh::NT;
   constexpr int CBL = f32_geometry_block(K);
@@ -101,7 +102,8 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
   constexpr bool TANG = SIPG && !CART;        // tangential gradients on faces
   constexpr int NBF = SIPG ? 2 : 1;           // neighbour face fields (value, normal derivative)
   constexpr int NBB = SIPG ? (CART ? 2 : 3) : 1;  // after the first in-face sweep
-  constexpr int NA = GEO == GEO_FULL ? 10 : (SIPG ? 6 : 3);
+  constexpr bool POS = GEO == GEO_POS;  // G2: positions (+ kappa) per point, J in the kernel
+  constexpr int NA = GEO == GEO_FULL ? 10 : POS ? (SIPG ? 4 : 3) : (SIPG ? 6 : 3);
   static_assert(C == 4 || C == 8 || C == 16 || C == 32 || C == 64, "cells per block");
   static_assert(CBL % C == 0, "geometry block width");
 
@@ -121,10 +123,10 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
                                  // then the pulled face test components [2][2][2][K KP][C]
   int* NBC = reinterpret_cast<int*>(FB + 6 * FSB * C);  // [6][C] neighbour cell or -1
   int* FID = NBC + 6 * C;                                    // [6][C] face id
+  float* XP = reinterpret_cast<float*>(FID + 6 * C);          // G2: [3][NP][C] Gauss-point positions
   constexpr int RS = K3;  // cell stride of the staged source
   static_assert((C + 2) * RS <= 2 * NP * C, "staged source fits in G1/G2");
 
-  const Tables<float>& tb = P.tab;
   const Geometry<float>& gm = P.geo;
   // face arrays: blocks of FBW faces, [face block][array][point][face in
   // block]; element (m, fp) of face f at face_at(d, f)[(m K2 + fp) FBW]
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
   const int a = ln % K, b = ln / K;
   const int fpt = a + f32_face_pitch(K) * b;  // face point (a, b) in the face buffers
   const int ncell = (int)gm.n_cells;
-  const int cell0 = (int)P.cell_begin + (int)blockIdx.x * C;  // this block's first cell
+  const int cell0 = (int)P.cell_begin + blk * C;  // this block's first cell
   const int cell_end = (int)P.cell_end;                         // end of this launch's cells
   const int cell_raw = cell0 + lc;
   const bool valid = cell_raw < cell_end;
@@ -258,7 +260,19 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
     const int e0 = d == 0 ? gm.P[0] : gm.n[0], e1 = d == 1 ? gm.P[1] : gm.n[1];
     FID[t * C + lc] = f0 + e0 * (f1 + e1 * f2);
   }
-  if constexpr (ASYNC_R || STAGE_YZ) f32_cp_async_wait();
+  if constexpr (POS) {
+    // G2: the block's Gauss-point positions (cell-blocked arrays 0..2) into
+    // the padded cell-minor layout of the point fields
+    const float* gb = gm.cell + ((size_t)(cell0 / CBL) * NA * K3) * CBL + (cell0 % CBL);
+    constexpr int NE = 3 * K3 * C;
+#pragma unroll 1
+    for (int e = tid; e < NE; e += NT) {
+      const int c = e % C, q = (e / C) % K3, m = e / (C * K3);
+      const int x = q % K, y = (q / K) % K, z = q / K2;
+      f32_cp_async4(XP + (m * NP + x + XS * y + YS * z) * C + c, gb + (m * K3 + q) * CBL + c);
+    }
+  }
+  if constexpr (ASYNC_R || STAGE_YZ || POS) f32_cp_async_wait();
   __syncthreads();
 
   // start the HBM fetch of this block's cell geometry (read in phase 6)
@@ -624,6 +638,39 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
   constexpr int MS = K3 * CBL;  // array stride
   float kx = 1.f;
   if (CART && SIPG && gm.kq) kx = gm.kq[i0 * K + a];
+  // G2 (Sec. 5): J at (a, b, j) by the collocation derivative D^co of the
+  // staged positions along the three lines through the point; J^{-1} by the
+  // adjugate (Ji[r*3 + s] = (J^{-1})_{rs}); returns det J
+  auto g2_jinv = [&](int j, float(&Ji)[9]) -> float {
+    float J[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float* X = XP + i * NP * C + lc;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        s0 = fmaf(tb.D[a * K + m], X[(m + XS * b + YS * j) * C], s0);
+        s1 = fmaf(tb.D[b * K + m], X[(a + XS * m + YS * j) * C], s1);
+        s2 = fmaf(tb.D[j * K + m], X[(a + XS * b + YS * m) * C], s2);
+      }
+      J[i * 3 + 0] = s0;
+      J[i * 3 + 1] = s1;
+      J[i * 3 + 2] = s2;
+    }
+    const float c00 = J[4] * J[8] - J[5] * J[7], c01 = J[5] * J[6] - J[3] * J[8], c02 = J[3] * J[7] - J[4] * J[6];
+    const float det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+    const float r = 1.f / det;
+    Ji[0] = c00 * r;
+    Ji[3] = c01 * r;
+    Ji[6] = c02 * r;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) * r;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) * r;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) * r;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) * r;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) * r;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) * r;
+    return det;
+  };
   // q-point operation at (a, b, j) and the z faces' gradient-test injection
   // (tgz: the z faces' coefficients, [component][side])
   auto qpoint = [&](int j, float g0, float g1, float g2, float uq, const float(&tgz)[3][2], float& t0, float& t1,
@@ -648,6 +695,16 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
         t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
         t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
         t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+      } else if (POS) {
+        float Ji[9];
+        const float det = g2_jinv(j, Ji);
+        const float kw = cp[3 * MS] * det * (wa * wb * tb.W[j]);
+        const float x0 = kw * (Ji[0] * g0 + Ji[3] * g1 + Ji[6] * g2);
+        const float x1 = kw * (Ji[1] * g0 + Ji[4] * g1 + Ji[7] * g2);
+        const float x2 = kw * (Ji[2] * g0 + Ji[5] * g1 + Ji[8] * g2);
+        t0 = Ji[0] * x0 + Ji[1] * x1 + Ji[2] * x2;
+        t1 = Ji[3] * x0 + Ji[4] * x1 + Ji[5] * x2;
+        t2 = Ji[6] * x0 + Ji[7] * x1 + Ji[8] * x2;
       } else {
         const float a00 = cp[0], a01 = cp[MS], a02 = cp[2 * MS], a11 = cp[3 * MS], a12 = cp[4 * MS],
                     a22 = cp[5 * MS];
@@ -677,6 +734,12 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
         b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
         b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
         b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+      } else if (POS) {
+        float Ji[9];
+        const float jw = -(g2_jinv(j, Ji) * (wa * wb * tb.W[j]));
+        b0 = jw * (Ji[0] * gm.vel[0] + Ji[1] * gm.vel[1] + Ji[2] * gm.vel[2]);
+        b1 = jw * (Ji[3] * gm.vel[0] + Ji[4] * gm.vel[1] + Ji[5] * gm.vel[2]);
+        b2 = jw * (Ji[6] * gm.vel[0] + Ji[7] * gm.vel[1] + Ji[8] * gm.vel[2]);
       } else {
         b0 = cp[0];
         b1 = cp[MS];
@@ -918,10 +981,24 @@ __global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
         for (int i = tid; i < NT; i += 32) t += red[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if (tid == 0) P.dot_partial[blockIdx.x] = t;
+        if (tid == 0) P.dot_partial[blk] = t;
       }
     }
   }
+}
+
+template <int K, int C, int GEO, int OP>
+__global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
+    apply_f32_kernel(const __grid_constant__ ApplyParams<float> P) {
+  if (P.skip != nullptr && *P.skip != 0.0) return;
+  f32_body<K, C, GEO, OP>(P.tab, P, (int)blockIdx.x);
+}
+
+template <int K, int C, int GEO, int OP>
+__global__ void __launch_bounds__(C * K * K, f32_min_blocks(K, C, OP))
+    apply_f32_batch(const __grid_constant__ BatchParams<float> B) {
+  const int i = batch_op(B, (int)blockIdx.x);
+  f32_body<K, C, GEO, OP>(B.tab, B.op[i], (int)blockIdx.x - B.block_start[i]);
 }
 
 // Compiled tile shapes (cells per block) of the binary32 kernel.
@@ -939,10 +1016,11 @@ cudaError_t launch_f32_one(const ApplyLaunch& L, int64_t n_cells) {
   P.src = static_cast<const float*>(L.src);
   P.dst = static_cast<float*>(L.dst);
   P.dot_partial = L.dot_partial;
+  P.skip = L.skip;
   P.C = C;
   P.cell_begin = L.cell_begin;
   P.cell_end = L.cell_end;
-  const int smem = f32_smem_bytes(K, OP, C);
+  const int smem = f32_smem_bytes(K, OP, C, GEO);
   static bool configured = false;
   if (!configured) {
     cudaError_t e =
@@ -968,10 +1046,12 @@ cudaError_t launch_f32_tile(const ApplyLaunch& L, int64_t n_cells) {
   if (L.op == OP_SIPG) {
     if (L.geo == GEO_CART) return launch_f32_one<K, C, GEO_CART, OP_SIPG>(L, n_cells);
     if (L.geo == GEO_FULL) return launch_f32_one<K, C, GEO_FULL, OP_SIPG>(L, n_cells);
+    if (L.geo == GEO_POS) return launch_f32_one<K, C, GEO_POS, OP_SIPG>(L, n_cells);
     return launch_f32_one<K, C, GEO_MERGED, OP_SIPG>(L, n_cells);
   }
   if (L.geo == GEO_CART) return launch_f32_one<K, C, GEO_CART, OP_ADV>(L, n_cells);
   if (L.geo == GEO_FULL) return launch_f32_one<K, C, GEO_FULL, OP_ADV>(L, n_cells);
+  if (L.geo == GEO_POS) return launch_f32_one<K, C, GEO_POS, OP_ADV>(L, n_cells);
   return launch_f32_one<K, C, GEO_MERGED, OP_ADV>(L, n_cells);
 }
 

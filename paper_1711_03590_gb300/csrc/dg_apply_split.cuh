@@ -67,9 +67,9 @@ __host__ __device__ constexpr int split_table_scalars() {
 // Step 1: sweeps, own traces, q-point operation.  T: double (binary64) or
 // df64 (double-float on the FP32 pipe; vectors, traces and gradient-test
 // fields are stored as 8-byte values either way).
-template <int K, typename T, int GEO, int OP>
-__global__ void __launch_bounds__(Shape<K>::max_threads)
-    split_cell_forward(const __grid_constant__ ApplyParams<T> P, const __grid_constant__ SplitArrays SA) {
+template <int K, typename T, int GEO, int OP, typename PP>
+__device__ __forceinline__ void split_forward_body(const Tables<T>& tb, const PP& P, const SplitArrays& SA,
+                                                   const int blk) {
   using A = Arith<T>;
   constexpr int K2 = K * K, K3 = K2 * K;
   constexpr int NTR = SplitFields<OP>::NTR;
@@ -86,16 +86,16 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
   T* sW = sE + 2 * K;                     // [K]
   T* sS = sW + K;                         // [K][K]
   T* sD = sS + K2;                        // [K][K]
+  T* XP = sD + K2;                        // [3][C][K3] Gauss-point positions (G2 only)
   T* const tr_out[3] = {reinterpret_cast<T*>(SA.tr[0]), reinterpret_cast<T*>(SA.tr[1]),
                         reinterpret_cast<T*>(SA.tr[2])};
   T* const tq_out = reinterpret_cast<T*>(SA.tq);
-  const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
   const int tid = threadIdx.x;
   const int lc = tid / K2;
   const int ln = tid - lc * K2;
   const int la = ln % K, lb = ln / K;
-  const int64_t cell0 = P.cell_begin + (int64_t)blockIdx.x * C;
+  const int64_t cell0 = P.cell_begin + (int64_t)blk * C;
   const int64_t cell = cell0 + lc;
   const bool active = cell < P.cell_end;
   const int nloc = (int)min((int64_t)C, P.cell_end - cell0);
@@ -112,6 +112,14 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
     ijk[2] = (int)(q / (unsigned)gm.n[1]);
   }
   for (int i = tid; i < nloc * K3; i += blockDim.x) U[i] = A::load(P.src + cell0 * K3 + i);
+  if constexpr (GEO == GEO_POS) {
+    for (int i = tid; i < nloc * K3; i += blockDim.x) {
+      const int64_t q = cell0 * K3 + i;
+      XP[i] = gm.cell[q];
+      XP[C * K3 + i] = gm.cell[gm.ncq + q];
+      XP[2 * C * K3 + i] = gm.cell[2 * gm.ncq + q];
+    }
+  }
   if constexpr (kCompact) {
     if (tid < 2 * K) sE[tid] = tb.E[tid / K][tid % K];
     if (tid < K) sW[tid] = tb.W[tid];
@@ -215,6 +223,18 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
         t0 = J[0] * x0 + J[1] * x1 + J[2] * x2;
         t1 = J[3] * x0 + J[4] * x1 + J[5] * x2;
         t2 = J[6] * x0 + J[7] * x1 + J[8] * x2;
+      } else if (GEO == GEO_POS) {
+        // G2: J from the positions; kappa stored per point (array 3)
+        T Ji[9];
+        const T det = g2_inverse_jacobian<K, T>(mD, XP + lc * K3, XP + (C + lc) * K3, XP + (2 * C + lc) * K3, la,
+                                                lb, z, Ji);
+        const T kw = gm.cell[3 * gm.ncq + qi] * det * (wa * wb * mW[z]);
+        const T x0 = kw * (Ji[0] * g0 + Ji[3] * g1 + Ji[6] * g2);
+        const T x1 = kw * (Ji[1] * g0 + Ji[4] * g1 + Ji[7] * g2);
+        const T x2 = kw * (Ji[2] * g0 + Ji[5] * g1 + Ji[8] * g2);
+        t0 = Ji[0] * x0 + Ji[1] * x1 + Ji[2] * x2;
+        t1 = Ji[3] * x0 + Ji[4] * x1 + Ji[5] * x2;
+        t2 = Ji[6] * x0 + Ji[7] * x1 + Ji[8] * x2;
       } else {
         const T* cp = gm.cell + qi;
         const int64_t n = gm.ncq;
@@ -241,6 +261,14 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
         b0 = jw * (J[0] * gm.vel[0] + J[1] * gm.vel[1] + J[2] * gm.vel[2]);
         b1 = jw * (J[3] * gm.vel[0] + J[4] * gm.vel[1] + J[5] * gm.vel[2]);
         b2 = jw * (J[6] * gm.vel[0] + J[7] * gm.vel[1] + J[8] * gm.vel[2]);
+      } else if (GEO == GEO_POS) {
+        T Ji[9];
+        const T det = g2_inverse_jacobian<K, T>(mD, XP + lc * K3, XP + (C + lc) * K3, XP + (2 * C + lc) * K3, la,
+                                                lb, z, Ji);
+        const T jw = -(det * (wa * wb * mW[z]));
+        b0 = jw * (Ji[0] * gm.vel[0] + Ji[1] * gm.vel[1] + Ji[2] * gm.vel[2]);
+        b1 = jw * (Ji[3] * gm.vel[0] + Ji[4] * gm.vel[1] + Ji[5] * gm.vel[2]);
+        b2 = jw * (Ji[6] * gm.vel[0] + Ji[7] * gm.vel[1] + Ji[8] * gm.vel[2]);
       } else {
         const T* cp = gm.cell + qi;
         const int64_t n = gm.ncq;
@@ -334,9 +362,9 @@ __device__ __forceinline__ void split_slot_flux(const T* W, const Geometry<T>& g
 
 // Step 2: the numerical flux of this cell's slot on its six faces from both
 // slots' traces, injection of the test coefficients, integration, dst.
-template <int K, typename T, int GEO, int OP>
-__global__ void __launch_bounds__(Shape<K>::max_threads)
-    split_cell_backward(const __grid_constant__ ApplyParams<T> P, const __grid_constant__ SplitArrays SA) {
+template <int K, typename T, int GEO, int OP, typename PP>
+__device__ __forceinline__ void split_backward_body(const Tables<T>& tb, const PP& P, const SplitArrays& SA,
+                                                    const int blk) {
   using A = Arith<T>;
   constexpr int K2 = K * K, K3 = K2 * K;
   constexpr int NTR = SplitFields<OP>::NTR, NFT = SplitFields<OP>::NFT;
@@ -357,13 +385,12 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
   const T* const tr_in[3] = {reinterpret_cast<const T*>(SA.tr[0]), reinterpret_cast<const T*>(SA.tr[1]),
                              reinterpret_cast<const T*>(SA.tr[2])};
   const T* const tq_in = reinterpret_cast<const T*>(SA.tq);
-  const Tables<T>& tb = P.tab;
   const Geometry<T>& gm = P.geo;
   const int tid = threadIdx.x;
   const int lc = tid / K2;
   const int ln = tid - lc * K2;
   const int la = ln % K, lb = ln / K;
-  const int64_t cell0 = P.cell_begin + (int64_t)blockIdx.x * C;
+  const int64_t cell0 = P.cell_begin + (int64_t)blk * C;
   const int64_t cell = cell0 + lc;
   const bool active = cell < P.cell_end;
   const int nloc = (int)min((int64_t)C, P.cell_end - cell0);
@@ -494,10 +521,36 @@ __global__ void __launch_bounds__(Shape<K>::max_threads)
       if (tid == 0) {
         double t = 0.0;
         for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
-        P.dot_partial[blockIdx.x] = t;
+        P.dot_partial[blk] = t;
       }
     }
   }
+}
+
+template <int K, typename T, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads)
+    split_cell_forward(const __grid_constant__ ApplyParams<T> P, const __grid_constant__ SplitArrays SA) {
+  if (P.skip != nullptr && *P.skip != 0.0) return;
+  split_forward_body<K, T, GEO, OP>(P.tab, P, SA, (int)blockIdx.x);
+}
+template <int K, typename T, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads)
+    split_cell_backward(const __grid_constant__ ApplyParams<T> P, const __grid_constant__ SplitArrays SA) {
+  if (P.skip != nullptr && *P.skip != 0.0) return;
+  split_backward_body<K, T, GEO, OP>(P.tab, P, SA, (int)blockIdx.x);
+}
+// The same over the blocks of several operators (one batched launch each)
+template <int K, typename T, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads)
+    split_forward_batch(const __grid_constant__ BatchParams<T> B) {
+  const int i = batch_op(B, (int)blockIdx.x);
+  split_forward_body<K, T, GEO, OP>(B.tab, B.op[i], B.op[i].split, (int)blockIdx.x - B.block_start[i]);
+}
+template <int K, typename T, int GEO, int OP>
+__global__ void __launch_bounds__(Shape<K>::max_threads)
+    split_backward_batch(const __grid_constant__ BatchParams<T> B) {
+  const int i = batch_op(B, (int)blockIdx.x);
+  split_backward_body<K, T, GEO, OP>(B.tab, B.op[i], B.op[i].split, (int)blockIdx.x - B.block_start[i]);
 }
 
 template <int K, typename T, int GEO, int OP>
@@ -509,6 +562,7 @@ cudaError_t launch_split(const ApplyLaunch& L) {
   P.src = static_cast<const double*>(L.src);
   P.dst = static_cast<double*>(L.dst);
   P.dot_partial = L.dot_partial;
+  P.skip = L.skip;
   const int C = (L.cpb >= 1 && L.cpb <= cells_per_block(K)) ? L.cpb : cells_per_block(K);
   P.C = C;
   P.cell_begin = L.cell_begin;
@@ -518,7 +572,7 @@ cudaError_t launch_split(const ApplyLaunch& L) {
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(split_cell_forward<K, T, GEO, OP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         split_smem_forward(K, cells_per_block(K)));
+                                         split_smem_forward(K, cells_per_block(K), GEO));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(split_cell_backward<K, T, GEO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                split_smem_backward(K, OP, cells_per_block(K)));
@@ -528,7 +582,7 @@ cudaError_t launch_split(const ApplyLaunch& L) {
   const int64_t grid = (L.cell_end - L.cell_begin + C - 1) / C;
   if (grid <= 0) return cudaSuccess;
   if (L.split_stage != 2)
-    split_cell_forward<K, T, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_forward(K, C), L.stream>>>(P, SA);
+    split_cell_forward<K, T, GEO, OP><<<(unsigned)grid, C * K * K, split_smem_forward(K, C, GEO), L.stream>>>(P, SA);
   if (L.split_stage != 1)
     split_cell_backward<K, T, GEO, OP>
         <<<(unsigned)grid, C * K * K, split_smem_backward(K, OP, C), L.stream>>>(P, SA);
@@ -540,10 +594,12 @@ cudaError_t launch_apply_split_t(const ApplyLaunch& L) {
   if (L.op == OP_SIPG) {
     if (L.geo == GEO_CART) return launch_split<K, T, GEO_CART, OP_SIPG>(L);
     if (L.geo == GEO_FULL) return launch_split<K, T, GEO_FULL, OP_SIPG>(L);
+    if (L.geo == GEO_POS) return launch_split<K, T, GEO_POS, OP_SIPG>(L);
     return launch_split<K, T, GEO_MERGED, OP_SIPG>(L);
   }
   if (L.geo == GEO_CART) return launch_split<K, T, GEO_CART, OP_ADV>(L);
   if (L.geo == GEO_FULL) return launch_split<K, T, GEO_FULL, OP_ADV>(L);
+  if (L.geo == GEO_POS) return launch_split<K, T, GEO_POS, OP_ADV>(L);
   return launch_split<K, T, GEO_MERGED, OP_ADV>(L);
 }
 

@@ -16,7 +16,10 @@ namespace dg {
 constexpr int kMaxK = 9;  // degree 8
 constexpr int kHalf = (kMaxK + 1) / 2;
 
-enum Geo { GEO_CART = 0, GEO_FULL = 2, GEO_MERGED = 3 };
+// Geometry variants of the kernels (Sec. 5): Cartesian compression, G3 (full
+// per-point Jacobians), G4 (merged coefficients), G2 (per-point positions;
+// the Jacobian by a collocation derivative in the kernel)
+enum Geo { GEO_CART = 0, GEO_FULL = 2, GEO_MERGED = 3, GEO_POS = 4 };
 enum Op { OP_SIPG = 0, OP_ADV = 1 };
 
 // 1D tables, passed by value as kernel parameters (constant bank).
@@ -90,6 +93,8 @@ struct ApplyLaunch {
   const void* tables;    // Tables<T>*
   const void* geometry;  // Geometry<T>*
   double* dot_partial;   // optional: per-block partial of src . dst (FP64)
+  const double* skip;    // optional device flag: every block returns at once while *skip != 0
+                         // (frozen iterations of the device-driven solvers)
   cudaStream_t stream;
   int cpb;               // cells per block (1 .. cells_per_block(k))
   int64_t cell_begin;    // the launch covers cells cell_begin .. cell_end - 1 (neighbours anywhere);
@@ -99,6 +104,25 @@ struct ApplyLaunch {
                          // backward launch only (cell ranges: the forward launch of every
                          // neighbour of the range must have run)
   const void* split;     // SplitArrays* of the face loop
+};
+
+// Host description of one operator in a batched launch (one launch covering
+// the blocks of several operators of the same degree, arithmetic, geometry
+// variant, weak form, face mode and tile shape; dg_batch.cu).
+constexpr int kBatchOps = 64;  // operators per batched launch (kernel parameter space)
+struct BatchOp {
+  const void* geometry;  // Geometry<T>*
+  const void* src;
+  void* dst;
+  const void* split;     // SplitArrays* of a face-loop operator, else null
+  int64_t n_cells;
+};
+struct BatchLaunch {
+  int k, prec, geo, op, face_mode, cpb;
+  const void* tables;    // Tables<T>* (the same for every operator of the launch)
+  int nops;              // 1 .. kBatchOps
+  const BatchOp* ops;
+  cudaStream_t stream;
 };
 
 // Largest number of cells per block of the apply kernel for k points per
@@ -124,8 +148,8 @@ __host__ __device__ constexpr int split_cells_per_block(int k, int prec) {
 
 // Shared-memory bytes of the face-loop kernels (C cells per block; 8-byte
 // scalars, plus the double-float kernels' tables).
-__host__ __device__ constexpr int split_smem_forward(int k, int C) {
-  return (4 * C * k * k * k + 3 * k + 2 * k * k) * 8;
+__host__ __device__ constexpr int split_smem_forward(int k, int C, int geo = 0) {
+  return (4 * C * k * k * k + 3 * k + 2 * k * k + (geo == GEO_POS ? 3 * C * k * k * k : 0)) * 8;
 }
 __host__ __device__ constexpr int split_smem_backward(int k, int op, int C) {
   return (4 * C * k * k * k + C * 6 * (op == OP_SIPG ? 4 : 1) * k * k + 3 * k + 2 * k * k) * 8;
@@ -177,10 +201,10 @@ __host__ __device__ constexpr int f32_face_pad(int k, int C, int nf) {
 }
 
 // Shared-memory bytes of the binary32 kernel for k points and C cells: four
-// padded point fields, the neighbour face data (6 faces x 2 fields), the
+// padded point fields (seven with the G2 positions), the neighbour face data (6 faces x 2 fields), the
 // in-face sweep buffer (6 faces x 3 fields) and two face tables (6 ints each).
-__host__ __device__ constexpr int f32_smem_bytes(int k, int op, int C) {
-  return 4 * (4 * (k * (k % 2 == 0 ? k + 1 : k) * k) * C +
+__host__ __device__ constexpr int f32_smem_bytes(int k, int op, int C, int geo = 0) {
+  return 4 * ((geo == GEO_POS ? 7 : 4) * (k * (k % 2 == 0 ? k + 1 : k) * k) * C +
               6 * ((op == OP_SIPG ? 2 : 1) * k * f32_face_pitch(k) + f32_face_pad(k, C, op == OP_SIPG ? 2 : 1)) * C +
               6 * ((op == OP_SIPG ? 3 : 1) * k * f32_face_pitch(k) + f32_face_pad(k, C, op == OP_SIPG ? 3 : 1)) * C +
               12 * C);
@@ -207,5 +231,13 @@ cudaError_t launch_apply_k6(const ApplyLaunch&, int64_t n_cells);
 cudaError_t launch_apply_k7(const ApplyLaunch&, int64_t n_cells);
 cudaError_t launch_apply_k8(const ApplyLaunch&, int64_t n_cells);
 cudaError_t launch_apply_k9(const ApplyLaunch&, int64_t n_cells);
+cudaError_t launch_batch_k2(const BatchLaunch&);
+cudaError_t launch_batch_k3(const BatchLaunch&);
+cudaError_t launch_batch_k4(const BatchLaunch&);
+cudaError_t launch_batch_k5(const BatchLaunch&);
+cudaError_t launch_batch_k6(const BatchLaunch&);
+cudaError_t launch_batch_k7(const BatchLaunch&);
+cudaError_t launch_batch_k8(const BatchLaunch&);
+cudaError_t launch_batch_k9(const BatchLaunch&);
 
 }  // namespace dg

@@ -1,11 +1,17 @@
 // Solve server: continuous batching of Poisson solve requests on one GPU.
 //
 // Requests are queued in arrival order.  A fixed number of worker threads
-// ("slots"), each with its own non-blocking CUDA stream, take the oldest
+// ("slots"), each with its own non-blocking CUDA stream, take a queued
 // request as soon as a slot is free AND the request's estimated device
 // memory fits into the remaining budget; so requests that arrive while
 // others run are admitted as slots and memory free up, and the GPU work of
-// all admitted requests overlaps on the device.  Each request is solved
+// all admitted requests overlaps on the device.  Which queued request a
+// free slot takes is the admission policy (dg_server_set_policy): the
+// oldest (FIFO, the default: a large request at the head makes the others
+// wait), or the smallest estimated work (dofs x (p+1)) among those that fit
+// the budget, except that requests queued longer than a given age go first,
+// oldest first (shortest job first with aging: small requests are not stuck
+// behind large ones, and no request waits forever).  Each request is solved
 // end to end with device-resident state: FP64 and FP32 operators on its
 // mesh, the manufactured right-hand side, the mixed-precision solve
 // (dg_cg_solve_mixed), optional copy of the solution to the host.  A solve
@@ -38,6 +44,8 @@ struct dg_server {
   int device = 0;
   int64_t budget = 0;
   int64_t in_use = 0;
+  int policy = 0;          // 0 FIFO, 1 shortest job first with aging
+  double max_age_s = 0.0;  // policy 1: requests queued longer than this go first
   bool stopping = false;
   int64_t next_ticket = 1;
   std::deque<int64_t> queue;
@@ -115,21 +123,62 @@ void solve_one(dg_server* srv, Entry& e, cudaStream_t stream) {
   (void)srv;
 }
 
+// estimated work of a request: dofs x (p + 1) (the cost of one CG iteration)
+double request_work(const dg_request& r) { return (double)request_dofs(&r) * (r.degree + 1); }
+
+// Position in the queue of the request a free slot takes now, or -1 if none
+// may start (FIFO: the head when it fits; shortest job first with aging:
+// the oldest request queued longer than max_age_s if it fits, else the
+// smallest estimated work among the requests that fit).  Called with the
+// lock held.
+long pick(dg_server* srv) {
+  if (srv->queue.empty()) return -1;
+  if (srv->policy == 0) {
+    const Entry& head = srv->entries[srv->queue.front()];
+    return srv->in_use + head.bytes <= srv->budget ? 0 : -1;
+  }
+  const double now = now_s(srv);
+  long best = -1;
+  double best_work = 0.0;
+  for (size_t i = 0; i < srv->queue.size(); ++i) {
+    const Entry& e = srv->entries[srv->queue[i]];
+    const bool fits = srv->in_use + e.bytes <= srv->budget;
+    if (now - e.res.t_submit > srv->max_age_s) {
+      // aged: it goes first, oldest first (and blocks younger ones while it does not fit)
+      return fits ? (long)i : -1;
+    }
+    if (!fits) continue;
+    const double w = request_work(e.req);
+    if (best < 0 || w < best_work) {
+      best = (long)i;
+      best_work = w;
+    }
+  }
+  return best;
+}
+
 void worker_main(dg_server* srv) {
   cudaSetDevice(srv->device);
   cudaStream_t stream = nullptr;
   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
   std::unique_lock<std::mutex> lock(srv->mu);
   while (true) {
-    // the oldest request runs as soon as it fits into the remaining budget
-    srv->cv_work.wait(lock, [&] {
-      if (srv->queue.empty()) return srv->stopping;
-      const Entry& head = srv->entries[srv->queue.front()];
-      return srv->in_use + head.bytes <= srv->budget;
-    });
-    if (srv->queue.empty()) break;
-    const int64_t t = srv->queue.front();
-    srv->queue.pop_front();
+    // a queued request runs as soon as the policy picks one that fits into
+    // the remaining budget (aging is rechecked at least every 10 ms)
+    long pos = -1;
+    while (true) {
+      if (srv->queue.empty()) {
+        if (srv->stopping) break;
+        srv->cv_work.wait(lock);
+        continue;
+      }
+      pos = pick(srv);
+      if (pos >= 0) break;
+      srv->cv_work.wait_for(lock, std::chrono::milliseconds(10));
+    }
+    if (pos < 0) break;
+    const int64_t t = srv->queue[pos];
+    srv->queue.erase(srv->queue.begin() + pos);
     Entry& e = srv->entries[t];
     e.state = 1;
     srv->in_use += e.bytes;
@@ -226,6 +275,17 @@ dg_status dg_server_destroy(dg_server* s) {
   }
   for (auto& w : s->workers) w.join();
   delete s;
+  return DG_OK;
+}
+
+dg_status dg_server_set_policy(dg_server* s, int policy, double max_age_s) {
+  if (!s) return server_fail(DG_ERR_ARG, "server is NULL");
+  if (policy != 0 && policy != 1) return server_fail(DG_ERR_ARG, "policy must be 0 (FIFO) or 1 (shortest job first)");
+  if (!(max_age_s >= 0.0)) return server_fail(DG_ERR_ARG, "max_age_s must be >= 0");
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->policy = policy;
+  s->max_age_s = max_age_s;
+  s->cv_work.notify_all();
   return DG_OK;
 }
 

@@ -279,3 +279,29 @@ def test_emulated_fp64_cg_matches_fp64_cg():
     xe, ite, rre, st = oe.cg(rhs, rtol=1e-11, max_it=20000)
     assert st == dgp.DG_OK
     assert np.linalg.norm(b - A @ xe.cpu().numpy()) <= 3e-11 * np.linalg.norm(b)
+
+
+def _componentwise(got, ref, A, u):
+    """max_i |y_gpu - y_ref|_i / (|A| |u|)_i: the error of each entry against
+    the magnitude of the terms summed into it (cancellation-aware)."""
+    scale = abs(A) @ np.abs(u)
+    return float(np.max(np.abs(got - ref) / np.maximum(scale, 1e-300)))
+
+
+@pytest.mark.parametrize("p", [1, 3, 5, 8])
+@pytest.mark.parametrize("case", [1, 3, 6])
+@pytest.mark.parametrize("op", ["sipg", "advection"])
+def test_componentwise_error_against_abs_a_abs_u(p, case, op):
+    """The componentwise diagnostic: every entry of the GPU apply within the
+    stated tolerance of (|A| |u|)_i, A the oracle's assembled matrix."""
+    mesh, geom = SMALL[case]
+    if oracle.n_cells(mesh) * (p + 1) ** 6 > 3e7:
+        mesh = dict(mesh, n=tuple(min(v, 2) for v in mesh["n"]))
+    form = dict(op=op, coeff=1 if op == "sipg" else 0, velocity=dg_inputs.VELOCITY)
+    A = oracle.assemble(mesh, p, form)
+    u = dg_inputs.src_vector(A.shape[0], seed=300 + p)
+    ref = A @ u
+    for prec in ("fp64", "fp32", "fp64emu", "fp64-loop", "fp64emu-loop"):
+        got = _gpu_apply(mesh, p, geom, form, prec, u)
+        cw = _componentwise(got, ref, A, u)
+        assert cw < TOL[prec], (prec, cw)
