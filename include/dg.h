@@ -250,23 +250,48 @@ dg_status dg_l2_error(dg_handle *h, const double *x, double *err);
 dg_status dg_cg_solve(dg_handle *h, const double *rhs, double *x, double rtol, int max_it, int *iters,
                       double *final_rel_res);
 
-/* Mixed-precision solve of A x = rhs (SIPG) by FP64 defect correction around
- * an FP32 conjugate-gradient solver.  h64 and h32 describe the same operator
- * (mesh, degree, geometry, coefficient, penalty) in DG_FP64 and DG_FP32.
- * Outer step: r = rhs - A x with the FP64 apply and FP64 vectors; stop when
- * |r| <= rtol |rhs|; else solve A d = r / |r| with CG on the FP32 handle
- * (FP32 applies and vectors, every inner product accumulated in FP64) from
- * d = 0 until its residual drops by inner_rtol (or max_inner iterations), and
- * update x += |r| d in FP64.  rhs, x: device pointers to n_dofs doubles; x is
- * the initial guess on entry.  Work vectors are allocated on first use.  Runs
- * on h64's stream.  Returns DG_ERR_NOT_CONVERGED after max_outer corrections,
- * DG_ERR_BREAKDOWN on a non-finite residual or an inner CG breakdown.
- * outer_iters, inner_iters (total FP32 iterations), final_rel_res may be
- * NULL.  Synchronous.  (Beyond the paper, whose solvers are only
+/* Mixed-precision solve of A x = rhs (SIPG): conjugate gradients in a
+ * cheaper arithmetic with residual replacement ("reliable updates") by the
+ * FP64 residual.  h64 and h32 describe the same operator (mesh, degree,
+ * geometry, coefficient, penalty); h64 is DG_FP64 (or DG_FP64_EMU), h32 the
+ * inner handle: DG_FP32 (binary32 vectors and applies) or DG_FP64_EMU
+ * (binary64 vectors, double-float applies).  The inner CG works on the
+ * system scaled by 1 / |r| (every inner product accumulated in FP64); once
+ * its recursive residual has dropped by inner_rtol against the largest since
+ * the last replacement (or reached the scaled target, or after max_inner
+ * iterations), its solution is added to x in FP64, r = rhs - A x is
+ * recomputed with h64, and the recursion continues from the new r with
+ * beta = |r|^2 / |r_old|^2 and p = r + beta p, so the search directions
+ * built so far are kept (Sleijpen & van der Vorst 1996; Clark et al. 2010).
+ * Stops when |r| <= rtol |rhs| with the FP64 residual.  rhs, x: device
+ * pointers to n_dofs doubles; x is the initial guess on entry.  Work vectors
+ * are allocated on first use.  Ordered on h64's stream.  Returns
+ * DG_ERR_NOT_CONVERGED after max_outer replacements or when four
+ * replacements in a row do not halve the best residual (the attainable
+ * floor of an emulated-FP64 h64, about 2e-10 relative at p = 5);
+ * DG_ERR_BREAKDOWN on a non-finite residual or an inner breakdown.
+ * outer_iters (replacements), inner_iters (inner iterations), final_rel_res
+ * may be NULL.  Synchronous.  (Beyond the paper, whose solvers are only
  * referred to in Sec. 1 and Sec. 6.) */
 dg_status dg_cg_solve_mixed(dg_handle *h64, dg_handle *h32, const double *rhs, double *x, double rtol,
                             int max_outer, double inner_rtol, int max_inner, int *outer_iters, int *inner_iters,
                             double *final_rel_res);
+
+/* The same with the inner arithmetic chosen by measurement: double-float
+ * iterations (hemu, DG_FP64_EMU) in chunks of 16, at most 48, measure the
+ * convergence rate; as soon as at that rate the remaining iterations are few
+ * (<= 200) the double-float recursion continues (a binary32 recursion would
+ * add rounding noise across the whole spectrum, which CG must then remove:
+ * on smooth, fast-converging problems that costs far more iterations than it
+ * saves per iteration); after 48 without that, the binary32 recursion (h32,
+ * DG_FP32) takes over from the current x.  h64,
+ * hemu and h32 describe the same operator.  inner_prec (may be NULL)
+ * receives the inner arithmetic used after the probe (DG_FP64_EMU or
+ * DG_FP32); the counts include the probe.  Other arguments and results as
+ * dg_cg_solve_mixed.  Synchronous. */
+dg_status dg_cg_solve_mixed_auto(dg_handle *h64, dg_handle *hemu, dg_handle *h32, const double *rhs, double *x,
+                                 double rtol, int max_outer, double inner_rtol, int max_inner, int *outer_iters,
+                                 int *inner_iters, double *final_rel_res, int *inner_prec);
 
 /* Batched evaluation (beyond the paper, which evaluates one operator
  * at a time).  A batch applies count set-up operators -- any mix of meshes,

@@ -53,7 +53,7 @@ EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg
             "dg_set_cells_per_block", "dg_autotune", "dg_batch_create", "dg_batch_launch", "dg_batch_destroy",
             "dg_batch_last_error", "dg_request_device_bytes", "dg_server_create", "dg_server_submit",
             "dg_server_wait", "dg_server_destroy", "dg_server_last_error", "dg_l2_error", "dg_set_face_mode",
-            "dg_peak_probe", "dg_batch_info", "dg_server_set_policy"]
+            "dg_peak_probe", "dg_batch_info", "dg_server_set_policy", "dg_cg_solve_mixed_auto"]
 
 
 class DGLibraryMissing(RuntimeError):
@@ -145,6 +145,9 @@ def load_library(path=None):
                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_double)]
     L.dg_peak_probe.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.dg_cg_solve_mixed_auto.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     L.dg_destroy.argtypes = [_vp]
     L.dg_last_error.argtypes = [_vp]
     L.dg_last_error.restype = ctypes.c_char_p
@@ -251,6 +254,20 @@ def dg_cg_solve_mixed(h64, h32, rhs_ptr, x_ptr, rtol, max_outer=50, inner_rtol=1
     if raise_on_error:
         _check(st, h64)
     return st, oi.value, ii.value, rr.value
+
+
+def dg_cg_solve_mixed_auto(h64, hemu, h32, rhs_ptr, x_ptr, rtol, max_outer=50, inner_rtol=1e-2, max_inner=20000,
+                           raise_on_error=True):
+    """Returns (status, replacements, inner iterations, final relative
+    residual, inner precision used: "fp64emu" or "fp32")."""
+    oi, ii, kind = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(-1)
+    rr = ctypes.c_double(0.0)
+    st = load_library().dg_cg_solve_mixed_auto(_vp(h64), _vp(hemu), _vp(h32), _vp(rhs_ptr), _vp(x_ptr), float(rtol),
+                                               int(max_outer), float(inner_rtol), int(max_inner), ctypes.byref(oi),
+                                               ctypes.byref(ii), ctypes.byref(rr), ctypes.byref(kind))
+    if raise_on_error:
+        _check(st, h64)
+    return st, oi.value, ii.value, rr.value, {DG_FP32: "fp32", DG_FP64_EMU: "fp64emu"}.get(kind.value)
 
 
 def dg_set_cells_per_block(handle, cells_per_block):

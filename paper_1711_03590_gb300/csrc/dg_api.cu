@@ -850,12 +850,8 @@ __global__ void mp_residual(int64_t n, const double* b, const double* ap, double
   block_store_sum(rr, part + blockIdx.x);
 }
 
-__global__ void mp_to_float(int64_t n, const double* r, double scale, float* r32) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    r32[i] = (float)(r[i] * scale);
-}
-
-__global__ void mp_correct(int64_t n, double scale, const float* d, double* x) {
+template <typename T>
+__global__ void mp_correct(int64_t n, double scale, const T* d, double* x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = fma(scale, (double)d[i], x[i]);
 }
@@ -901,25 +897,27 @@ __global__ void ru_scalars_beta(const double* part, int64_t nparts, double* scal
 }
 
 // p = r + beta p, except in iterations frozen after a replacement request
-__global__ void ru_direction(int64_t n, const double* scal, const float* r, float* p) {
+template <typename T>
+__global__ void ru_direction(int64_t n, const double* scal, const T* r, T* p) {
   if (scal[S_KEEP] != 0.0) return;
-  const float b = (float)scal[S_BETA];
+  const T b = (T)scal[S_BETA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fmaf(b, p[i], r[i]);
+    p[i] = fma(b, p[i], r[i]);
 }
 
 // Restart of the recursion from the FP64 residual: r32 = sigma r64 and
 // p32 = r32 + bscaled p32 (bscaled = beta sigma_new / sigma_old; 0 on the
 // first start), xl32 = 0; partials of r32.r32 (FP64).
-__global__ void ru_restart(int64_t n, const double* r64, double sigma, double bscaled, float* r32, float* p32,
-                           float* xl32, double* part) {
+template <typename T>
+__global__ void ru_restart(int64_t n, const double* r64, double sigma, double bscaled, T* r32, T* p32, T* xl32,
+                           double* part) {
   double rr = 0.0;
-  const float fb = (float)bscaled;
+  const T fb = (T)bscaled;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float ri = (float)(r64[i] * sigma);
+    const T ri = (T)(r64[i] * sigma);
     r32[i] = ri;
-    p32[i] = bscaled != 0.0 ? fmaf(fb, p32[i], ri) : ri;
-    xl32[i] = 0.f;
+    p32[i] = bscaled != 0.0 ? fma(fb, p32[i], ri) : ri;
+    xl32[i] = T(0);
     rr += (double)ri * (double)ri;
   }
   block_store_sum(rr, part + blockIdx.x);
@@ -1731,49 +1729,62 @@ dg_status dg_cg_solve(dg_handle* h, const double* rhs, double* x, double rtol, i
   return st;
 }
 
-dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, double* x, double rtol, int max_outer,
-                            double inner_rtol, int max_inner, int* outer_iters, int* inner_iters,
-                            double* final_rel_res) {
-  if (!h64 || !h32) return DG_ERR_ARG;
-  if (h64->op != DG_OP_SIPG || h32->op != DG_OP_SIPG)
-    return fail(h64, DG_ERR_UNSUPPORTED, "mixed-precision CG needs the symmetric SIPG operator");
-  if (h64->prec == DG_FP32 || h32->prec != DG_FP32)
-    return fail(h64, DG_ERR_ARG, "mixed-precision CG needs an FP64 handle and an FP32 handle");
-  if (memcmp(&h64->mesh, &h32->mesh, sizeof(dg_mesh)) != 0 || h64->degree != h32->degree ||
-      h64->geom != h32->geom || h64->opts.coeff != h32->opts.coeff ||
-      h64->opts.penalty_scale != h32->opts.penalty_scale)
-    return fail(h64, DG_ERR_ARG, "the FP64 and FP32 handles describe different operators");
-  if (!rhs || !x) return fail(h64, DG_ERR_ARG, "rhs or x is NULL");
-  if (!(rtol > 0.0) || !(inner_rtol > 0.0) || inner_rtol >= 1.0 || max_outer < 0 || max_inner < 1)
-    return fail(h64, DG_ERR_ARG, "need rtol > 0, 0 < inner_rtol < 1, max_outer >= 0, max_inner >= 1");
+}  // extern "C"
+
+namespace {
+
+// Result of one run of the mixed-precision iteration.
+struct MixedOut {
+  int outer = 0;        // residual replacements (FP64 residuals after the first)
+  int inner = 0;        // iterations of the low-precision recursion
+  double rel = 0.0;     // |b - A x| / |b| (FP64) at return
+  double rel0 = 0.0;    // the same at entry
+  bool converged = false;
+  bool slow = false;    // probe: the recursion was judged too slow (see mixed_run)
+};
+
+// Conjugate gradients in the inner handle's arithmetic T (binary32 vectors
+// for a DG_FP32 handle, binary64 vectors with double-float applies for a
+// DG_FP64_EMU handle) with residual replacement by the FP64 residual of h64
+// (the kernels above): every replacement adds the inner solution to x in
+// FP64, recomputes b - A x with the FP64 operator and continues the CG
+// recursion from it.  probe > 0: at most 16 inner iterations per phase, and
+// at every replacement the iterations still needed at the rate observed
+// since entry are estimated; once they are at most `few` the run goes on
+// normally, but after `probe` inner iterations without that it returns with
+// mo.slow set (x holds the solution so far).  x holds the initial guess.
+template <typename T>
+dg_status mixed_run(dg_handle* h64, dg_handle* hl, const double* rhs, double* x, double rtol, int max_outer,
+                    double delta, int max_inner, int probe, double few, MixedOut& mo) {
   dg_status st = ensure_cg_work(h64, false);
-  if (st == DG_OK) st = ensure_cg_work(h32, true);
+  if (st == DG_OK) st = ensure_cg_work(hl, true);
   if (st != DG_OK) return st;
-  // the whole solve runs on the FP32 handle's solver stream (capturable),
+  // the whole solve runs on the inner handle's solver stream (capturable),
   // ordered after the caller's stream and before its later work
   cudaStream_t user = h64->stream;
-  if (!h32->cg_stream) DG_CUDA(h64, cudaStreamCreateWithFlags(&h32->cg_stream, cudaStreamNonBlocking));
-  if (!h32->cg_event) DG_CUDA(h64, cudaEventCreateWithFlags(&h32->cg_event, cudaEventDisableTiming));
-  DG_CUDA(h64, cudaEventRecord(h32->cg_event, user));
-  DG_CUDA(h64, cudaStreamWaitEvent(h32->cg_stream, h32->cg_event, 0));
-  cudaStream_t s = h32->cg_stream;
-  cudaStream_t saved32 = h32->stream;
+  if (!hl->cg_stream) DG_CUDA(h64, cudaStreamCreateWithFlags(&hl->cg_stream, cudaStreamNonBlocking));
+  if (!hl->cg_event) DG_CUDA(h64, cudaEventCreateWithFlags(&hl->cg_event, cudaEventDisableTiming));
+  DG_CUDA(h64, cudaEventRecord(hl->cg_event, user));
+  DG_CUDA(h64, cudaStreamWaitEvent(hl->cg_stream, hl->cg_event, 0));
+  cudaStream_t s = hl->cg_stream;
+  cudaStream_t savedl = hl->stream;
   h64->stream = s;
-  h32->stream = s;
+  hl->stream = s;
   const int64_t n = h64->n_dofs;
   const int vb = (int)std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads);
-  const int64_t nblk32 = apply_blocks(h32);
-  float* r32 = reinterpret_cast<float*>(h32->r);
-  float* p32 = reinterpret_cast<float*>(h32->p);
-  float* ap32 = reinterpret_cast<float*>(h32->ap);
-  float* xl32 = reinterpret_cast<float*>(h32->xw);
-  double* part32 = h32->partial;
-  double* part_apply32 = h32->partial + 2 * kRedBlocks;
-  const double delta2 = inner_rtol * inner_rtol;
+  const int64_t nblkl = apply_blocks(hl);
+  T* r32 = reinterpret_cast<T*>(hl->r);
+  T* p32 = reinterpret_cast<T*>(hl->p);
+  T* ap32 = reinterpret_cast<T*>(hl->ap);
+  T* xl32 = reinterpret_cast<T*>(hl->xw);
+  double* part32 = hl->partial;
+  double* part_apply32 = hl->partial + 2 * kRedBlocks;
+  const double delta2 = delta * delta;
   cudaGraphExec_t exec = nullptr;
   int outer = 0, inner_total = 0;
   double rel = 0.0, bnorm = 1.0, sigma = 1.0;
-
+  int phase_max = probe > 0 ? std::min(16, max_inner) : max_inner;
+  bool probing = probe > 0;
   // FP64 residual r64 = b - A x into h64->r and its r.r into h64->scal[S_RR]
   auto fp64_residual = [&](double* rr_out) -> dg_status {
     dg_status s2 = launch_apply(h64, x, h64->ap, nullptr);
@@ -1788,7 +1799,7 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
     *rr_out = h64->scal_host[S_RR];
     return DG_OK;
   };
-  // restart the binary32 recursion from the FP64 residual (norm^2 rr64);
+  // restart the inner recursion from the FP64 residual (norm^2 rr64);
   // rr_old: |r_old|^2 of the replacing iteration in the old scaling
   auto restart = [&](double rr64, bool first, double rr_old) -> dg_status {
     const double sig = 1.0 / std::sqrt(rr64);
@@ -1797,28 +1808,28 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
     const double bscaled = first ? 0.0 : (rr64 * sigma * sigma / rr_old) * (sig / sigma);
     if (!first && !(std::isfinite(bscaled) && bscaled > 0.0))
       return fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG: invalid beta at a residual replacement");
-    ru_restart<<<vb, kRedThreads, 0, s>>>(n, h64->r, sig, bscaled, r32, p32, xl32, part32);
+    ru_restart<T><<<vb, kRedThreads, 0, s>>>(n, h64->r, sig, bscaled, r32, p32, xl32, part32);
     sigma = sig;
     const double tol = rtol * bnorm * sigma;
-    ru_scalars_reset<<<1, kRedThreads, 0, s>>>(part32, vb, h32->scal, tol * tol, delta2, (double)max_inner);
+    ru_scalars_reset<<<1, kRedThreads, 0, s>>>(part32, vb, hl->scal, tol * tol, delta2, (double)phase_max);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DG_OK : cuda_fail(h64, e, "mixed-precision restart");
   };
-  // a block of binary32 iterations; the applies skip themselves once the
+  // a block of inner iterations; the applies skip themselves once the
   // iteration is frozen (replacement requested or breakdown)
   const int kIterBlock = 8;
   auto enqueue_block = [&]() -> dg_status {
     for (int j = 0; j < kIterBlock; ++j) {
-      dg_status s2 = launch_apply(h32, p32, ap32, part_apply32);
+      dg_status s2 = launch_apply(hl, p32, ap32, part_apply32);
       if (s2 != DG_OK) return s2;
-      cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply32, nblk32, h32->scal);
-      cg_update<float><<<vb, kRedThreads, 0, s>>>(n, h32->scal, xl32, r32, p32, ap32, part32);
-      ru_scalars_beta<<<1, kRedThreads, 0, s>>>(part32, vb, h32->scal);
-      ru_direction<<<vb, kRedThreads, 0, s>>>(n, h32->scal, r32, p32);
+      cg_scalars_alpha<<<1, kRedThreads, 0, s>>>(part_apply32, nblkl, hl->scal);
+      cg_update<T><<<vb, kRedThreads, 0, s>>>(n, hl->scal, xl32, r32, p32, ap32, part32);
+      ru_scalars_beta<<<1, kRedThreads, 0, s>>>(part32, vb, hl->scal);
+      ru_direction<T><<<vb, kRedThreads, 0, s>>>(n, hl->scal, r32, p32);
     }
     return DG_OK;
   };
-  h32->skip = h32->scal + S_STOP;
+  hl->skip = hl->scal + S_STOP;
   do {
     // |b| and the initial residual
     cg_init<double><<<vb, kRedThreads, 0, s>>>(n, rhs, nullptr, h64->r, h64->p, h64->partial);
@@ -1827,6 +1838,7 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
     if ((st = fp64_residual(&rr64)) != DG_OK) break;
     bnorm = std::sqrt(h64->scal_host[S_BB] > 0 ? h64->scal_host[S_BB] : 1.0);
     rel = std::sqrt(rr64) / bnorm;
+    mo.rel0 = rel;
     if (!std::isfinite(rel)) {
       st = fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG: non-finite residual");
       break;
@@ -1862,22 +1874,22 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
       } else if ((st = enqueue_block()) != DG_OK) {
         break;
       }
-      cudaError_t e = cudaMemcpyAsync(h32->scal_host, h32->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaMemcpyAsync(hl->scal_host, hl->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
         st = cuda_fail(h64, e, "mixed-precision scalars");
         break;
       }
-      const int it = (int)h32->scal_host[S_ITER];
+      const int it = (int)hl->scal_host[S_ITER];
       inner_total += it - last_it;
       last_it = it;
-      if (h32->scal_host[S_FLAG] != 0.0) {
+      if (hl->scal_host[S_FLAG] != 0.0) {
         st = fail(h64, DG_ERR_BREAKDOWN, "mixed-precision CG breakdown: p.Ap <= 0 or non-finite scalar");
         break;
       }
-      if (h32->scal_host[S_RU] == 0.0) continue;
+      if (hl->scal_host[S_RU] == 0.0) continue;
       // residual replacement: x += xl / sigma, FP64 residual, restart
-      mp_correct<<<vb, kRedThreads, 0, s>>>(n, 1.0 / sigma, xl32, x);
+      mp_correct<T><<<vb, kRedThreads, 0, s>>>(n, 1.0 / sigma, xl32, x);
       if ((st = fp64_residual(&rr64)) != DG_OK) break;
       ++outer;
       rel = std::sqrt(rr64) / bnorm;
@@ -1886,6 +1898,18 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
         break;
       }
       if (rel <= rtol || rr64 <= 0.0) break;
+      if (probing) {
+        double need = 1e30;
+        if (rel > 0.0 && mo.rel0 > rel && inner_total > 0)
+          need = inner_total * std::log(rel / rtol) / std::log(mo.rel0 / rel);
+        if (need <= few) {
+          probing = false;
+          phase_max = max_inner;
+        } else if (inner_total >= probe) {
+          mo.slow = true;
+          break;
+        }
+      }
       if (outer >= max_outer) {
         st = fail(h64, DG_ERR_NOT_CONVERGED, "mixed-precision CG reached max_outer residual replacements");
         break;
@@ -1900,19 +1924,90 @@ dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, d
         st = fail(h64, DG_ERR_NOT_CONVERGED, "mixed-precision CG stagnated: the outer residual no longer decreases");
         break;
       }
-      if ((st = restart(rr64, false, h32->scal_host[S_RR])) != DG_OK) break;
+      if ((st = restart(rr64, false, hl->scal_host[S_RR])) != DG_OK) break;
       last_it = 0;
     }
   } while (false);
-  h32->skip = nullptr;
+  hl->skip = nullptr;
   if (exec) cudaGraphExecDestroy(exec);
-  cudaEventRecord(h32->cg_event, s);
-  cudaStreamWaitEvent(user, h32->cg_event, 0);
+  cudaEventRecord(hl->cg_event, s);
+  cudaStreamWaitEvent(user, hl->cg_event, 0);
   h64->stream = user;
-  h32->stream = saved32;
-  if (outer_iters) *outer_iters = outer;
-  if (inner_iters) *inner_iters = inner_total;
-  if (final_rel_res) *final_rel_res = rel;
+  hl->stream = savedl;
+  mo.outer += outer;
+  mo.inner += inner_total;
+  mo.rel = rel;
+  mo.converged = st == DG_OK && rel <= rtol;
+  return st;
+}
+
+dg_status check_mixed_pair(dg_handle* h64, dg_handle* hl) {
+  if (h64->op != DG_OP_SIPG || hl->op != DG_OP_SIPG)
+    return fail(h64, DG_ERR_UNSUPPORTED, "mixed-precision CG needs the symmetric SIPG operator");
+  if (memcmp(&h64->mesh, &hl->mesh, sizeof(dg_mesh)) != 0 || h64->degree != hl->degree ||
+      h64->geom != hl->geom || h64->opts.coeff != hl->opts.coeff ||
+      h64->opts.penalty_scale != hl->opts.penalty_scale)
+    return fail(h64, DG_ERR_ARG, "the handles of the mixed-precision solve describe different operators");
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_cg_solve_mixed(dg_handle* h64, dg_handle* h32, const double* rhs, double* x, double rtol, int max_outer,
+                            double inner_rtol, int max_inner, int* outer_iters, int* inner_iters,
+                            double* final_rel_res) {
+  if (!h64 || !h32) return DG_ERR_ARG;
+  if (h64->prec == DG_FP32 || (h32->prec != DG_FP32 && h32->prec != DG_FP64_EMU))
+    return fail(h64, DG_ERR_ARG, "mixed-precision CG needs an FP64 (or emulated FP64) handle and an FP32 or "
+                                 "emulated-FP64 inner handle");
+  dg_status st = check_mixed_pair(h64, h32);
+  if (st != DG_OK) return st;
+  if (!rhs || !x) return fail(h64, DG_ERR_ARG, "rhs or x is NULL");
+  if (!(rtol > 0.0) || !(inner_rtol > 0.0) || inner_rtol >= 1.0 || max_outer < 0 || max_inner < 1)
+    return fail(h64, DG_ERR_ARG, "need rtol > 0, 0 < inner_rtol < 1, max_outer >= 0, max_inner >= 1");
+  MixedOut mo;
+  st = h32->prec == DG_FP32 ? mixed_run<float>(h64, h32, rhs, x, rtol, max_outer, inner_rtol, max_inner, 0, 0.0, mo)
+                            : mixed_run<double>(h64, h32, rhs, x, rtol, max_outer, inner_rtol, max_inner, 0, 0.0, mo);
+  if (outer_iters) *outer_iters = mo.outer;
+  if (inner_iters) *inner_iters = mo.inner;
+  if (final_rel_res) *final_rel_res = mo.rel;
+  return st;
+}
+
+dg_status dg_cg_solve_mixed_auto(dg_handle* h64, dg_handle* hemu, dg_handle* h32, const double* rhs, double* x,
+                                 double rtol, int max_outer, double inner_rtol, int max_inner, int* outer_iters,
+                                 int* inner_iters, double* final_rel_res, int* inner_prec) {
+  if (!h64 || !hemu || !h32) return DG_ERR_ARG;
+  if (h64->prec == DG_FP32 || hemu->prec != DG_FP64_EMU || h32->prec != DG_FP32)
+    return fail(h64, DG_ERR_ARG, "need an FP64 handle, an emulated-FP64 handle and an FP32 handle");
+  dg_status st = check_mixed_pair(h64, hemu);
+  if (st == DG_OK) st = check_mixed_pair(h64, h32);
+  if (st != DG_OK) return st;
+  if (!rhs || !x) return fail(h64, DG_ERR_ARG, "rhs or x is NULL");
+  if (!(rtol > 0.0) || !(inner_rtol > 0.0) || inner_rtol >= 1.0 || max_outer < 1 || max_inner < 1)
+    return fail(h64, DG_ERR_ARG, "need rtol > 0, 0 < inner_rtol < 1, max_outer >= 1, max_inner >= 1");
+  // the double-float recursion first, as a probe: it goes on if the
+  // iterations still needed at the observed rate are few (a binary32
+  // recursion would add rounding noise across the whole spectrum, which CG
+  // then has to remove again), otherwise after kProbe iterations the
+  // binary32 recursion, several times cheaper per iteration, takes over
+  constexpr int kProbe = 48;
+  constexpr double kFewIterations = 200.0;
+  MixedOut mo;
+  int kind = DG_FP64_EMU;
+  st = mixed_run<double>(h64, hemu, rhs, x, rtol, max_outer, inner_rtol, max_inner, kProbe, kFewIterations, mo);
+  if (st == DG_OK && mo.slow) {
+    kind = DG_FP32;
+    const int left = std::max(1, max_outer - mo.outer);
+    mo.slow = false;
+    st = mixed_run<float>(h64, h32, rhs, x, rtol, left, inner_rtol, max_inner, 0, 0.0, mo);
+  }
+  if (outer_iters) *outer_iters = mo.outer;
+  if (inner_iters) *inner_iters = mo.inner;
+  if (final_rel_res) *final_rel_res = mo.rel;
+  if (inner_prec) *inner_prec = kind;
   return st;
 }
 

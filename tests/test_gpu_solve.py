@@ -105,3 +105,49 @@ def test_l2_error_matches_oracle():
         ref = oracle.l2_error(mesh, p, x)
         assert abs(got - ref) <= 1e-12 * ref
         op.close()
+
+
+def test_mixed_with_double_float_inner_against_the_oracle():
+    """The inner recursion in double-float arithmetic (DG_FP64_EMU handle,
+    binary64 vectors) with FP64 residual replacement: the oracle's residual
+    of the solution."""
+    dgp.build()
+    mesh = dict(n=(4, 3, 5), periodic=False, mapping=1, amplitude=0.1)
+    p = 3
+    A = oracle.assemble(mesh, p, dict(op="sipg", coeff=1))
+    b = oracle.rhs(mesh, p, 1)
+    o64 = dgp.Operator(mesh["n"], p, geom="full", prec="fp64", mapping=1, coeff=1)
+    oe = dgp.Operator(mesh["n"], p, geom="full", prec="fp64emu", mapping=1, coeff=1)
+    oe.set_face_mode("loop")
+    rhs = torch.tensor(b, device="cuda")
+    x = torch.zeros_like(rhs)
+    st, outer, inner, rr = dgp.dg_cg_solve_mixed(o64.handle, oe.handle, rhs.data_ptr(), x.data_ptr(), 1e-10)
+    assert st == dgp.DG_OK and rr <= 1e-10 and outer >= 1
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 3e-10 * np.linalg.norm(b)
+    o64.close()
+    oe.close()
+
+
+@pytest.mark.parametrize("n,mapping,expect", [((12, 12, 12), 0, "fp64emu"), ((16, 16, 16), 1, "fp32")])
+def test_mixed_auto_picks_the_inner_arithmetic(n, mapping, expect):
+    """Cartesian manufactured problem: FP64 CG converges in a few dozen
+    iterations, so the probe keeps the double-float recursion; deformed mesh
+    with variable kappa: hundreds of iterations, so binary32 takes over.
+    Either way the FP64 residual meets the target and the solution matches
+    plain FP64 CG."""
+    dgp.build()
+    p = 3
+    kw = dict(geom="full" if mapping else "cartesian", mapping=mapping, coeff=mapping)
+    o64 = dgp.Operator(n, p, prec="fp64", **kw)
+    oe = dgp.Operator(n, p, prec="fp64emu", **kw)
+    o32 = dgp.Operator(n, p, prec="fp32", **kw)
+    rhs = o64.rhs(mapping)
+    xr, it, rr, st = o64.cg(rhs, rtol=1e-10, max_it=20000)
+    x = torch.zeros_like(rhs)
+    st, outer, inner, rel, kind = dgp.dg_cg_solve_mixed_auto(o64.handle, oe.handle, o32.handle, rhs.data_ptr(),
+                                                             x.data_ptr(), 1e-10)
+    assert st == dgp.DG_OK and rel <= 1e-10
+    assert kind == expect, (kind, it)
+    assert float((x - xr).norm() / xr.norm()) <= 1e-7
+    for o in (o64, oe, o32):
+        o.close()
