@@ -60,7 +60,9 @@ typedef enum { DG_OP_SIPG = 0, DG_OP_ADVECTION = 1 } dg_op;
  *  CARTESIAN: identity mapping only; constant J^{-1} and det J per mesh,
  *             no per-point arrays (the kappa coefficient, when enabled, is a
  *             table over x positions).
- *  AFFINE:    reserved; dg_setup returns DG_ERR_UNSUPPORTED.
+ *  (Value 1 is not a geometry variant: a per-cell compressed storage for
+ *  affine cells is not offered; affine (sheared, mapping 2) meshes take
+ *  FULL_JAC, MERGED or POSITIONS, and dg_setup answers 1 with DG_ERR_ARG.)
  *  FULL_JAC:  variant G3: per cell quadrature point J^{-1} (9 values) and
  *             det J * w (* kappa for SIPG) (1 value) -- for SIPG in binary64
  *             and double-float storage the weight is folded in as
@@ -85,7 +87,6 @@ typedef enum { DG_OP_SIPG = 0, DG_OP_ADVECTION = 1 } dg_op;
  *             allocates its work arrays; DG_FACE_ELEMENT is refused). */
 typedef enum {
   DG_GEOM_CARTESIAN = 0,
-  DG_GEOM_AFFINE = 1,
   DG_GEOM_FULL_JAC = 2,
   DG_GEOM_MERGED = 3,
   DG_GEOM_POSITIONS = 4

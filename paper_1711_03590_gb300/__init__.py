@@ -33,7 +33,6 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_OOM", 3: "DG_ERR_CUDA", 
 DG_OP_SIPG = 0
 DG_OP_ADVECTION = 1
 DG_GEOM_CARTESIAN = 0
-DG_GEOM_AFFINE = 1
 DG_GEOM_FULL_JAC = 2
 DG_GEOM_MERGED = 3
 DG_GEOM_POSITIONS = 4
@@ -43,7 +42,7 @@ DG_FP64 = 0
 DG_FP32 = 1
 DG_FP64_EMU = 2
 
-GEOMS = {"cartesian": DG_GEOM_CARTESIAN, "affine": DG_GEOM_AFFINE, "full": DG_GEOM_FULL_JAC,
+GEOMS = {"cartesian": DG_GEOM_CARTESIAN, "full": DG_GEOM_FULL_JAC,
          "merged": DG_GEOM_MERGED, "positions": DG_GEOM_POSITIONS}
 OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
 PRECS = {"fp64": DG_FP64, "fp32": DG_FP32, "fp64emu": DG_FP64_EMU}

@@ -1432,7 +1432,6 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   if (opts->prec != DG_FP64 && opts->prec != DG_FP32 && opts->prec != DG_FP64_EMU)
     return fail(nullptr, DG_ERR_ARG, "unknown precision");
   if (opts->coeff != 0 && opts->coeff != 1) return fail(nullptr, DG_ERR_ARG, "coeff must be 0 or 1");
-  if (geom == DG_GEOM_AFFINE) return fail(nullptr, DG_ERR_UNSUPPORTED, "affine geometry storage is not implemented");
   if (geom != DG_GEOM_CARTESIAN && geom != DG_GEOM_FULL_JAC && geom != DG_GEOM_MERGED && geom != DG_GEOM_POSITIONS)
     return fail(nullptr, DG_ERR_ARG, "unknown geometry variant");
   if (geom == DG_GEOM_CARTESIAN && mesh->mapping != 0)

@@ -53,5 +53,5 @@ def test_setup_errors_without_gpu_are_status_codes():
         dgp.dg_setup(m, 9, "full", dgp.make_opts())
     assert e.value.status == dgp.DG_ERR_ARG
     with pytest.raises(dgp.DGError) as e:
-        dgp.dg_setup(m, 2, "affine", dgp.make_opts())
-    assert e.value.status == dgp.DG_ERR_UNSUPPORTED
+        dgp.dg_setup(m, 2, 1, dgp.make_opts())  # 1: no geometry variant (no per-cell affine storage)
+    assert e.value.status == dgp.DG_ERR_ARG
