@@ -12,7 +12,10 @@ Mesh and form descriptions are plain dicts:
     (mapping 2: the affine shear x_i = X_i + a X_{(i+1) mod 3}; cell_jacobian
     "g2": the cell term's Jacobian is the collocation derivative of the Gauss
     points' positions, geometry variant G2 of Sec. 5; faces, penalty, rhs
-    and errors keep the analytic map)
+    and errors keep the analytic map; "basis": "lagrange" (default, on the
+    Gauss-Lobatto points) or "hermite" (the Hermite-like basis of degree
+    >= 3 defined in dg_oracle.c, whose face values and normal derivatives
+    each come from one coefficient per face point; Sec. 3.1))
     form = {"op": "sipg"|"advection", "coeff": 0|1,
             "velocity": (c0, c1, c2), "penalty_scale": 1.0}
 
@@ -40,7 +43,7 @@ _lib = None
 class _Mesh(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("periodic", ctypes.c_int),
                 ("mapping", ctypes.c_int), ("amplitude", ctypes.c_double),
-                ("cell_jacobian", ctypes.c_int)]
+                ("cell_jacobian", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 class _Form(ctypes.Structure):
@@ -64,6 +67,8 @@ def lib():
         L.or_lagrange.restype = _d
         L.or_lagrange_deriv.argtypes = [ctypes.c_int, _P(_d), ctypes.c_int, _d]
         L.or_lagrange_deriv.restype = _d
+        L.or_basis_value.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, ctypes.c_int]
+        L.or_basis_value.restype = _d
         L.or_cell_volume.argtypes = [_P(_Mesh), ctypes.c_int, _i64]
         L.or_cell_volume.restype = _d
         L.or_apply_cells.argtypes = [_P(_Mesh), ctypes.c_int, _P(_Form), _P(_d), _P(_d),
@@ -96,8 +101,10 @@ def _mesh(m):
         n = (n, n, n)
     cj = m.get("cell_jacobian", 0)
     cj = {"analytic": 0, "g2": 1}.get(cj, cj)
+    bs = m.get("basis", 0)
+    bs = {"lagrange": 0, "gl": 0, "hermite": 1}.get(bs, bs)
     return _Mesh((ctypes.c_int * 3)(*n), int(bool(m.get("periodic", False))),
-                 int(m.get("mapping", 0)), float(m.get("amplitude", 0.0)), int(cj))
+                 int(m.get("mapping", 0)), float(m.get("amplitude", 0.0)), int(cj), int(bs))
 
 
 def _form(f):
@@ -143,6 +150,12 @@ def lagrange(nodes, j, t, deriv=False):
     nodes = np.ascontiguousarray(nodes, dtype=np.float64)
     fn = lib().or_lagrange_deriv if deriv else lib().or_lagrange
     return fn(len(nodes), _ptr(nodes), j, float(t))
+
+
+def basis_value(kind, degree, j, t, deriv=False):
+    """1D basis function j (kind "lagrange" or "hermite") at t, or its derivative."""
+    kind = {"lagrange": 0, "gl": 0, "hermite": 1}.get(kind, kind)
+    return lib().or_basis_value(int(kind), int(degree), int(j), float(t), int(bool(deriv)))
 
 
 def cell_volume(mesh, degree, cell):

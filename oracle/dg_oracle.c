@@ -55,6 +55,8 @@ typedef struct {
   int cell_jacobian; /* 0: analytic J of the mapping; 1: variant G2 of Sec. 5, the
                         cell term's J is the collocation derivative of the
                         positions of the cell's Gauss points */
+  int basis;         /* 0: Lagrange on the Gauss-Lobatto points; 1: Hermite-like (degree >= 3,
+                        see herm_value) */
 } or_mesh;
 
 typedef struct {
@@ -250,18 +252,62 @@ static double kappa_at(const or_form *f, const double x[3]) {
 
 typedef struct {
   int k;
-  double gl[OR_MAXK];          /* GL nodes (basis support) */
+  int kind;                    /* 0 Gauss-Lobatto Lagrange, 1 Hermite-like */
+  double gl[OR_MAXK];          /* GL nodes (basis support of the Lagrange basis) */
+  double bn[OR_MAXK];          /* Hermite-like: nodes of the interior functions */
   double gq[OR_MAXK], gw[OR_MAXK]; /* Gauss points/weights (quadrature) */
 } basis1d;
 
-static int basis_init(basis1d *b, int degree) {
+static int basis_init(basis1d *b, int degree, int kind) {
   int k = degree + 1;
   if (degree < 1 || k > OR_MAXK) return -1;
+  if (kind == 1 && degree < 3) return -1;
   b->k = k;
+  b->kind = kind;
   double wl[OR_MAXK];
   if (or_gauss_lobatto(k, b->gl, wl)) return -1;
   if (or_gauss(k, b->gq, b->gw)) return -1;
+  if (kind == 1 && degree >= 4) {
+    /* the p - 3 interior nodes of the (p - 1)-point Gauss-Lobatto rule */
+    double x[OR_MAXK], w[OR_MAXK];
+    if (or_gauss_lobatto(degree - 1, x, w)) return -1;
+    for (int i = 0; i < degree - 3; ++i) b->bn[i] = x[i + 1];
+  }
   return 0;
+}
+
+/* Hermite-like basis of degree p >= 3 (the paper's Laplacian basis, Sec.
+ * 3.1 and the table of tensor-product kernels, is characterized there only
+ * by its face property: at most two nonzero entries in S_f and in D_f).
+ * Reading: the cubic Hermite functions at both ends,
+ *   phi_0 = (1 - t)^2 (1 + 2t), phi_1 = t (1 - t)^2,
+ *   phi_{p-1} = t^2 (1 - t),    phi_p = t^2 (3 - 2t),
+ * and for p >= 4 the interior functions phi_{2+i} = t^2 (1 - t)^2 l_i(t) /
+ * (b_i^2 (1 - b_i)^2), i = 0 .. p-4, with l_i the Lagrange polynomials on
+ * the p - 3 interior Gauss-Lobatto points b_i of degree p - 2 (phi_{2+i}(b_j)
+ * = delta_ij).  They span P_p (t^2 (1-t)^2 P_{p-4} plus the cubics), every
+ * function but phi_0 vanishes at t = 0 and every one but phi_1 has a zero
+ * derivative there (phi_1'(0) = 1), symmetrically at t = 1 (phi_p(1) = 1,
+ * phi_{p-1}'(1) = -1), and phi_{p-j}(t) = phi_j(1 - t).  deriv != 0: the
+ * derivative. */
+static double herm_value(const basis1d *b, int j, double t, int deriv) {
+  int p = b->k - 1;
+  double u = 1.0 - t;
+  if (j == 0) return deriv ? -6.0 * t * u : u * u * (1.0 + 2.0 * t);
+  if (j == 1) return deriv ? u * u - 2.0 * t * u : t * u * u;
+  if (j == p - 1) return deriv ? 2.0 * t * u - t * t : t * t * u;
+  if (j == p) return deriv ? 6.0 * t * u : t * t * (3.0 - 2.0 * t);
+  int i = j - 2, nb = p - 3;
+  double bi = b->bn[i], sc = 1.0 / (bi * bi * (1.0 - bi) * (1.0 - bi));
+  double g = t * t * u * u, dg = 2.0 * t * u * u - 2.0 * t * t * u;
+  double l = or_lagrange(nb, b->bn, i, t), dl = or_lagrange_deriv(nb, b->bn, i, t);
+  return sc * (deriv ? dg * l + g * dl : g * l);
+}
+
+/* 1D basis function j of the basis at t (or its derivative). */
+static double basis1(const basis1d *b, int j, double t, int deriv) {
+  if (b->kind == 1) return herm_value(b, j, t, deriv);
+  return deriv ? or_lagrange_deriv(b->k, b->gl, j, t) : or_lagrange(b->k, b->gl, j, t);
 }
 
 /* Point x and the Jacobian used by the cell integral at the Gauss point
@@ -296,8 +342,8 @@ static void basis_at(const basis1d *b, const double xi[3], double *val, double (
   double l[3][OR_MAXK], dl[3][OR_MAXK];
   for (int d = 0; d < 3; ++d)
     for (int j = 0; j < k; ++j) {
-      l[d][j] = or_lagrange(k, b->gl, j, xi[d]);
-      dl[d][j] = or_lagrange_deriv(k, b->gl, j, xi[d]);
+      l[d][j] = basis1(b, j, xi[d], 0);
+      dl[d][j] = basis1(b, j, xi[d], 1);
     }
   for (int i2 = 0; i2 < k; ++i2)
     for (int i1 = 0; i1 < k; ++i1)
@@ -320,7 +366,7 @@ static void to_physical(int nb, const double Jinv[3][3], double (*gref)[3], doub
 /* |K| by the cell's k-point Gauss rule of det J. */
 double or_cell_volume(const or_mesh *m, int degree, int64_t c) {
   basis1d b;
-  if (basis_init(&b, degree)) return -1.0;
+  if (basis_init(&b, degree, m->basis)) return -1.0;
   int k = b.k;
   double vol = 0.0;
   for (int q2 = 0; q2 < k; ++q2)
@@ -491,7 +537,7 @@ static void apply_one_cell(const or_mesh *m, const basis1d *b, const or_form *f,
 int or_apply_cells(const or_mesh *m, int degree, const or_form *f, const double *u, double *y,
                    const int64_t *cells, int64_t ncells) {
   basis1d b;
-  if (basis_init(&b, degree)) return -1;
+  if (basis_init(&b, degree, m->basis)) return -1;
   int64_t nc = cells ? ncells : n_cells(m);
   int nb3 = b.k * b.k * b.k;
   int err = 0;
@@ -558,7 +604,7 @@ int64_t or_assemble_nnz(const or_mesh *m, int degree) {
 int64_t or_assemble(const or_mesh *m, int degree, const or_form *f, int64_t *rowptr, int32_t *col,
                     double *valout) {
   basis1d b;
-  if (basis_init(&b, degree)) return -1;
+  if (basis_init(&b, degree, m->basis)) return -1;
   int k = b.k, nb3 = k * k * k;
   int64_t nc = n_cells(m);
   blockrow *br = (blockrow *)calloc(nc, sizeof(blockrow));
@@ -768,7 +814,7 @@ int or_cg_csr(int64_t n, const int64_t *rowptr, const int32_t *col, const double
  * interpolate / JxW / integrate sequence of Sec. 3.1, evaluated directly). */
 int or_mass_apply(const or_mesh *m, int degree, const double *u, double *y) {
   basis1d b;
-  if (basis_init(&b, degree)) return -1;
+  if (basis_init(&b, degree, m->basis)) return -1;
   int k = b.k, nb3 = k * k * k;
   int64_t nc = n_cells(m);
 #pragma omp parallel
@@ -815,7 +861,7 @@ static double rhs_f(int which, const double x[3]) {
 /* rhs_i = (phi_i, f) with the (k+2)-point Gauss rule per direction. */
 int or_rhs(const or_mesh *m, int degree, int which, double *rhs) {
   basis1d b;
-  if (basis_init(&b, degree)) return -1;
+  if (basis_init(&b, degree, m->basis)) return -1;
   int k = b.k, nb3 = k * k * k, kq = k + 2;
   double gq[OR_MAXK + 2], gw[OR_MAXK + 2];
   or_gauss(kq, gq, gw);
@@ -848,7 +894,7 @@ int or_rhs(const or_mesh *m, int degree, int which, double *rhs) {
 /* ||u_h - u||_{L2} with the (k+2)-point Gauss rule. */
 double or_l2_error(const or_mesh *m, int degree, const double *u) {
   basis1d b;
-  if (basis_init(&b, degree)) return -1.0;
+  if (basis_init(&b, degree, m->basis)) return -1.0;
   int k = b.k, nb3 = k * k * k, kq = k + 2;
   double gq[OR_MAXK + 2], gw[OR_MAXK + 2];
   or_gauss(kq, gq, gw);
@@ -877,10 +923,20 @@ double or_l2_error(const or_mesh *m, int degree, const double *u) {
   return sqrt(err);
 }
 
+/* Value (deriv = 0) or derivative (deriv = 1) of 1D basis function j of the
+ * given kind (0 Gauss-Lobatto Lagrange, 1 Hermite-like) and degree at t;
+ * NaN for an invalid degree. */
+double or_basis_value(int kind, int degree, int j, double t, int deriv) {
+  basis1d b;
+  if (basis_init(&b, degree, kind) || j < 0 || j > degree) return NAN;
+  return basis1(&b, j, t, deriv);
+}
+
 /* Physical coordinates of every dof (images of the GL nodes), xyz[3 i + d]. */
 int or_dof_points(const or_mesh *m, int degree, double *xyz) {
   basis1d b;
-  if (basis_init(&b, degree)) return -1;
+  if (m->basis != 0) return -1;  /* the Hermite-like basis is not nodal */
+  if (basis_init(&b, degree, m->basis)) return -1;
   int k = b.k, nb3 = k * k * k;
   int64_t nc = n_cells(m);
   for (int64_t c = 0; c < nc; ++c)

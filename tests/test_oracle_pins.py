@@ -476,3 +476,85 @@ def test_g2_converges_to_analytic_on_sine_map():
         if prev is not None:
             assert r < prev / 3, (p, r, prev)
         prev = r
+
+
+# ---- Hermite-like basis (Sec. 3.1: face values and normal derivatives from
+# at most two coefficients per face point) -----------------------------------
+
+def _hermite_numpy(p):
+    """The Hermite-like basis of degree p written out with numpy polynomial
+    algebra, independently of the oracle: cubic Hermite functions at both
+    ends and interior functions t^2 (1-t)^2 l_i(t), normalized at the
+    interior Gauss-Lobatto points of degree p - 2."""
+    from numpy.polynomial import polynomial as P
+    t, u = np.array([0.0, 1.0]), np.array([1.0, -1.0])
+    u2, t2 = P.polymul(u, u), P.polymul(t, t)
+    polys = [None] * (p + 1)
+    polys[0] = P.polymul(u2, [1.0, 2.0])
+    polys[1] = P.polymul(t, u2)
+    polys[p - 1] = P.polymul(t2, u)
+    polys[p] = P.polymul(t2, [3.0, -2.0])
+    if p >= 4:
+        nodes = ref1d.gl_nodes(p - 1)[1:-1]
+        bub = P.polymul(t2, u2)
+        for i, bi in enumerate(nodes):
+            li = np.array([1.0])
+            for m, bm in enumerate(nodes):
+                if m != i:
+                    li = P.polymul(li, np.array([-bm, 1.0]) / (bi - bm))
+            polys[2 + i] = P.polymul(bub, li) / (bi ** 2 * (1 - bi) ** 2)
+    return polys
+
+
+@pytest.mark.parametrize("p", range(3, 9))
+def test_hermite_basis_matches_its_definition(p):
+    from numpy.polynomial import polynomial as P
+    polys = _hermite_numpy(p)
+    for j, c in enumerate(polys):
+        assert len(np.trim_zeros(c, "b")) <= p + 1  # degree <= p
+        for t in np.linspace(0.0, 1.0, 7):
+            assert abs(oracle.basis_value("hermite", p, j, t) - P.polyval(t, c)) < 1e-11
+            # (the monomial form loses about 1e-12 in values and 1e-11 in derivatives at p = 8)
+            assert abs(oracle.basis_value("hermite", p, j, t, True) - P.polyval(t, P.polyder(c))) < 1e-10
+
+
+@pytest.mark.parametrize("p", range(3, 9))
+def test_hermite_face_property_and_symmetry(p):
+    """At t = 0 only phi_0 is nonzero (value 1) and only phi_1 has a nonzero
+    derivative (1); at t = 1 phi_p and phi_{p-1} (derivative -1): S_f and D_f
+    have one nonzero entry each, within the paper's "at most two"; and
+    phi_{p-j}(t) = phi_j(1 - t)."""
+    val = lambda j, t, d=False: oracle.basis_value("hermite", p, j, t, d)  # noqa: E731
+    np.testing.assert_allclose([val(j, 0.0) for j in range(p + 1)], np.eye(p + 1)[0], atol=1e-15)
+    np.testing.assert_allclose([val(j, 1.0) for j in range(p + 1)], np.eye(p + 1)[p], atol=1e-15)
+    np.testing.assert_allclose([val(j, 0.0, True) for j in range(p + 1)], np.eye(p + 1)[1], atol=1e-13)
+    np.testing.assert_allclose([val(j, 1.0, True) for j in range(p + 1)], -np.eye(p + 1)[p - 1], atol=1e-13)
+    for j in range(p + 1):
+        for t in (0.1, 0.37, 0.8):
+            assert abs(val(p - j, t) - val(j, 1.0 - t)) < 1e-13
+
+
+@pytest.mark.parametrize("mesh,form", [
+    (dict(n=(2, 2, 2), periodic=True, mapping=1, amplitude=0.1), dict(op="sipg", coeff=1)),
+    (dict(n=(2, 1, 3), periodic=False, mapping=0), dict(op="sipg", coeff=0)),
+    (dict(n=(2, 2, 1), periodic=False, mapping=1, amplitude=0.1), dict(op="advection")),
+])
+@pytest.mark.parametrize("p", [3, 4, 5])
+def test_hermite_operator_is_a_change_of_basis(mesh, form, p):
+    """Both bases span Q_p on every cell, so the Hermite-basis matrix is
+    T^T A T with A the Gauss-Lobatto Lagrange matrix and T the cell-wise
+    Kronecker product of T1[i][j] = phi^H_j(x^GL_i) (the Lagrange coefficients
+    of the Hermite-like functions), T1 built from the numpy construction."""
+    import scipy.sparse as sp
+    from numpy.polynomial import polynomial as P
+    k = p + 1
+    xs = ref1d.gl_nodes(k)
+    T1 = np.array([[P.polyval(x, c) for c in _hermite_numpy(p)] for x in xs])
+    Tc = np.kron(np.kron(T1, T1), T1)
+    T = sp.csr_matrix(sp.kron(sp.identity(oracle.n_cells(mesh)), Tc))
+    A = oracle.assemble(mesh, p, form)
+    H = oracle.assemble(dict(mesh, basis="hermite"), p, form)
+    R = (T.T @ A @ T).toarray()
+    assert np.abs(H.toarray() - R).max() < 1e-12 * np.abs(R).max()
+    u = dg_inputs.src_vector(H.shape[0], seed=11)
+    assert np.linalg.norm(oracle.apply(dict(mesh, basis="hermite"), p, form, u) - H @ u) < 1e-13 * np.linalg.norm(H @ u)
