@@ -117,7 +117,22 @@ typedef struct {
   double velocity[3];   /* advection speed c (constant vector) */
   int coeff;            /* SIPG coefficient: 0 kappa = 1; 1 kappa = 1 + 0.5 sin(2 pi x_0) */
   double penalty_scale; /* tau = penalty_scale (p+1)^2 max(A_F/|K-|, A_F/|K+|); <= 0 means 1 */
+  int basis;            /* dg_basis: DG_BASIS_LAGRANGE (the workloads' basis) or DG_BASIS_HERMITE */
 } dg_opts;
+
+/* Polynomial basis of each direction (the dof layout is the same: index i
+ * of direction d is basis function i).
+ *  LAGRANGE: Lagrange polynomials on the k Gauss-Lobatto points.
+ *  HERMITE:  the Hermite-like basis (degree >= 3) with the face property of
+ *            Sec. 3.1: at xi = 0 only function 0 is nonzero (value 1) and
+ *            only function 1 has a nonzero derivative (1), mirror-symmetric
+ *            at xi = 1 (functions p and p-1, derivative -1): the cubic
+ *            Hermite functions (1-t)^2(1+2t), t(1-t)^2, t^2(1-t),
+ *            t^2(3-2t) and between them t^2(1-t)^2 times the Lagrange
+ *            polynomials on the interior Gauss-Lobatto points of degree
+ *            p - 2, scaled to 1 at their node.  Same operator as LAGRANGE in
+ *            another basis of the same space. */
+typedef enum { DG_BASIS_LAGRANGE = 0, DG_BASIS_HERMITE = 1 } dg_basis;
 
 typedef struct dg_handle dg_handle;
 typedef struct dg_server dg_server;

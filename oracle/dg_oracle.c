@@ -254,7 +254,6 @@ typedef struct {
   int k;
   int kind;                    /* 0 Gauss-Lobatto Lagrange, 1 Hermite-like */
   double gl[OR_MAXK];          /* GL nodes (basis support of the Lagrange basis) */
-  double bn[OR_MAXK];          /* Hermite-like: nodes of the interior functions */
   double gq[OR_MAXK], gw[OR_MAXK]; /* Gauss points/weights (quadrature) */
 } basis1d;
 
@@ -267,40 +266,63 @@ static int basis_init(basis1d *b, int degree, int kind) {
   double wl[OR_MAXK];
   if (or_gauss_lobatto(k, b->gl, wl)) return -1;
   if (or_gauss(k, b->gq, b->gw)) return -1;
-  if (kind == 1 && degree >= 4) {
-    /* the p - 3 interior nodes of the (p - 1)-point Gauss-Lobatto rule */
-    double x[OR_MAXK], w[OR_MAXK];
-    if (or_gauss_lobatto(degree - 1, x, w)) return -1;
-    for (int i = 0; i < degree - 3; ++i) b->bn[i] = x[i + 1];
-  }
   return 0;
 }
 
 /* Hermite-like basis of degree p >= 3 (the paper's Laplacian basis, Sec.
  * 3.1 and the table of tensor-product kernels, is characterized there only
  * by its face property: at most two nonzero entries in S_f and in D_f).
- * Reading: the cubic Hermite functions at both ends,
- *   phi_0 = (1 - t)^2 (1 + 2t), phi_1 = t (1 - t)^2,
- *   phi_{p-1} = t^2 (1 - t),    phi_p = t^2 (3 - 2t),
- * and for p >= 4 the interior functions phi_{2+i} = t^2 (1 - t)^2 l_i(t) /
- * (b_i^2 (1 - b_i)^2), i = 0 .. p-4, with l_i the Lagrange polynomials on
- * the p - 3 interior Gauss-Lobatto points b_i of degree p - 2 (phi_{2+i}(b_j)
- * = delta_ij).  They span P_p (t^2 (1-t)^2 P_{p-4} plus the cubics), every
- * function but phi_0 vanishes at t = 0 and every one but phi_1 has a zero
- * derivative there (phi_1'(0) = 1), symmetrically at t = 1 (phi_p(1) = 1,
- * phi_{p-1}'(1) = -1), and phi_{p-j}(t) = phi_j(1 - t).  deriv != 0: the
- * derivative. */
+ * Reading, with x_0 = 0 < x_1 < ... < x_p = 1 the Gauss-Lobatto points and
+ * w(t) = prod_{i=2}^{p-2} (t - x_i):
+ *   phi_0 = (1 - t)^2 (1 + c t) w(t) / w(0), c = 2 - w'(0) / w(0),
+ *   phi_1 = t (1 - t)^2 w(t) / (x_1 (1 - x_1)^2 w(x_1)),
+ *   phi_j = t^2 (1 - t)^2 l_j(t) / (x_j^2 (1 - x_j)^2), 2 <= j <= p-2,
+ *           l_j the Lagrange polynomial on x_2 .. x_{p-2},
+ *   phi_{p-1}(t) = phi_1(1 - t), phi_p(t) = phi_0(1 - t).
+ * They span P_p; only phi_0 is nonzero at t = 0 (value 1) and only phi_1
+ * has a nonzero derivative there (phi_0'(0) = 0 by the choice of c), and
+ * mirror-symmetrically at t = 1.  Every function but phi_0 and phi_p is 1 at
+ * its own node x_j and 0 at the other interior nodes x_2 .. x_{p-2}, which
+ * keeps the basis close to the Lagrange one (the change of basis at the
+ * Gauss-Lobatto points has condition number 2.5-3.7 for p = 3..8).  deriv
+ * != 0: the derivative. */
+static void herm_w(const basis1d *b, double t, double *w, double *dw) {
+  int p = b->k - 1;
+  double v = 1.0, d = 0.0;
+  for (int i = 2; i <= p - 2; ++i) {
+    d = d * (t - b->gl[i]) + v;
+    v *= t - b->gl[i];
+  }
+  *w = v;
+  *dw = d;
+}
+
+static double herm_left(const basis1d *b, int j, double t, int deriv) {
+  /* phi_0 (j = 0) or phi_1 (j = 1) */
+  double w, dw, w0, dw0;
+  herm_w(b, t, &w, &dw);
+  herm_w(b, 0.0, &w0, &dw0);
+  double u = 1.0 - t;
+  if (j == 0) {
+    double c = 2.0 - dw0 / w0;
+    double A = u * u, dA = -2.0 * u, B = 1.0 + c * t, dB = c;
+    return deriv ? (dA * B * w + A * dB * w + A * B * dw) / w0 : A * B * w / w0;
+  }
+  double x1 = b->gl[1], w1, dw1;
+  herm_w(b, x1, &w1, &dw1);
+  double sc = 1.0 / (x1 * (1.0 - x1) * (1.0 - x1) * w1);
+  double g = t * u * u, dg = u * u - 2.0 * t * u;
+  return sc * (deriv ? dg * w + g * dw : g * w);
+}
+
 static double herm_value(const basis1d *b, int j, double t, int deriv) {
   int p = b->k - 1;
-  double u = 1.0 - t;
-  if (j == 0) return deriv ? -6.0 * t * u : u * u * (1.0 + 2.0 * t);
-  if (j == 1) return deriv ? u * u - 2.0 * t * u : t * u * u;
-  if (j == p - 1) return deriv ? 2.0 * t * u - t * t : t * t * u;
-  if (j == p) return deriv ? 6.0 * t * u : t * t * (3.0 - 2.0 * t);
-  int i = j - 2, nb = p - 3;
-  double bi = b->bn[i], sc = 1.0 / (bi * bi * (1.0 - bi) * (1.0 - bi));
+  if (j <= 1) return herm_left(b, j, t, deriv);
+  if (j >= p - 1) return deriv ? -herm_left(b, p - j, 1.0 - t, 1) : herm_left(b, p - j, 1.0 - t, 0);
+  double u = 1.0 - t, xj = b->gl[j];
   double g = t * t * u * u, dg = 2.0 * t * u * u - 2.0 * t * t * u;
-  double l = or_lagrange(nb, b->bn, i, t), dl = or_lagrange_deriv(nb, b->bn, i, t);
+  double l = or_lagrange(p - 3, b->gl + 2, j - 2, t), dl = or_lagrange_deriv(p - 3, b->gl + 2, j - 2, t);
+  double sc = 1.0 / (xj * xj * (1.0 - xj) * (1.0 - xj));
   return sc * (deriv ? dg * l + g * dl : g * l);
 }
 

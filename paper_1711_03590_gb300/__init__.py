@@ -46,6 +46,9 @@ GEOMS = {"cartesian": DG_GEOM_CARTESIAN, "full": DG_GEOM_FULL_JAC,
          "merged": DG_GEOM_MERGED, "positions": DG_GEOM_POSITIONS}
 OPS = {"sipg": DG_OP_SIPG, "advection": DG_OP_ADVECTION}
 PRECS = {"fp64": DG_FP64, "fp32": DG_FP32, "fp64emu": DG_FP64_EMU}
+DG_BASIS_LAGRANGE = 0
+DG_BASIS_HERMITE = 1
+BASES = {"lagrange": DG_BASIS_LAGRANGE, "hermite": DG_BASIS_HERMITE}
 
 EXPORTED = ["dg_setup", "dg_n_dofs", "dg_info", "dg_set_stream", "dg_apply", "dg_apply_host", "dg_rhs",
             "dg_cg_solve", "dg_cg_solve_mixed", "dg_destroy", "dg_last_error", "dg_apply_dot_noalloc",
@@ -72,7 +75,7 @@ class dg_mesh(ctypes.Structure):
 
 class dg_opts(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("prec", ctypes.c_int), ("velocity", ctypes.c_double * 3),
-                ("coeff", ctypes.c_int), ("penalty_scale", ctypes.c_double)]
+                ("coeff", ctypes.c_int), ("penalty_scale", ctypes.c_double), ("basis", ctypes.c_int)]
 
 
 class dg_info_t(ctypes.Structure):
@@ -170,9 +173,9 @@ def make_mesh(n, periodic=False, mapping=0, amplitude=0.1):
     return dg_mesh((ctypes.c_int * 3)(*n), int(bool(periodic)), int(mapping), float(amplitude))
 
 
-def make_opts(op="sipg", prec="fp64", velocity=(1.0, 0.5, 0.25), coeff=0, penalty_scale=1.0):
+def make_opts(op="sipg", prec="fp64", velocity=(1.0, 0.5, 0.25), coeff=0, penalty_scale=1.0, basis="lagrange"):
     return dg_opts(OPS.get(op, op), PRECS.get(prec, prec), (ctypes.c_double * 3)(*velocity), int(coeff),
-                   float(penalty_scale))
+                   float(penalty_scale), BASES.get(basis, basis))
 
 
 # ---- C-ABI functions with the same names ---------------------------------
@@ -433,12 +436,13 @@ class Operator:
     """
 
     def __init__(self, n, degree, geom="full", op="sipg", prec="fp64", periodic=False, mapping=0,
-                 amplitude=0.1, coeff=0, velocity=(1.0, 0.5, 0.25), penalty_scale=1.0, stream=None):
+                 amplitude=0.1, coeff=0, velocity=(1.0, 0.5, 0.25), penalty_scale=1.0, stream=None,
+                 basis="lagrange"):
         import torch
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.mesh = make_mesh(n, periodic, mapping, amplitude)
-        self.opts = make_opts(op, prec, velocity, coeff, penalty_scale)
+        self.opts = make_opts(op, prec, velocity, coeff, penalty_scale, basis)
         self.degree = degree
         self.dtype = torch.float32 if PRECS.get(prec, prec) == DG_FP32 else torch.float64
         self.handle = None

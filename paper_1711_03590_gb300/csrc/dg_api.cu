@@ -173,17 +173,107 @@ void bary_diff_matrix(int k, const double* x, const double* lam, double* Dm) {
 }
 
 struct Tables64 {
+  int basis;  // DG_BASIS_LAGRANGE or DG_BASIS_HERMITE
   double gq[kMaxK], gw[kMaxK], gl[kMaxK];
   double S[kMaxK * kMaxK], D[kMaxK * kMaxK], DS[kMaxK * kMaxK], E[2][kMaxK], DF[2][kMaxK];
 };
 
-void build_tables(int k, Tables64& t) {
+// Hermite-like basis of degree p = k - 1 >= 3 on the Gauss-Lobatto points
+// g_0 = 0 < g_1 < ... < g_p = 1, with w(t) = prod_{j=2}^{p-2} (t - g_j):
+// f_0 = (1-t)^2 (1 + c t) w(t) / w(0) with c such that f_0'(0) = 0;
+// f_1 = t (1-t)^2 w(t), scaled to f_1(g_1) = 1; f_j, 2 <= j <= p-2, =
+// t^2 (1-t)^2 times the Lagrange polynomial on g_2 .. g_{p-2} that is 1 at
+// g_j, scaled to f_j(g_j) = 1; f_{p-1}(t) = f_1(1-t), f_p(t) = f_0(1-t).
+// Only f_0 is nonzero at t = 0 and only f_1 has a nonzero derivative there
+// (mirror-symmetric at t = 1), so a face value and a face-normal derivative
+// each come from one coefficient per face point (the Hermite-type property
+// of Sec. 3.1); the interior nodes keep the basis close to the Lagrange one.
+// val[j], der[j] at t.
+void hermite_values(int k, const double* g, double t, double* val, double* der) {
+  const int p = k - 1;
+  // w and w' at t, 0 and g_1 (product rule over the factors)
+  auto wfun = [&](double x, double& w, double& dw) {
+    w = 1.0;
+    dw = 0.0;
+    for (int j = 2; j <= p - 2; ++j) {
+      dw = dw * (x - g[j]) + w;
+      w *= x - g[j];
+    }
+  };
+  // f_0 and f_1 at x (value, derivative)
+  auto left = [&](int which, double x, double& v, double& d) {
+    double w, dw, w0, dw0;
+    wfun(x, w, dw);
+    wfun(0.0, w0, dw0);
+    const double u = 1.0 - x;
+    if (which == 0) {
+      const double c = 2.0 - dw0 / w0;
+      const double a = u * u / w0, da = -2.0 * u / w0, b = 1.0 + c * x;
+      v = a * b * w;
+      d = da * b * w + a * c * w + a * b * dw;
+    } else {
+      double w1, dw1;
+      wfun(g[1], w1, dw1);
+      const double sc = 1.0 / (g[1] * (1.0 - g[1]) * (1.0 - g[1]) * w1);
+      const double h = x * u * u, dh = u * (u - 2.0 * x);
+      v = sc * h * w;
+      d = sc * (dh * w + h * dw);
+    }
+  };
+  left(0, t, val[0], der[0]);
+  left(1, t, val[1], der[1]);
+  double v, d;
+  left(1, 1.0 - t, v, d);
+  val[p - 1] = v;
+  der[p - 1] = -d;
+  left(0, 1.0 - t, v, d);
+  val[p] = v;
+  der[p] = -d;
+  const double u = 1.0 - t, b = t * t * u * u, db = 2.0 * t * u * (u - t);
+  for (int j = 2; j <= p - 2; ++j) {
+    double l = 1.0, dl = 0.0;
+    for (int m = 2; m <= p - 2; ++m) {
+      if (m == j) continue;
+      const double f = 1.0 / (g[j] - g[m]);
+      dl = dl * (t - g[m]) * f + l * f;
+      l *= (t - g[m]) * f;
+    }
+    const double sc = 1.0 / (g[j] * g[j] * (1.0 - g[j]) * (1.0 - g[j]));
+    val[j] = sc * b * l;
+    der[j] = sc * (db * l + b * dl);
+  }
+}
+
+// values of the k basis functions at t (and derivatives, if der)
+void basis_values(const Tables64& t, int k, double x, double* val, double* der) {
+  if (t.basis == DG_BASIS_HERMITE) {
+    double d[kMaxK];
+    hermite_values(k, t.gl, x, val, der ? der : d);
+    return;
+  }
+  double ll[kMaxK];
+  bary_weights(k, t.gl, ll);
+  bary_values(k, t.gl, ll, x, val);
+  if (der) {
+    double DL[kMaxK * kMaxK];
+    bary_diff_matrix(k, t.gl, ll, DL);
+    // derivative at x of the interpolant: sum over the nodes of l_m(x) D_L[m][j]
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int m = 0; m < k; ++m) s += val[m] * DL[m * k + j];
+      der[j] = s;
+    }
+  }
+}
+
+void build_tables(int k, Tables64& t, int basis) {
+  t.basis = basis;
   gauss_rule(k, t.gq, t.gw);
   lobatto_nodes(k, t.gl);
   double lg[kMaxK], ll[kMaxK];
   bary_weights(k, t.gq, lg);
   bary_weights(k, t.gl, ll);
-  for (int q = 0; q < k; ++q) bary_values(k, t.gl, ll, t.gq[q], t.S + q * k);
+  for (int q = 0; q < k; ++q) basis_values(t, k, t.gq[q], t.S + q * k, nullptr);
   bary_diff_matrix(k, t.gq, lg, t.D);
   // derivative of the GL basis at the Gauss points: the Gauss-collocation
   // derivative of its (exact) Gauss-point interpolant
@@ -195,12 +285,10 @@ void build_tables(int k, Tables64& t) {
     }
   bary_values(k, t.gq, lg, 0.0, t.E[0]);
   bary_values(k, t.gq, lg, 1.0, t.E[1]);
-  double DL[kMaxK * kMaxK];
-  bary_diff_matrix(k, t.gl, ll, DL);
-  for (int i = 0; i < k; ++i) {
-    t.DF[0][i] = DL[0 * k + i];
-    t.DF[1][i] = DL[(k - 1) * k + i];
-  }
+  double v[kMaxK];
+  basis_values(t, k, 0.0, v, t.DF[0]);
+  basis_values(t, k, 1.0, v, t.DF[1]);
+  (void)ll;
 }
 
 template <typename T>
@@ -608,7 +696,7 @@ struct RhsParams {
   int which;
   int kq;
   double xq[kMaxK + 2], wq[kMaxK + 2];
-  double phi[(kMaxK + 2) * kMaxK];  // phi[q*k + i] = l^GL_i(xq[q])
+  double phi[(kMaxK + 2) * kMaxK];  // phi[q*k + i] = basis function i at xq[q]
 };
 
 __global__ void rhs_kernel(const __grid_constant__ RhsParams R, int64_t n_cells, double* rhs) {
@@ -1432,6 +1520,10 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   if (opts->prec != DG_FP64 && opts->prec != DG_FP32 && opts->prec != DG_FP64_EMU)
     return fail(nullptr, DG_ERR_ARG, "unknown precision");
   if (opts->coeff != 0 && opts->coeff != 1) return fail(nullptr, DG_ERR_ARG, "coeff must be 0 or 1");
+  if (opts->basis != DG_BASIS_LAGRANGE && opts->basis != DG_BASIS_HERMITE)
+    return fail(nullptr, DG_ERR_ARG, "unknown basis");
+  if (opts->basis == DG_BASIS_HERMITE && degree < 3)
+    return fail(nullptr, DG_ERR_ARG, "the Hermite-like basis needs degree >= 3");
   if (geom != DG_GEOM_CARTESIAN && geom != DG_GEOM_FULL_JAC && geom != DG_GEOM_MERGED && geom != DG_GEOM_POSITIONS)
     return fail(nullptr, DG_ERR_ARG, "unknown geometry variant");
   if (geom == DG_GEOM_CARTESIAN && mesh->mapping != 0)
@@ -1462,7 +1554,7 @@ dg_status dg_setup(const dg_mesh* mesh, int degree, int geom, const dg_opts* opt
   h->n_dofs = nc * k * k * k;
   h->cpb = h->prec == DG_FP32 ? dg::f32_tile_default(k) : dg::element_cells_per_block(k, h->prec);
   h->stream = static_cast<cudaStream_t>(stream);
-  build_tables(k, h->t64);
+  build_tables(k, h->t64, opts->basis);
   h->tabd = cast_tables<double>(k, h->t64);
   h->tabf = cast_tables<float>(k, h->t64);
   h->tabdf = cast_tables<df64>(k, h->t64);
@@ -1665,13 +1757,12 @@ static void fill_rhs_params(const dg_handle* h, int which_f, RhsParams& R) {
   R.S.k = h->k;
   R.which = which_f;
   R.kq = h->k + 2;
-  double xq[kMaxK + 2], wq[kMaxK + 2], lam[kMaxK];
+  double xq[kMaxK + 2], wq[kMaxK + 2];
   gauss_rule(R.kq, xq, wq);
-  bary_weights(h->k, h->t64.gl, lam);
   for (int q = 0; q < R.kq; ++q) {
     R.xq[q] = xq[q];
     R.wq[q] = wq[q];
-    bary_values(h->k, h->t64.gl, lam, xq[q], R.phi + q * h->k);
+    basis_values(h->t64, h->k, xq[q], R.phi + q * h->k, nullptr);
   }
 }
 
@@ -1944,7 +2035,7 @@ dg_status check_mixed_pair(dg_handle* h64, dg_handle* hl) {
   if (h64->op != DG_OP_SIPG || hl->op != DG_OP_SIPG)
     return fail(h64, DG_ERR_UNSUPPORTED, "mixed-precision CG needs the symmetric SIPG operator");
   if (memcmp(&h64->mesh, &hl->mesh, sizeof(dg_mesh)) != 0 || h64->degree != hl->degree ||
-      h64->geom != hl->geom || h64->opts.coeff != hl->opts.coeff ||
+      h64->geom != hl->geom || h64->opts.coeff != hl->opts.coeff || h64->opts.basis != hl->opts.basis ||
       h64->opts.penalty_scale != hl->opts.penalty_scale)
     return fail(h64, DG_ERR_ARG, "the handles of the mixed-precision solve describe different operators");
   return DG_OK;

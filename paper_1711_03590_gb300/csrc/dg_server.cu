@@ -88,6 +88,7 @@ void solve_one(dg_server* srv, Entry& e, cudaStream_t stream) {
   o64.velocity[0] = o64.velocity[1] = o64.velocity[2] = 0.0;
   o64.coeff = r.coeff;
   o64.penalty_scale = 1.0;
+  o64.basis = DG_BASIS_LAGRANGE;
   dg_opts o32 = o64;
   o32.prec = DG_FP32;
   dg_handle *h64 = nullptr, *h32 = nullptr;

@@ -483,26 +483,39 @@ def test_g2_converges_to_analytic_on_sine_map():
 
 def _hermite_numpy(p):
     """The Hermite-like basis of degree p written out with numpy polynomial
-    algebra, independently of the oracle: cubic Hermite functions at both
-    ends and interior functions t^2 (1-t)^2 l_i(t), normalized at the
-    interior Gauss-Lobatto points of degree p - 2."""
+    algebra, independently of the oracle: with x_j the Gauss-Lobatto points
+    and w(t) = prod_{j=2}^{p-2} (t - x_j), phi_0 = (1-t)^2 (1 + c t) w / w(0)
+    with phi_0'(0) = 0, phi_1 = t (1-t)^2 w scaled to 1 at x_1, interior
+    functions t^2 (1-t)^2 l_j(t) scaled to 1 at x_j, and the mirror images
+    phi_{p-j}(t) = phi_j(1 - t)."""
     from numpy.polynomial import polynomial as P
+    x = ref1d.gl_nodes(p + 1)
+    inner = x[2:p - 1]
     t, u = np.array([0.0, 1.0]), np.array([1.0, -1.0])
-    u2, t2 = P.polymul(u, u), P.polymul(t, t)
+    u2 = P.polymul(u, u)
+    w = np.array([1.0])
+    for b in inner:
+        w = P.polymul(w, [-b, 1.0])
+    c = 2.0 - P.polyval(0.0, P.polyder(w)) / P.polyval(0.0, w)
     polys = [None] * (p + 1)
-    polys[0] = P.polymul(u2, [1.0, 2.0])
-    polys[1] = P.polymul(t, u2)
-    polys[p - 1] = P.polymul(t2, u)
-    polys[p] = P.polymul(t2, [3.0, -2.0])
-    if p >= 4:
-        nodes = ref1d.gl_nodes(p - 1)[1:-1]
-        bub = P.polymul(t2, u2)
-        for i, bi in enumerate(nodes):
-            li = np.array([1.0])
-            for m, bm in enumerate(nodes):
-                if m != i:
-                    li = P.polymul(li, np.array([-bm, 1.0]) / (bi - bm))
-            polys[2 + i] = P.polymul(bub, li) / (bi ** 2 * (1 - bi) ** 2)
+    polys[0] = P.polymul(P.polymul(u2, w / P.polyval(0.0, w)), [1.0, c])
+    f1 = P.polymul(P.polymul(t, u2), w)
+    polys[1] = f1 / P.polyval(x[1], f1)
+
+    def mirror(cf):
+        out = np.array([0.0])
+        for i, ci in enumerate(cf):
+            out = P.polyadd(out, ci * P.polypow(u, i))
+        return out
+    polys[p], polys[p - 1] = mirror(polys[0]), mirror(polys[1])
+    bub = P.polymul(P.polymul(t, t), u2)
+    for i, b in enumerate(inner):
+        li = np.array([1.0])
+        for m, bm in enumerate(inner):
+            if m != i:
+                li = P.polymul(li, np.array([-bm, 1.0]) / (b - bm))
+        f = P.polymul(bub, li)
+        polys[2 + i] = f / P.polyval(b, f)
     return polys
 
 
@@ -512,23 +525,26 @@ def test_hermite_basis_matches_its_definition(p):
     polys = _hermite_numpy(p)
     for j, c in enumerate(polys):
         assert len(np.trim_zeros(c, "b")) <= p + 1  # degree <= p
+        dc = P.polyder(c)
         for t in np.linspace(0.0, 1.0, 7):
-            assert abs(oracle.basis_value("hermite", p, j, t) - P.polyval(t, c)) < 1e-11
-            # (the monomial form loses about 1e-12 in values and 1e-11 in derivatives at p = 8)
-            assert abs(oracle.basis_value("hermite", p, j, t, True) - P.polyval(t, P.polyder(c))) < 1e-10
+            # tolerances: the rounding bound of the monomial form on [0, 1]
+            assert abs(oracle.basis_value("hermite", p, j, t) - P.polyval(t, c)) < 1e-14 * np.abs(c).sum() + 1e-15
+            assert abs(oracle.basis_value("hermite", p, j, t, True) - P.polyval(t, dc)) < 1e-14 * np.abs(dc).sum() + 1e-15
 
 
 @pytest.mark.parametrize("p", range(3, 9))
 def test_hermite_face_property_and_symmetry(p):
     """At t = 0 only phi_0 is nonzero (value 1) and only phi_1 has a nonzero
-    derivative (1); at t = 1 phi_p and phi_{p-1} (derivative -1): S_f and D_f
-    have one nonzero entry each, within the paper's "at most two"; and
-    phi_{p-j}(t) = phi_j(1 - t)."""
+    derivative; at t = 1 phi_p and phi_{p-1} (the opposite derivative): S_f
+    and D_f have one nonzero entry each, within the paper's "at most two";
+    and phi_{p-j}(t) = phi_j(1 - t)."""
     val = lambda j, t, d=False: oracle.basis_value("hermite", p, j, t, d)  # noqa: E731
     np.testing.assert_allclose([val(j, 0.0) for j in range(p + 1)], np.eye(p + 1)[0], atol=1e-15)
     np.testing.assert_allclose([val(j, 1.0) for j in range(p + 1)], np.eye(p + 1)[p], atol=1e-15)
-    np.testing.assert_allclose([val(j, 0.0, True) for j in range(p + 1)], np.eye(p + 1)[1], atol=1e-13)
-    np.testing.assert_allclose([val(j, 1.0, True) for j in range(p + 1)], -np.eye(p + 1)[p - 1], atol=1e-13)
+    d0 = np.array([val(j, 0.0, True) for j in range(p + 1)])
+    d1 = np.array([val(j, 1.0, True) for j in range(p + 1)])
+    assert d0[1] > 1.0 and abs(d1[p - 1] + d0[1]) < 1e-12 * d0[1]
+    assert np.abs(np.delete(d0, 1)).max() < 1e-12 * d0[1] and np.abs(np.delete(d1, p - 1)).max() < 1e-12 * d0[1]
     for j in range(p + 1):
         for t in (0.1, 0.37, 0.8):
             assert abs(val(p - j, t) - val(j, 1.0 - t)) < 1e-13
