@@ -637,6 +637,35 @@ def degree_sweep_metrics(torch, dgp, steps=30):
     return {"operator": "SIPG, kappa = 1 + 0.5 sin(2 pi x), Dirichlet", "hbm_peak_gbs": hbm, "rows": rows}
 
 
+def fp32_degree_sweep(torch, dgp, steps=20, degrees=(2, 3, 4, 5, 6)):
+    """The binary32 G3 SIPG apply (sine-deformed mesh, kappa variable,
+    Dirichlet) for p = 2..6 on the paper's larger-than-cache size schedule
+    (128^3 for p <= 2, 64^3 for p = 3-5, 32^3 for p >= 6): DoFs/s from the
+    mean per-apply CUDA-event time, GB/s of the algorithmic bytes and the
+    fraction of the measured HBM bandwidth."""
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    rows = []
+    for p in degrees:
+        n = dg_inputs.paper_size_schedule(p)
+        o = dgp.Operator(n, p, geom="full", prec="fp32", mapping=1, amplitude=0.1, coeff=1)
+        src = torch.tensor(dg_inputs.src_vector(o.n_dofs, 3), dtype=o.dtype, device="cuda")
+        dst = torch.empty_like(src)
+        for _ in range(3):
+            o.apply(src, dst)
+        _, ms = time_applies(torch, o, src, dst, steps)
+        bpd = bytes_per_dof(p + 1, 4, "sipg", "full")
+        gbs = bpd * o.n_dofs / (ms / 1e3) / 1e9
+        rows.append({"p": p, "mesh": "%d^3" % n, "dofs": o.n_dofs, "us": round(ms * 1e3, 2),
+                     "gdofs_per_s": round(o.n_dofs / (ms / 1e3) / 1e9, 3), "bytes_per_dof": round(bpd, 2),
+                     "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                     "hbm_frac_survey_bytes": round((8 + 40 + 84 / (p + 1)) * o.n_dofs / (ms / 1e3) / 1e9 / hbm, 4)})
+        o.close()
+        del src, dst
+        torch.cuda.empty_cache()
+    return {"operator": "SIPG G3, kappa = 1 + 0.5 sin(2 pi x), Dirichlet, FP32", "hbm_peak_gbs": hbm, "rows": rows}
+
+
 def cpu_baseline(workload, form, target_s=12.0):
     """The FP64 oracle (cell-by-cell brute-force quadrature, OpenMP on the
     host cores) on a seeded sample of cells of the same workload; DoFs/s =
@@ -941,6 +970,7 @@ def main():
         tota, la = time_applies(torch, opa, src, dst, max(10, args.steps // 2))
         extras["advection_fp64"] = {"value": n / (tota / max(10, args.steps // 2) / 1e3), "unit": UNIT}
         opa.close()
+        extras["fp32_degree_sweep"] = fp32_degree_sweep(torch, dgp)
 
     if not args.no_extras and args.prec == "fp64":
         extras["solve"] = solve_metrics(torch, dgp, args)
@@ -955,7 +985,7 @@ def main():
         # the serving stream's shape (dofs lognormal over 1e4..2e7, degrees
         # 2..6, half Cartesian / half deformed, mixed CG to 1e-8, 120 GB),
         # bounded to 160 requests: saturated, then 90% load with both policies
-        extras["serve_config5_bounded"] = serve_metrics(dgp, count=160, seed=11, dof_hi=2e7, rates=(0.9,),
+        extras["serve_config5_bounded"] = serve_metrics(dgp, count=160, seed=11, dof_hi=2e7, rates=(0.5, 0.9),
                                                         policies=(0, 1), max_age_s=5.0)
 
     cpu = None
