@@ -771,9 +771,10 @@ def main():
 
     if args.serve_config5:
         # the full stream: 2000 requests, 1e4..2e7 dofs (mean about 2.7e6),
-        # saturated and at 90% of that capacity; each run prints when done
+        # saturated, then at 90% of that capacity under FIFO and under
+        # shortest-job-first admission; each run prints when done
         if rank == 0:
-            serve_metrics(dgp, count=2000, seed=11, dof_hi=2e7, rates=(0.9,),
+            serve_metrics(dgp, count=2000, seed=11, dof_hi=2e7, rates=(0.9,), policies=(0, 1), max_age_s=5.0,
                           progress=lambda r: print(json.dumps({"serve_config5": r}), flush=True))
         return
     if args.degree_sweep:
