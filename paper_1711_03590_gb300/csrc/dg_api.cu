@@ -1615,7 +1615,7 @@ dg_status dg_info(const dg_handle* h, dg_info_t* info) {
   info->face_geometry_bytes = h->face_bytes;
   info->cells_per_block = h->cpb;
   info->threads_per_block = h->cpb * h->k * h->k;
-  info->shared_bytes_per_block = h->prec == DG_FP32 ? dg::f32_smem_bytes(h->k, h->op, h->cpb)
+  info->shared_bytes_per_block = h->prec == DG_FP32 ? dg::f32_smem_bytes(h->k, h->op, h->cpb, kernel_geo(h->geom))
                                  : h->face_mode == DG_FACE_LOOP ? dg::split_smem_backward(h->k, h->op, h->cpb)
                                                                 : dg::smem_bytes_per_block(h->k, h->op, 8, h->cpb);
   info->blocks = apply_blocks(h);

@@ -24,6 +24,12 @@ CASES = [
     dict(n=(5, 6, 4), p=3, geom="full", prec="fp64", periodic=False, mapping=1, coeff=1, op="sipg", face="loop"),
     dict(n=(4, 4, 4), p=5, geom="merged", prec="fp64emu", periodic=True, mapping=1, coeff=0, op="advection",
          face="loop"),
+    # G2 (positions; binary64 runs the face loop), the sheared mapping, the Hermite-like basis
+    dict(n=(4, 3, 5), p=3, geom="positions", prec="fp64", periodic=False, mapping=1, coeff=1, op="sipg"),
+    dict(n=(3, 3, 3), p=4, geom="positions", prec="fp32", periodic=True, mapping=1, coeff=1, op="sipg"),
+    dict(n=(3, 4, 3), p=5, geom="full", prec="fp64", periodic=False, mapping=2, coeff=1, op="sipg", basis="hermite"),
+    dict(n=(3, 3, 4), p=3, geom="merged", prec="fp32", periodic=False, mapping=1, coeff=0, op="advection",
+         basis="hermite"),
 ]
 
 
@@ -33,7 +39,7 @@ def test_batch_equals_individual_applies(branches, autotune):
     ops, srcs, dsts, refs = [], [], [], []
     for i, c in enumerate(CASES):
         op = dgp.Operator(c["n"], c["p"], geom=c["geom"], op=c["op"], prec=c["prec"], periodic=c["periodic"],
-                          mapping=c["mapping"], coeff=c["coeff"])
+                          mapping=c["mapping"], coeff=c["coeff"], basis=c.get("basis", "lagrange"))
         if c.get("face"):
             op.set_face_mode(c["face"])
         src = torch.tensor(dg_inputs.src_vector(op.n_dofs, 40 + i), dtype=op.dtype, device="cuda")

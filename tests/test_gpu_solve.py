@@ -151,3 +151,31 @@ def test_mixed_auto_picks_the_inner_arithmetic(n, mapping, expect):
     assert float((x - xr).norm() / xr.norm()) <= 1e-7
     for o in (o64, oe, o32):
         o.close()
+
+
+@pytest.mark.parametrize("geom,basis", [("positions", "lagrange"), ("full", "hermite")])
+def test_mixed_solvers_with_g2_and_hermite(geom, basis):
+    """The automatic mixed solver on G2 storage and on the Hermite-like basis
+    (the three operators of the solve share geometry and basis): FP64
+    residual below the target, solution equal to plain FP64 CG's."""
+    dgp.build()
+    n, p = (6, 5, 6), 3
+    kw = dict(geom=geom, mapping=1, coeff=1, basis=basis)
+    o64 = dgp.Operator(n, p, prec="fp64", **kw)
+    oe = dgp.Operator(n, p, prec="fp64emu", **kw)
+    o32 = dgp.Operator(n, p, prec="fp32", **kw)
+    rhs = o64.rhs(1)
+    xr, it, rr, st = o64.cg(rhs, rtol=1e-10, max_it=50000)
+    assert st == dgp.DG_OK
+    x = torch.zeros_like(rhs)
+    st, outer, inner, rel, kind = dgp.dg_cg_solve_mixed_auto(o64.handle, oe.handle, o32.handle, rhs.data_ptr(),
+                                                             x.data_ptr(), 1e-10)
+    assert st == dgp.DG_OK and rel <= 1e-10
+    assert float((x - xr).norm() / xr.norm()) <= 1e-6
+    other = dgp.Operator(n, p, prec="fp32", geom=geom, mapping=1, coeff=1,
+                         basis="hermite" if basis == "lagrange" else "lagrange")
+    with pytest.raises(dgp.DGError) as e:
+        dgp.dg_cg_solve_mixed(o64.handle, other.handle, rhs.data_ptr(), x.data_ptr(), 1e-10)
+    assert e.value.status == dgp.DG_ERR_ARG
+    for o in (o64, oe, o32, other):
+        o.close()
