@@ -962,6 +962,25 @@ def main():
                         "vs_g3": (total_ms / args.steps) / lg if prec == "fp64" else (l32 / lg)}
             og.close()
         extras["g2_positions"] = g2
+        # the Hermite-like basis (Sec. 3.1): the same operator in another
+        # basis; the binary32 kernel reads two layers of each neighbour instead
+        # of k (slim face access)
+        her = {}
+        for prec in ("fp64", "fp32"):
+            oh = dgp.Operator(mesh["n"], p, geom=w["geom"], op="sipg", prec=prec, coeff=w["coeff"], basis="hermite",
+                              **common)
+            if prec == "fp64" and loop:
+                oh.set_face_mode("loop")
+            sh = src if prec == "fp64" else src.float()
+            dh = torch.empty_like(sh)
+            for _ in range(args.warmup):
+                oh.apply(sh, dh)
+            _, lh = time_applies(torch, oh, sh, dh, args.steps)
+            ref_ms = (total_ms / args.steps) if prec == "fp64" else l32
+            her[prec] = {"value": n / (lh / 1e3), "unit": UNIT, "ms_per_step": lh,
+                         "vs_lagrange": ref_ms / lh, "face_mode": "loop" if prec == "fp64" and loop else "element"}
+            oh.close()
+        extras["hermite_basis"] = her
         # advection, FP64
         opa = dgp.Operator(mesh["n"], p, geom=w["geom"], op="advection", prec="fp64", **common)
         if loop:

@@ -306,6 +306,7 @@ dg::Tables<T> cast_tables(int k, const Tables64& t) {
       o.DF[s][i] = (T)t.DF[s][i];
     }
   for (int i = 0; i < k; ++i) o.W[i] = (T)t.gw[i];
+  o.slim = t.basis == DG_BASIS_HERMITE ? 1 : 0;
   // even-odd halves, from the FP64 tables
   const int h = k / 2, h2 = (k + 1) / 2;
   for (int m = 0; m < 4; ++m) {

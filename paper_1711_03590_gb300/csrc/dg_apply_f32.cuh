@@ -173,7 +173,14 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
   constexpr bool ASYNC_R = K >= 5;
   auto yz_chunk = [&](int j) -> float* { return j == 0 ? G0 : FB + (j - 1) * C * K3; };
   float wyz[EARLY && !STAGE_YZ ? 4 : 1][EARLY && !STAGE_YZ ? K : 1];
-  if constexpr (STAGE_YZ) {
+  // slim face access (a basis whose face value and normal derivative each
+  // come from one layer, Sec. 3.1): only layers edge and edge +- 1 of a
+  // neighbour's normal line are read; the others have zero weight in D_f
+  const bool slim = tb.slim != 0;
+  auto need = [&](int l, int s) -> bool {
+    return SIPG ? (!slim || l == (s ? 0 : K - 1) || l == (s ? 1 : K - 2)) : l == (s ? 0 : K - 1);
+  };
+  if (STAGE_YZ && !slim) {
     const int n0 = gm.n[0], n01 = gm.n[0] * gm.n[1];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -209,7 +216,7 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
       const float* pz = P.src + (size_t)nz[s] * K3 + a + K * b;
 #pragma unroll
       for (int l = 0; l < K; ++l) {
-        if (SIPG || l == (s ? 0 : K - 1)) {
+        if (need(l, s)) {
           wyz[s][l] = py[l * K];
           wyz[2 + s][l] = pz[l * K2];
         } else {
@@ -314,25 +321,25 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
       const int r = (nb >= 0 ? nb : cell) - cfirst;
       if (r >= 0 && r < C + 2) {
 #pragma unroll
-        for (int l = 0; l < K; ++l) w[l] = R[r * RS + off + l];
+        for (int l = 0; l < K; ++l) w[l] = need(l, s) ? R[r * RS + off + l] : 0.f;
       } else {
         const float* p = P.src + (size_t)nb * K3 + off;
 #pragma unroll
-        for (int l = 0; l < K; ++l) w[l] = p[l];
+        for (int l = 0; l < K; ++l) w[l] = need(l, s) ? p[l] : 0.f;
       }
     } else if constexpr (STAGE_YZ) {
       const int nstep = d == 1 ? gm.n[0] : gm.n[0] * gm.n[1];
-      if (nb == cell + (s ? nstep : -nstep)) {
+      if (!slim && nb == cell + (s ? nstep : -nstep)) {
         const float* p = yz_chunk(t - 2) + lc * K3 + off;
 #pragma unroll
         for (int l = 0; l < K; ++l) w[l] = p[l * str];
       } else if (nb >= 0) {
         const float* p = P.src + (size_t)nb * K3 + off;
 #pragma unroll
-        for (int l = 0; l < K; ++l) w[l] = p[l * str];
+        for (int l = 0; l < K; ++l) w[l] = need(l, s) ? p[l * str] : 0.f;
       } else {
 #pragma unroll
-        for (int l = 0; l < K; ++l) w[l] = R[(lc + 1) * RS + off + l * str];
+        for (int l = 0; l < K; ++l) w[l] = need(l, s) ? R[(lc + 1) * RS + off + l * str] : 0.f;
       }
     } else if constexpr (EARLY) {
 #pragma unroll
@@ -340,7 +347,7 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
     } else {
       const float* p = P.src + (size_t)(nb >= 0 ? nb : cell) * K3 + off;
 #pragma unroll
-      for (int l = 0; l < K; ++l) w[l] = (SIPG || l == (s ? 0 : K - 1)) ? p[l * str] : 0.f;
+      for (int l = 0; l < K; ++l) w[l] = need(l, s) ? p[l * str] : 0.f;
     }
     FA[(t * FSA + fpt) * C + lc] = s ? w[0] : w[K - 1];
     if (SIPG) {

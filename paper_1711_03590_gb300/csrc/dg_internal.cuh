@@ -40,6 +40,11 @@ struct Tables {
   //   MO[q][i] = (M[q][i] - M[q][k-1-i]) / 2 (i < h),
   // stored with row stride kHalf.
   T EO[4][2][kHalf * kHalf];
+  // 1 for a basis with one nonzero in S_f and in D_f per end (the
+  // Hermite-like basis: value from layer 0, normal derivative from layer 1,
+  // mirrored at xi = 1): kernels may then read only those two layers of a
+  // neighbour (the "slim" face access of Sec. 3.1)
+  int slim;
 };
 enum { EO_S = 0, EO_ST = 1, EO_D = 2, EO_DT = 3 };
 
