@@ -81,3 +81,29 @@ def test_hermite_needs_degree_three():
     with pytest.raises(dgp.DGError) as e:
         dgp.Operator((2, 2, 2), 2, geom="full", mapping=1, basis="hermite")
     assert e.value.status == dgp.DG_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hermite_full_size_sampled(prec):
+    """The 32^3 deformed p = 4 workload in the Hermite-like basis at full
+    size (binary32 with the slim neighbour access), on the corner cells and
+    a seeded sample, against the oracle's Hermite route."""
+    dgp.build()
+    w = dg_inputs.workload("deformed_dirichlet_32^3_p4")
+    mesh, p = w["mesh"], 4
+    nc, n = oracle.n_cells(mesh), oracle.n_dofs(mesh, p)
+    u = dg_inputs.src_vector(n, seed=19)
+    N = mesh["n"][0]
+    corners = [i + N * (j + N * k) for i in (0, N - 1) for j in (0, N - 1) for k in (0, N - 1)]
+    cells = dg_inputs.sample_cells(nc, 40, seed=5, must=corners)
+    form = dict(op="sipg", coeff=w["coeff"])
+    ref = oracle.apply(dict(mesh, basis="hermite"), p, form, u, cells=cells)
+    op = dgp.Operator(mesh["n"], p, geom="full", prec=prec, mapping=1, amplitude=0.1, coeff=w["coeff"],
+                      basis="hermite")
+    if prec == "fp64":
+        op.set_face_mode("loop")
+    got = op.apply(torch.tensor(u, dtype=op.dtype, device="cuda")).double().cpu().numpy()
+    op.close()
+    k3 = (p + 1) ** 3
+    idx = (cells[:, None] * k3 + np.arange(k3)[None, :]).ravel()
+    assert _rel(got[idx], ref[idx]) < TOL[prec]
