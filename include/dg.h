@@ -344,11 +344,13 @@ const char *dg_batch_last_error(void);
 /* Solve server (beyond the paper: serving with continuous batching).
  * A request is a Poisson problem -div(kappa grad u) = f with the
  * manufactured u = sin(pi x) sin(pi y) sin(pi z), Dirichlet boundary,
- * solved by dg_cg_solve_mixed on its own FP64/FP32 operators.  Requests are
+ * solved by dg_cg_solve_mixed_auto on its own FP64, emulated-FP64 (face
+ * loop) and FP32 operators.  Requests are
  * queued in arrival order; `slots` worker threads (one CUDA stream each)
- * admit the oldest request as soon as a slot is free and its estimated
- * device memory (dg_request_device_bytes) fits into the remaining budget, so
- * the work of all admitted requests overlaps on the device.  A result does
+ * admit a queued request (the oldest, or by dg_server_set_policy) as soon as
+ * a slot is free and its estimated device memory (dg_request_device_bytes)
+ * fits into the remaining budget, so the work of all admitted requests
+ * overlaps on the device.  A result does
  * not depend on the other requests (fixed-order reductions): it is the same
  * alone and in the mix, bit for bit.  Device memory comes from the
  * stream-ordered pool, which keeps freed memory for later requests. */
