@@ -344,8 +344,8 @@ const char *dg_batch_last_error(void);
 /* Solve server (beyond the paper: serving with continuous batching).
  * A request is a Poisson problem -div(kappa grad u) = f with the
  * manufactured u = sin(pi x) sin(pi y) sin(pi z), Dirichlet boundary,
- * solved by dg_cg_solve_mixed_auto on its own FP64, emulated-FP64 (face
- * loop) and FP32 operators.  Requests are
+ * solved by dg_cg_solve_mixed (binary32 inner CG) on its own FP64 and FP32
+ * operators.  Requests are
  * queued in arrival order; `slots` worker threads (one CUDA stream each)
  * admit a queued request (the oldest, or by dg_server_set_policy) as soon as
  * a slot is free and its estimated device memory (dg_request_device_bytes)
