@@ -186,6 +186,14 @@ MEASURED_TRAFFIC = {
 }
 
 
+# FP64-pipe warp instructions per apply (ncu sass__inst_executed_per_opcode:
+# DFMA + DADD + DMUL of both launches) of the same workload and launch
+# configuration; to be re-taken whenever the kernels change.
+MEASURED_FP64_WARP_INSTR = {
+    ("fp64", "loop", 4, 5): 18.560220e6,
+}
+
+
 def measured_traffic(prec, face_mode, degree, cpb, workload):
     if workload != "deformed_dirichlet_32^3_p%d" % degree:
         return None
@@ -855,15 +863,34 @@ def main():
            "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc, "kernel": kname,
            "bytes_per_dof": bpd, "algorithmic_bytes_per_launch": bpd * n, "peak_source": peaks.get("source")}
     if args.prec == "fp64":
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
-                    "frac": achieved_tf / alu["fp64_tflops"], "traffic": traffic, "traffic_source": tsrc,
+        # achieved: the algorithmic flops (the paper's counting method) per
+        # apply over its time; issue_slots: the kernels' own operation count
+        # with every FP64 instruction charged as an FMA; fp64_pipe: the FP64
+        # warp instructions ncu counted for this configuration against the
+        # measured FMA rate (how full the FP64 pipe is)
+        issue = {"flops_per_launch": flops, "achieved": achieved_tf, "frac": achieved_tf / alu["fp64_tflops"],
+                 "counting": "2 per FP64 arithmetic instruction of the kernels' operation count"}
+        winstr = MEASURED_FP64_WARP_INSTR.get((args.prec, "loop" if loop else "element", p,
+                                               op.info()["cells_per_block"])) if wname == \
+            "deformed_dirichlet_32^3_p%d" % p else None
+        pipe = None if winstr is None else {
+            "warp_instructions_per_launch": winstr,
+            "frac": winstr * 32 * 2 / (launch_ms / 1e3) / 1e12 / alu["fp64_tflops"],
+            "source": "ncu sass__inst_executed_per_opcode (DFMA + DADD + DMUL) of this launch configuration"}
+        if flops_alg is not None:
+            ach = flops_alg / (launch_ms / 1e3) / 1e12
+            top = {"achieved": ach, "frac": ach / alu["fp64_tflops"], "flops_per_launch": flops_alg,
+                   "flops_counting": "paper's method (Sec. 4.1): FMA 2, other add/mul 1, even-odd sweeps"}
+        else:
+            top = {"achieved": achieved_tf, "frac": achieved_tf / alu["fp64_tflops"], "flops_per_launch": flops,
+                   "flops_counting": issue["counting"]}
+        roofline = {"bound": "alu", "achieved": top["achieved"], "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                    "frac": top["frac"], "traffic": traffic, "traffic_source": tsrc,
                     "kernel": kname,
-                    "flops_per_launch": flops,
-                    "flops_counting": "2 per FP64 arithmetic instruction (issue-slot count)",
-                    "algorithmic": None if flops_alg is None else {
-                        "flops_per_launch": flops_alg, "achieved": flops_alg / (launch_ms / 1e3) / 1e12,
-                        "frac": flops_alg / (launch_ms / 1e3) / 1e12 / alu["fp64_tflops"],
-                        "counting": "paper's method (Sec. 4.1): FMA 2, other add/mul 1, even-odd sweeps"},
+                    "flops_per_launch": top["flops_per_launch"],
+                    "flops_counting": top["flops_counting"],
+                    "issue_slots": issue,
+                    "fp64_pipe": pipe,
                     "peak_source": alu["fp64_tflops_source"],
                     "peak_derived": FP64_PEAK_TFLOPS,
                     "hbm": hbm}
