@@ -370,7 +370,7 @@ struct dg_handle {
   int face_mode;
   dg::SplitArrays split;
   const double* skip;     // device flag handed to the apply launches (null: never skip)
-  cudaStream_t h2d_stream, d2h_stream, cmp_stream;
+  cudaStream_t h2d_stream, d2h_stream, cmp_stream, bwd_stream[2];
   cudaEvent_t pipe_ev[3 * kHostSlabs + 2];
   std::string err;
 };
@@ -1287,6 +1287,8 @@ void free_handle(dg_handle* h) {
   if (h->h2d_stream) cudaStreamDestroy(h->h2d_stream);
   if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
   if (h->cmp_stream) cudaStreamDestroy(h->cmp_stream);
+  for (cudaStream_t bs : h->bwd_stream)
+    if (bs) cudaStreamDestroy(bs);
   for (auto e : h->pipe_ev)
     if (e) cudaEventDestroy(e);
   if (h->cg_event) cudaEventDestroy(h->cg_event);
@@ -1667,6 +1669,7 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
     DG_CUDA(h, cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking));
     DG_CUDA(h, cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
     DG_CUDA(h, cudaStreamCreateWithFlags(&h->cmp_stream, cudaStreamNonBlocking));
+    for (cudaStream_t& bs : h->bwd_stream) DG_CUDA(h, cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
     for (auto& e : h->pipe_ev) DG_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   const int64_t plane = (int64_t)h->mesh.n[0] * h->mesh.n[1];
@@ -1692,6 +1695,7 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
   DG_CUDA(h, cudaStreamWaitEvent(h->h2d_stream, ev_start, 0));
   DG_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, ev_start, 0));
   DG_CUDA(h, cudaStreamWaitEvent(h->cmp_stream, ev_start, 0));
+  for (cudaStream_t bs : h->bwd_stream) DG_CUDA(h, cudaStreamWaitEvent(bs, ev_start, 0));
   for (int s = 0; s < slabs; ++s) {
     const int64_t c0 = cell_of_slab(s), c1 = cell_of_slab(s + 1);
     const size_t off = (size_t)(c0 * k3) * scal, len = (size_t)((c1 - c0) * k3) * scal;
@@ -1700,31 +1704,42 @@ dg_status dg_apply_host(dg_handle* h, const void* src_host, void* dst_host) {
     DG_CUDA(h, cudaEventRecord(ev_in[s], h->h2d_stream));
   }
   if (h->face_mode == DG_FACE_LOOP) {
-    // face loop: forward launches on the handle's stream as the slabs
-    // arrive; slab s's backward launch, on the second compute stream, once
-    // the forward launch of slab s + 1 (which writes the upper neighbours'
-    // traces) is done; a backward launch overlaps the next forward launch
+    // face loop: the forward launch of slab s as soon as it has arrived, the
+    // backward launch of slab s once the forward launches of slabs s - 1, s
+    // and s + 1 (which write the traces of its z-neighbours) are done.
+    // Forward launches alternate between two streams and backward launches
+    // between two more, so that consecutive slabs overlap: a slab of few
+    // planes does not fill the GPU, and the pipeline's fill (the first
+    // slab's forward launch) and drain (the last slab's backward launch)
+    // then run beside their neighbours' launches instead of alone.
     cudaEvent_t* ev_fwd = h->pipe_ev + 2 * kHostSlabs + 2;
+    cudaStream_t fs[2] = {h->stream, h->cmp_stream};
     for (int s = 0; s < slabs; ++s) {
-      DG_CUDA(h, cudaStreamWaitEvent(h->stream, ev_in[s], 0));
-      if ((st = launch_apply_range(h, h->stage_src, h->stage_dst, nullptr, cell_of_slab(s), cell_of_slab(s + 1),
-                                   h->stream, 1)) != DG_OK)
+      cudaStream_t f = fs[s % 2];
+      DG_CUDA(h, cudaStreamWaitEvent(f, ev_in[s], 0));
+      if ((st = launch_apply_range(h, h->stage_src, h->stage_dst, nullptr, cell_of_slab(s), cell_of_slab(s + 1), f,
+                                   1)) != DG_OK)
         return st;
-      DG_CUDA(h, cudaEventRecord(ev_fwd[s], h->stream));
+      DG_CUDA(h, cudaEventRecord(ev_fwd[s], f));
     }
     for (int s = 0; s < slabs; ++s) {
       const int64_t c0 = cell_of_slab(s), c1 = cell_of_slab(s + 1);
-      DG_CUDA(h, cudaStreamWaitEvent(h->cmp_stream, ev_fwd[std::min(s + 1, slabs - 1)], 0));
-      if ((st = launch_apply_range(h, h->stage_src, h->stage_dst, nullptr, c0, c1, h->cmp_stream, 2)) != DG_OK)
-        return st;
-      DG_CUDA(h, cudaEventRecord(ev_out[s], h->cmp_stream));
+      cudaStream_t bs = h->bwd_stream[s % 2];
+      for (int n = std::max(s - 1, 0); n <= std::min(s + 1, slabs - 1); ++n)
+        DG_CUDA(h, cudaStreamWaitEvent(bs, ev_fwd[n], 0));
+      if ((st = launch_apply_range(h, h->stage_src, h->stage_dst, nullptr, c0, c1, bs, 2)) != DG_OK) return st;
+      DG_CUDA(h, cudaEventRecord(ev_out[s], bs));
       DG_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, ev_out[s], 0));
       const size_t off = (size_t)(c0 * k3) * scal, len = (size_t)((c1 - c0) * k3) * scal;
       DG_CUDA(h, cudaMemcpyAsync(static_cast<char*>(dst_host) + off, static_cast<const char*>(h->stage_dst) + off,
                                  len, cudaMemcpyDeviceToHost, h->d2h_stream));
     }
-    DG_CUDA(h, cudaEventRecord(ev_cmp, h->cmp_stream));
-    DG_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cmp, 0));
+    // join the compute streams into the handle's stream (later work and the
+    // next call's staging reuse follow it)
+    for (cudaStream_t js : {h->cmp_stream, h->bwd_stream[0], h->bwd_stream[1]}) {
+      DG_CUDA(h, cudaEventRecord(ev_cmp, js));
+      DG_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cmp, 0));
+    }
     DG_CUDA(h, cudaStreamSynchronize(h->d2h_stream));
     DG_CUDA(h, cudaStreamSynchronize(h->stream));
     return DG_OK;

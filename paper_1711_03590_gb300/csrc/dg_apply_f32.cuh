@@ -238,12 +238,26 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
     const unsigned lo = cfirst < 0 ? K3 : 0u;  // cell -1 does not exist
     const int rem = ncell - cfirst;            // cells from cfirst to the end of the mesh
     const unsigned hi = (unsigned)(rem < C + 2 ? rem : C + 2) * K3;
+    if (lo == 0 && hi == (unsigned)NR) {  // whole range inside the mesh (block-uniform)
 #pragma unroll
-    for (int r = 0; r < (NR + NT - 1) / NT; ++r) {
-      const unsigned e = tid + r * NT;
-      if (e >= lo && e < hi) {
+      for (int r = 0; r < NR / NT; ++r) {
+        const unsigned e = tid + r * NT;
         if constexpr (ASYNC_R) f32_cp_async4(R + e, P.src + base + e);
         else R[e] = P.src[base + e];
+      }
+      if (NR % NT != 0 && tid < NR % NT) {
+        const unsigned e = tid + (NR / NT) * NT;
+        if constexpr (ASYNC_R) f32_cp_async4(R + e, P.src + base + e);
+        else R[e] = P.src[base + e];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < (NR + NT - 1) / NT; ++r) {
+        const unsigned e = tid + r * NT;
+        if (e >= lo && e < hi) {
+          if constexpr (ASYNC_R) f32_cp_async4(R + e, P.src + base + e);
+          else R[e] = P.src[base + e];
+        }
       }
     }
   }
