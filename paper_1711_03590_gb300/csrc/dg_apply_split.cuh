@@ -467,19 +467,28 @@ __device__ __forceinline__ void split_backward_body(const Tables<T>& tb, const P
       const T* fz0 = ftc + (2 * 2 + 0) * NFT * K2 + la + K * lb;
       const T* fz1 = ftc + (2 * 2 + 1) * NFT * K2 + la + K * lb;
       const T ez0 = mE0[z], ez1 = mE1[z];
-      auto inj = [&](int f) {
-        T a = e0a * fx0[f * K2];
+      // the six faces' coefficients of field f extrapolated to the point
+      // (E_s along each direction), accumulated onto a
+      auto inj = [&](int f, T a) {
+        a = fma(e0a, fx0[f * K2], a);
         a = fma(e1a, fx1[f * K2], a);
         a = fma(e0b, fy0[f * K2], a);
         a = fma(e1b, fy1[f * K2], a);
         a = fma(ez0, fz0[f * K2], a);
         return fma(ez1, fz1[f * K2], a);
       };
-      Uc[pt] = inj(0);
+      {
+        T a = e0a * fx0[0];
+        a = fma(e1a, fx1[0], a);
+        a = fma(e0b, fy0[0], a);
+        a = fma(e1b, fy1[0], a);
+        a = fma(ez0, fz0[0], a);
+        Uc[pt] = fma(ez1, fz1[0], a);
+      }
       if (OP == OP_SIPG) {
-        G0[pt] += inj(1);
-        G1[pt] += inj(2);
-        G2[pt] += inj(3);
+        G0[pt] = inj(1, G0[pt]);
+        G1[pt] = inj(2, G1[pt]);
+        G2[pt] = inj(3, G2[pt]);
       }
     }
   }
