@@ -176,6 +176,10 @@ struct Tables64 {
   int basis;  // DG_BASIS_LAGRANGE or DG_BASIS_HERMITE
   double gq[kMaxK], gw[kMaxK], gl[kMaxK];
   double S[kMaxK * kMaxK], D[kMaxK * kMaxK], DS[kMaxK * kMaxK], E[2][kMaxK], DF[2][kMaxK];
+  // the basis values at t = 0 and t = 1 are the unit vectors e_0 and e_p
+  // (the face value is the end layer's coefficient: the face loop's forward
+  // launch relies on it for the x faces)
+  bool end_nodal;
 };
 
 // Hermite-like basis of degree p = k - 1 >= 3 on the Gauss-Lobatto points
@@ -285,9 +289,13 @@ void build_tables(int k, Tables64& t, int basis) {
     }
   bary_values(k, t.gq, lg, 0.0, t.E[0]);
   bary_values(k, t.gq, lg, 1.0, t.E[1]);
-  double v[kMaxK];
-  basis_values(t, k, 0.0, v, t.DF[0]);
-  basis_values(t, k, 1.0, v, t.DF[1]);
+  double v0[kMaxK], v1[kMaxK];
+  basis_values(t, k, 0.0, v0, t.DF[0]);
+  basis_values(t, k, 1.0, v1, t.DF[1]);
+  t.end_nodal = true;
+  for (int i = 0; i < k; ++i)
+    t.end_nodal = t.end_nodal && std::fabs(v0[i] - (i == 0 ? 1.0 : 0.0)) <= 1e-13 &&
+                  std::fabs(v1[i] - (i == k - 1 ? 1.0 : 0.0)) <= 1e-13;
   (void)ll;
 }
 
@@ -2122,6 +2130,8 @@ dg_status dg_set_face_mode(dg_handle* h, int mode) {
   if (mode != DG_FACE_ELEMENT && mode != DG_FACE_LOOP) return fail(h, DG_ERR_ARG, "unknown face mode");
   if (mode == DG_FACE_LOOP && h->prec == DG_FP32)
     return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply is implemented for DG_FP64 and DG_FP64_EMU");
+  if (mode == DG_FACE_LOOP && !h->t64.end_nodal)
+    return fail(h, DG_ERR_UNSUPPORTED, "the face-loop apply needs a basis whose face values are its end layers");
   if (mode == DG_FACE_ELEMENT && h->geom == DG_GEOM_POSITIONS && h->prec != DG_FP32)
     return fail(h, DG_ERR_UNSUPPORTED, "G2 (positions) binary64 and double-float operators run the face loop only");
   if (mode == DG_FACE_LOOP && !h->split.tq) {

@@ -142,11 +142,21 @@ __device__ __forceinline__ void split_forward_body(const Tables<T>& tb, const PP
     if constexpr (kEO) eo_derivative_to<K>(tb, Uc, base, stride, out, base, stride);
     else line_apply_to<K, kUq>(mD, Uc, base, stride, out, base, stride);
   };
-  if (active) sweep_S(K * (la + K * lb), 1);
+  // S along z, y, then x: before the x sweep the x-line (y = la, z = lb)
+  // holds the coefficients along x at the Gauss points in y and z, and its
+  // end layers are the cell's x-face traces of u at face point (la, lb)
+  // (both bases take the face value from the end layer alone: Lagrange on
+  // Gauss-Lobatto points, and the Hermite-like basis by construction)
+  T xu[2] = {T(0), T(0)};
+  if (active) sweep_S(la + K * lb, K2);
   __syncthreads();
   if (active) sweep_S(la + K2 * lb, K);
   __syncthreads();
-  if (active) sweep_S(la + K * lb, K2);
+  if (active) {
+    xu[0] = Uc[K * (la + K * lb)];
+    xu[1] = Uc[K * (la + K * lb) + K - 1];
+    sweep_S(K * (la + K * lb), 1);
+  }
   __syncthreads();
   if (OP == OP_SIPG) {
     if (active) {
@@ -182,12 +192,13 @@ __device__ __forceinline__ void split_forward_body(const Tables<T>& tb, const PP
 #pragma unroll
       for (int j = 0; j < K; ++j) {
         const T e = s ? mE1[j] : mE0[j];
-        v[0] = fma(e, lu[j], v[0]);
+        if (d != 0) v[0] = fma(e, lu[j], v[0]);
         if (OP == OP_SIPG) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) v[1 + c] = fma(e, lg[c][j], v[1 + c]);
         }
       }
+      if (d == 0) v[0] = xu[s];
       const int fid = split_face_id(ijk, d, s, gm.n, gm.P, gm.periodic);
       T* out = (d == 0 ? tr_out[0] : d == 1 ? tr_out[1] : tr_out[2]) + ((int64_t)(fid * 2 + (1 - s)) * NTR) * K2 + ln;
 #pragma unroll
