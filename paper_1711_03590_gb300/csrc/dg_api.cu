@@ -317,10 +317,13 @@ dg::Tables<T> cast_tables(int k, const Tables64& t) {
   o.slim = t.basis == DG_BASIS_HERMITE ? 1 : 0;
   // even-odd halves, from the FP64 tables
   const int h = k / 2, h2 = (k + 1) / 2;
-  for (int m = 0; m < 4; ++m) {
+  for (int m = 0; m < 5; ++m) {
     auto M = [&](int q, int i) {
-      return m == dg::EO_S ? t.S[q * k + i] : m == dg::EO_ST ? t.S[i * k + q] : m == dg::EO_D ? t.D[q * k + i]
-                                                                                               : t.D[i * k + q];
+      return m == dg::EO_S    ? t.S[q * k + i]
+             : m == dg::EO_ST ? t.S[i * k + q]
+             : m == dg::EO_D  ? t.D[q * k + i]
+             : m == dg::EO_DT ? t.D[i * k + q]
+                              : t.DS[q * k + i];
     };
     for (int q = 0; q < h2; ++q) {
       for (int i = 0; i < h; ++i) {

@@ -242,17 +242,25 @@ __device__ __forceinline__ void line_add_transposed(const T* __restrict__ M, con
 // centrosymmetric (ANTI = false: S, S^T) or anti-centrosymmetric (ANTI =
 // true: D, D^T) k x k matrix from its even and odd halves ME, MO (see
 // Tables::EO): about k^2/2 + 2k operations instead of k^2.
-template <int K, bool ANTI, typename T>
-__device__ __forceinline__ void eo_line(const T* __restrict__ ME, const T* __restrict__ MO, const T (&in)[K],
-                                        T (&out)[K]) {
-  constexpr int h = K / 2, H2 = (K + 1) / 2;
-  T e[H2], o[h];
+// Even-odd split of a line (Sec. 4.1): e_i = u_i + u_{k-1-i}, o_i = u_i -
+// u_{k-1-i} for i < k/2, and e_{k/2} = u_{k/2} for odd k.
+template <int K, typename T>
+__device__ __forceinline__ void eo_split(const T (&in)[K], T (&e)[(K + 1) / 2], T (&o)[K / 2]) {
+  constexpr int h = K / 2;
 #pragma unroll
   for (int i = 0; i < h; ++i) {
     e[i] = in[i] + in[K - 1 - i];
     o[i] = in[i] - in[K - 1 - i];
   }
   if (K % 2) e[h] = in[h];
+}
+
+// out = M in from the split line, M centrosymmetric (ANTI false) or
+// anti-centrosymmetric (ANTI true) with even-odd halves ME, MO.
+template <int K, bool ANTI, typename T>
+__device__ __forceinline__ void eo_combine(const T* __restrict__ ME, const T* __restrict__ MO,
+                                           const T (&e)[(K + 1) / 2], const T (&o)[K / 2], T (&out)[K]) {
+  constexpr int h = K / 2, H2 = (K + 1) / 2;
 #pragma unroll
   for (int q = 0; q < h; ++q) {
     T ev = ME[q * kHalf] * e[0];
@@ -277,6 +285,14 @@ __device__ __forceinline__ void eo_line(const T* __restrict__ ME, const T* __res
     }
     out[h] = mid;
   }
+}
+
+template <int K, bool ANTI, typename T>
+__device__ __forceinline__ void eo_line(const T* __restrict__ ME, const T* __restrict__ MO, const T (&in)[K],
+                                        T (&out)[K]) {
+  T e[(K + 1) / 2], o[K / 2];
+  eo_split<K>(in, e, o);
+  eo_combine<K, ANTI>(ME, MO, e, o, out);
 }
 
 // The sweeps of the binary64 kernel in even-odd form (k >= 5, where it saves

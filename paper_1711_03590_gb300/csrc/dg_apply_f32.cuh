@@ -78,6 +78,28 @@ __device__ __forceinline__ void f32_cp_async4(float* s, const float* g) {
 }
 __device__ __forceinline__ void f32_cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// One 1D sweep of a line in binary32, out = M in with M = S, D or S^T
+// (WHICH = EO_S, EO_D, EO_ST): from k = 5 on in the even-odd form of Sec.
+// 4.1 (k = 5: 21 instead of 25 operations; the kernel is bound by its
+// instruction count), below it directly.
+template <int K, int WHICH>
+__device__ __forceinline__ void f32_line(const Tables<float>& tb, const float (&in)[K], float (&out)[K]) {
+  if constexpr (K >= 5) {
+    eo_line<K, WHICH == EO_D>(tb.EO[WHICH][0], tb.EO[WHICH][1], in, out);
+  } else {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const float m = WHICH == EO_S ? tb.S[q * K + j] : WHICH == EO_D ? tb.D[q * K + j] : tb.S[j * K + q];
+        acc = fmaf(m, in[j], acc);
+      }
+      out[q] = acc;
+    }
+  }
+}
+
 // Resident blocks per SM the register allocation is sized for: about 900
 // threads per SM up to k = 8 (72-80 registers without spills; at k = 7, 8
 // 7-13% faster than the 700 that the longer lines of k = 9 keep, which
@@ -374,27 +396,22 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
     if (K >= 7 && s == 1) __syncwarp();
   }
   // S along z
+  {
+    float o[K];
+    f32_line<K, EO_S>(tb, v, o);
 #pragma unroll
-  for (int q = 0; q < K; ++q) {
-    float acc = 0.f;
-#pragma unroll
-    for (int j = 0; j < K; ++j) acc = fmaf(tb.S[q * K + j], v[j], acc);
-    U[(a + XS * b + YS * q) * C + lc] = acc;
+    for (int q = 0; q < K; ++q) U[(a + XS * b + YS * q) * C + lc] = o[q];
   }
   __syncthreads();
 
   // 2. S along y; first in-face sweep (along t1) of the neighbour data
   {
-    float w[K];
+    float w[K], o[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) w[j] = U[(a + XS * j + YS * b) * C + lc];
+    f32_line<K, EO_S>(tb, w, o);
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[q * K + j], w[j], acc);
-      U[(a + XS * q + YS * b) * C + lc] = acc;
-    }
+    for (int q = 0; q < K; ++q) U[(a + XS * q + YS * b) * C + lc] = o[q];
   }
   {
     constexpr int NTASK = 6 * K * C, ROUNDS = (NTASK + NT - 1) / NT;
@@ -412,18 +429,33 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
           xv[i] = in[i * C];
           if (SIPG) xn[i] = in[(KK + i) * C];
         }
+        if constexpr (K >= 5) {
+          // even-odd form, the split of xv shared by S and DS
+          float e[(K + 1) / 2], o[K / 2], s0[K], s1[K], s2[K];
+          eo_split<K>(xv, e, o);
+          eo_combine<K, false>(tb.EO[EO_S][0], tb.EO[EO_S][1], e, o, s0);
+          if (TANG) eo_combine<K, true>(tb.EO[EO_DS][0], tb.EO[EO_DS][1], e, o, s1);
+          if (SIPG) eo_line<K, false>(tb.EO[EO_S][0], tb.EO[EO_S][1], xn, s2);
 #pragma unroll
-        for (int qa = 0; qa < K; ++qa) {
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-          for (int i = 0; i < K; ++i) {
-            s0 = fmaf(tb.S[qa * K + i], xv[i], s0);
-            if (TANG) s1 = fmaf(tb.DS[qa * K + i], xv[i], s1);
-            if (SIPG) s2 = fmaf(tb.S[qa * K + i], xn[i], s2);
+          for (int qa = 0; qa < K; ++qa) {
+            out[qa * C] = s0[qa];
+            if (TANG) out[(KK + qa) * C] = s1[qa];
+            if (SIPG) out[((NBB - 1) * KK + qa) * C] = s2[qa];
           }
-          out[qa * C] = s0;
-          if (TANG) out[(KK + qa) * C] = s1;
-          if (SIPG) out[((NBB - 1) * KK + qa) * C] = s2;
+        } else {
+#pragma unroll
+          for (int qa = 0; qa < K; ++qa) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+              s0 = fmaf(tb.S[qa * K + i], xv[i], s0);
+              if (TANG) s1 = fmaf(tb.DS[qa * K + i], xv[i], s1);
+              if (SIPG) s2 = fmaf(tb.S[qa * K + i], xn[i], s2);
+            }
+            out[qa * C] = s0;
+            if (TANG) out[(KK + qa) * C] = s1;
+            if (SIPG) out[((NBB - 1) * KK + qa) * C] = s2;
+          }
         }
       }
     }
@@ -438,22 +470,13 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
     float w[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) w[j] = U[(j + XS * a + YS * b) * C + lc];
+    f32_line<K, EO_S>(tb, w, ux);
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[q * K + j], w[j], acc);
-      ux[q] = acc;
-      U[(q + XS * a + YS * b) * C + lc] = acc;
-    }
+    for (int q = 0; q < K; ++q) U[(q + XS * a + YS * b) * C + lc] = ux[q];
     if (SIPG) {
+      f32_line<K, EO_D>(tb, ux, w);
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        float acc = 0.f;
-#pragma unroll
-        for (int j = 0; j < K; ++j) acc = fmaf(tb.D[q * K + j], ux[j], acc);
-        G0[(q + XS * a + YS * b) * C + lc] = acc;
-      }
+      for (int q = 0; q < K; ++q) G0[(q + XS * a + YS * b) * C + lc] = w[q];
     }
   }
   {
@@ -477,18 +500,40 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
         const float* fg = nullptr;
         if (TANG) fg = face_at(d, FID[t * C + tc]) + qa * FBW;
         const float cj = CART && SIPG ? (s ? 1.f : -1.f) * gm.cart_jinv[d] : 0.f;
+        // u, dt2 = (S, DS) sv, dt1 = S dsv, dn = S sn at the K points qb
+        float uo[K], d2o[K], d1o[K], dno[K];
+        if constexpr (K >= 5) {
+          float e[(K + 1) / 2], o[K / 2];
+          eo_split<K>(sv, e, o);
+          eo_combine<K, false>(tb.EO[EO_S][0], tb.EO[EO_S][1], e, o, uo);
+          if (TANG) {
+            eo_combine<K, true>(tb.EO[EO_DS][0], tb.EO[EO_DS][1], e, o, d2o);
+            eo_line<K, false>(tb.EO[EO_S][0], tb.EO[EO_S][1], dsv, d1o);
+          }
+          if (SIPG) eo_line<K, false>(tb.EO[EO_S][0], tb.EO[EO_S][1], sn, dno);
+        } else {
+#pragma unroll
+          for (int qb = 0; qb < K; ++qb) {
+            float u = 0.f, dt2 = 0.f, dt1 = 0.f, dn = 0.f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              u = fmaf(tb.S[qb * K + j], sv[j], u);
+              if (TANG) {
+                dt2 = fmaf(tb.DS[qb * K + j], sv[j], dt2);
+                dt1 = fmaf(tb.S[qb * K + j], dsv[j], dt1);
+              }
+              if (SIPG) dn = fmaf(tb.S[qb * K + j], sn[j], dn);
+            }
+            uo[qb] = u;
+            d2o[qb] = dt2;
+            d1o[qb] = dt1;
+            dno[qb] = dn;
+          }
+        }
 #pragma unroll
         for (int qb = 0; qb < K; ++qb) {
-          float u = 0.f, dt2 = 0.f, dt1 = 0.f, dn = 0.f;
-#pragma unroll
-          for (int j = 0; j < K; ++j) {
-            u = fmaf(tb.S[qb * K + j], sv[j], u);
-            if (TANG) {
-              dt2 = fmaf(tb.DS[qb * K + j], sv[j], dt2);
-              dt1 = fmaf(tb.S[qb * K + j], dsv[j], dt1);
-            }
-            if (SIPG) dn = fmaf(tb.S[qb * K + j], sn[j], dn);
-          }
+          const float u = uo[qb], dt2 = TANG ? d2o[qb] : 0.f, dt1 = TANG ? d1o[qb] : 0.f,
+                      dn = SIPG ? dno[qb] : 0.f;
           out[qb * KP * C] = u;
           if (SIPG) {
             float wn;
@@ -517,22 +562,18 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
 
   // 4. D along y and z
   if (SIPG) {
-    float uy[K], uz[K];
+    float uy[K], uz[K], s1[K], s2[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       uy[j] = U[(a + XS * j + YS * b) * C + lc];
       uz[j] = U[(a + XS * b + YS * j) * C + lc];
     }
+    f32_line<K, EO_D>(tb, uy, s1);
+    f32_line<K, EO_D>(tb, uz, s2);
 #pragma unroll
     for (int q = 0; q < K; ++q) {
-      float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        s1 = fmaf(tb.D[q * K + j], uy[j], s1);
-        s2 = fmaf(tb.D[q * K + j], uz[j], s2);
-      }
-      G1[(a + XS * q + YS * b) * C + lc] = s1;
-      G2[(a + XS * b + YS * q) * C + lc] = s2;
+      G1[(a + XS * q + YS * b) * C + lc] = s1[q];
+      G2[(a + XS * b + YS * q) * C + lc] = s2[q];
     }
     __syncthreads();
   }
@@ -948,28 +989,21 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
       for (int j = 0; j < K; ++j) acc = fmaf(tb.D[j * K + i], t0[j], acc);
       w[i] = acc;
     }
+    float o[K];
+    f32_line<K, EO_ST>(tb, w, o);
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[j * K + i], w[j], acc);
-      U[(i + XS * a + YS * b) * C + lc] = acc;
-    }
+    for (int i = 0; i < K; ++i) U[(i + XS * a + YS * b) * C + lc] = o[i];
   }
   __syncthreads();
 
   // 9. S_y^T
   {
-    float w[K];
+    float w[K], o[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) w[j] = U[(a + XS * j + YS * b) * C + lc];
+    f32_line<K, EO_ST>(tb, w, o);
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[j * K + i], w[j], acc);
-      U[(a + XS * i + YS * b) * C + lc] = acc;
-    }
+    for (int i = 0; i < K; ++i) U[(a + XS * i + YS * b) * C + lc] = o[i];
   }
   __syncthreads();
 
@@ -981,14 +1015,10 @@ __device__ __forceinline__ void f32_body(const Tables<float>& tb, const PP& P, c
     float* o = P.dst + (size_t)cell * K3 + a + K * b;
     const float* s = P.src + (size_t)cell * K3 + a + K * b;
     float r[K];
+    f32_line<K, EO_ST>(tb, w, r);
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc = fmaf(tb.S[j * K + i], w[j], acc);
-      r[i] = acc;
-      if (valid) o[K2 * i] = acc;
-    }
+    for (int i = 0; i < K; ++i)
+      if (valid) o[K2 * i] = r[i];
     if (P.dot_partial) {
       double acc = 0.0;
 #pragma unroll

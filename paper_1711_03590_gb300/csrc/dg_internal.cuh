@@ -31,22 +31,23 @@ struct Tables {
   T E[2][kMaxK];        // E[s][j]   = l^G_j(s), Gauss-collocation value at xi = s
   T DF[2][kMaxK];       // DF[s][i]  = (l^GL_i)'(s), GL derivative at xi = s
   T W[kMaxK];           // Gauss weights on [0,1]
-  // Even-odd halves of S, S^T, D, D^T (index EO_S, EO_ST, EO_D, EO_DT) for
-  // the 1D kernels of Sec. 4.1: S is centrosymmetric (M[q][i] =
-  // M[k-1-q][k-1-i]) and D anti-centrosymmetric (M[q][i] = -M[k-1-q][k-1-i]),
+  // Even-odd halves of S, S^T, D, D^T and DS (index EO_S, EO_ST, EO_D,
+  // EO_DT, EO_DS) for the 1D kernels of Sec. 4.1: S is centrosymmetric
+  // (M[q][i] = M[k-1-q][k-1-i]) and D and DS anti-centrosymmetric
+  // (M[q][i] = -M[k-1-q][k-1-i]),
   // so with h = k/2, rows q < (k+1)/2 and e_i = u_i + u_{k-1-i},
   // o_i = u_i - u_{k-1-i} (i < h; e_h = u_h for odd k):
   //   ME[q][i] = (M[q][i] + M[q][k-1-i]) / 2 (i < h), ME[q][h] = M[q][h],
   //   MO[q][i] = (M[q][i] - M[q][k-1-i]) / 2 (i < h),
   // stored with row stride kHalf.
-  T EO[4][2][kHalf * kHalf];
+  T EO[5][2][kHalf * kHalf];
   // 1 for a basis with one nonzero in S_f and in D_f per end (the
   // Hermite-like basis: value from layer 0, normal derivative from layer 1,
   // mirrored at xi = 1): kernels may then read only those two layers of a
   // neighbour (the "slim" face access of Sec. 3.1)
   int slim;
 };
-enum { EO_S = 0, EO_ST = 1, EO_D = 2, EO_DT = 3 };
+enum { EO_S = 0, EO_ST = 1, EO_D = 2, EO_DT = 3, EO_DS = 4 };
 
 // Device geometry and mesh description used by the apply kernel.
 template <typename T>
