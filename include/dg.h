@@ -201,7 +201,10 @@ dg_status dg_set_cells_per_block(dg_handle *h, int cells_per_block);
  * stay with the handle until dg_destroy): 24/k + 3 doubles per dof for SIPG
  * (62 bytes per dof at p = 4), 6/k + 3 for advection.  DG_ERR_OOM if they do
  * not fit (the mode is then unchanged).
- * DG_FP64 and DG_FP64_EMU handles; DG_FP32: DG_ERR_UNSUPPORTED.  A tile
+ * DG_FP64 and DG_FP64_EMU handles; DG_FP32: DG_ERR_UNSUPPORTED.  The face
+ * loop takes the x faces' values from the end layers of the x lines, so it
+ * needs a basis whose value at each end of the interval is its end
+ * coefficient (both bases here are; another basis: DG_ERR_UNSUPPORTED).  A tile
  * shape equal to the previous mode's default moves to the new mode's
  * default; any other stays.  Synchronous. */
 typedef enum { DG_FACE_ELEMENT = 0, DG_FACE_LOOP = 1 } dg_face_mode;
