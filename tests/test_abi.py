@@ -55,3 +55,34 @@ def test_setup_errors_without_gpu_are_status_codes():
     with pytest.raises(dgp.DGError) as e:
         dgp.dg_setup(m, 2, 1, dgp.make_opts())  # 1: no geometry variant (no per-cell affine storage)
     assert e.value.status == dgp.DG_ERR_ARG
+
+
+@pytest.mark.parametrize("case", [
+    dict(n=(0, 4, 4)),                    # no cells along x
+    dict(n=(4, 4, -1)),                   # negative extent
+    dict(n=(1 << 21, 1, 1)),              # beyond 2^20 cells per direction
+    dict(n=(1 << 20, 1 << 20, 1)),        # more than 2^31 - 1 cells
+    dict(degree=0),
+    dict(degree=-3),
+    dict(mapping=3),
+    dict(op=5),
+    dict(prec=7),
+    dict(coeff=2),
+    dict(basis=3),
+    dict(basis="hermite", degree=2),      # the Hermite-like basis needs degree >= 3
+    dict(geom=9),
+    dict(geom="cartesian", mapping=1),    # Cartesian storage on a curved mesh
+    dict(mapping=2, periodic=True, coeff=1),  # kappa(x) not periodic on the sheared mesh
+])
+def test_degenerate_and_out_of_range_setup_arguments(case):
+    """Empty meshes, out-of-range sizes and degrees and unknown enum values
+    are rejected with DG_ERR_ARG before any device work (no GPU needed)."""
+    import paper_1711_03590_gb300 as dgp
+    dgp.build()
+    m = dgp.make_mesh(case.get("n", (4, 4, 4)), periodic=case.get("periodic", False),
+                      mapping=case.get("mapping", 1))
+    o = dgp.make_opts(op=case.get("op", "sipg"), prec=case.get("prec", "fp64"), coeff=case.get("coeff", 0),
+                      basis=case.get("basis", "lagrange"))
+    with pytest.raises(dgp.DGError) as e:
+        dgp.dg_setup(m, case.get("degree", 2), case.get("geom", "full"), o)
+    assert e.value.status == dgp.DG_ERR_ARG
