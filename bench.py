@@ -667,7 +667,10 @@ def fp32_degree_sweep(torch, dgp, steps=20, degrees=(2, 3, 4, 5, 6)):
         rows.append({"p": p, "mesh": "%d^3" % n, "dofs": o.n_dofs, "us": round(ms * 1e3, 2),
                      "gdofs_per_s": round(o.n_dofs / (ms / 1e3) / 1e9, 3), "bytes_per_dof": round(bpd, 2),
                      "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-                     "hbm_frac_survey_bytes": round((8 + 40 + 84 / (p + 1)) * o.n_dofs / (ms / 1e3) / 1e9 / hbm, 4)})
+                     # the same time against a byte count that moves both
+                     # sides' face vectors (7 values per face point, not 4)
+                     "hbm_frac_two_sided_face_bytes":
+                         round((8 + 40 + 84 / (p + 1)) * o.n_dofs / (ms / 1e3) / 1e9 / hbm, 4)})
         o.close()
         del src, dst
         torch.cuda.empty_cache()

@@ -1857,7 +1857,7 @@ struct MixedOut {
   double rel = 0.0;     // |b - A x| / |b| (FP64) at return
   double rel0 = 0.0;    // the same at entry
   bool converged = false;
-  bool slow = false;    // probe: the recursion was judged too slow (see mixed_run)
+  bool slow = false;    // probe: the recursion was found too slow (see mixed_run)
 };
 
 // Conjugate gradients in the inner handle's arithmetic T (binary32 vectors
