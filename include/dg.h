@@ -125,13 +125,16 @@ typedef struct {
  *  LAGRANGE: Lagrange polynomials on the k Gauss-Lobatto points.
  *  HERMITE:  the Hermite-like basis (degree >= 3) with the face property of
  *            Sec. 3.1: at xi = 0 only function 0 is nonzero (value 1) and
- *            only function 1 has a nonzero derivative (1), mirror-symmetric
- *            at xi = 1 (functions p and p-1, derivative -1): the cubic
- *            Hermite functions (1-t)^2(1+2t), t(1-t)^2, t^2(1-t),
- *            t^2(3-2t) and between them t^2(1-t)^2 times the Lagrange
- *            polynomials on the interior Gauss-Lobatto points of degree
- *            p - 2, scaled to 1 at their node.  Same operator as LAGRANGE in
- *            another basis of the same space. */
+ *            only function 1 has a nonzero derivative, mirror-symmetric at
+ *            xi = 1 (functions p and p-1).  With the Gauss-Lobatto points
+ *            g_0 = 0 < g_1 < ... < g_p = 1 and w(t) = prod_{j=2}^{p-2}
+ *            (t - g_j): f_0 = (1-t)^2 (1 + c t) w(t) / w(0) with c such
+ *            that f_0'(0) = 0; f_1 = t (1-t)^2 w(t) scaled to f_1(g_1) = 1;
+ *            f_j (2 <= j <= p-2) = t^2 (1-t)^2 times the Lagrange
+ *            polynomial on g_2 .. g_{p-2} that is 1 at g_j, scaled to
+ *            f_j(g_j) = 1; f_{p-1}(t) = f_1(1-t), f_p(t) = f_0(1-t) (nodal at
+ *            the interior points, for conditioning).  Same operator as
+ *            LAGRANGE in another basis of the same space. */
 typedef enum { DG_BASIS_LAGRANGE = 0, DG_BASIS_HERMITE = 1 } dg_basis;
 
 typedef struct dg_handle dg_handle;
@@ -382,6 +385,12 @@ typedef struct {
   char message[160];           /* error message when status != DG_OK */
 } dg_result;
 
+/* Device memory, in bytes, that the server budgets for a request: the
+ * geometry of its FP64 and FP32 operators, the solver's vectors and set-up
+ * scratch (per dof, from the degree and the geometry storage), plus 64 MiB.
+ * -1 for an invalid request (NULL, degree outside 1..8, or a mesh extent
+ * below 1).  Host arithmetic only; no device work.  No counterpart in the
+ * paper. */
 int64_t dg_request_device_bytes(const dg_request *r);
 dg_status dg_server_create(int device, int64_t budget_bytes, int slots, dg_server **out);
 /* Admission policy: which queued request a free slot takes.  policy 0

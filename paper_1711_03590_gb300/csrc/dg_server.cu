@@ -206,7 +206,7 @@ void worker_main(dg_server* srv) {
 extern "C" {
 
 int64_t dg_request_device_bytes(const dg_request* r) {
-  if (!r || r->degree < 1 || r->degree > 8) return -1;
+  if (!r || r->degree < 1 || r->degree > 8 || r->n[0] < 1 || r->n[1] < 1 || r->n[2] < 1) return -1;
   const double k = r->degree + 1;
   const double dofs = (double)request_dofs(r);
   double geo = 0.0;  // bytes per dof, FP64 + FP32 operators

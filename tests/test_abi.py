@@ -86,3 +86,28 @@ def test_degenerate_and_out_of_range_setup_arguments(case):
     with pytest.raises(dgp.DGError) as e:
         dgp.dg_setup(m, case.get("degree", 2), case.get("geom", "full"), o)
     assert e.value.status == dgp.DG_ERR_ARG
+
+
+def test_request_memory_estimate_is_host_arithmetic():
+    """The server's admission estimate (no device work, so no GPU needed):
+    invalid requests give -1; the estimate grows with the mesh, in
+    proportion to the dofs once the fixed 64 MiB is taken off, and orders
+    the geometry storages by their per-point arrays (G3 > G4 > Cartesian)."""
+    import paper_1711_03590_gb300 as dgp
+    dgp.build()
+    est = dgp.dg_request_device_bytes
+    assert est(dgp.make_request(8, 0)) == -1
+    assert est(dgp.make_request(8, 9)) == -1
+    assert est(dgp.make_request((0, 8, 8), 3)) == -1
+    fixed = 64 << 20
+    small, large = est(dgp.make_request(16, 4)), est(dgp.make_request(32, 4))
+    assert fixed < small < large
+    assert abs((large - fixed) / (small - fixed) - 8.0) < 1e-6
+    g3 = est(dgp.make_request(16, 4, geom="full"))
+    g4 = est(dgp.make_request(16, 4, geom="merged"))
+    g2 = est(dgp.make_request(16, 4, geom="positions"))
+    cart = est(dgp.make_request(16, 4, mapping=0))
+    assert g3 > g4 > g2 > cart > fixed
+    # 32^3 cells at p = 4 with G3 storage: 4,096,000 dofs at
+    # (10 + 21/5) x (8 + 4) geometry bytes and 88 vector bytes per dof
+    assert large == int(4096000 * ((10 + 21 / 5) * 12 + 88)) + fixed
